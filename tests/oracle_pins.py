@@ -1,0 +1,245 @@
+"""Checks that pin the FP64 oracle to facts outside itself.
+
+Each check takes an oracle build (``lib``; None = the default build) and
+raises AssertionError on failure. ``tests/test_oracle_pins.py`` runs them on
+the real oracle; ``tests/test_oracle_mutants.py`` runs them on copies of the
+oracle with a planted mistake and requires at least one to fail.
+
+What each check compares against:
+* closed forms: the two-point problem (alpha = min(C, 2 / (2 - 2k)), k the
+  kernel value) and the RBF kernel of known distances;
+* a brute-force exact solver of the dual QP (``qp_reference``) for n <= 12;
+* invariants that hold for any correct SMO run: sum y alpha = 0, box
+  constraints, monotone dual objective, maintained f equal to Eq. (fcache)
+  recomputed densely with numpy, KKT gap at exit;
+* numpy dense inner products and Gram matrices;
+* structural facts: shrinking does not change the optimum; with a correct
+  shrink rule the shrunk run selects the same pairs as the plain run until
+  late in the run; the first pair at alpha = 0 is (lowest index with y = +1,
+  lowest index with y = -1) by Eq. (bminmax).
+"""
+import numpy as np
+
+import oracle
+from paper_1406_5161_gb300 import synth
+import os as _os, sys as _sys
+_sys.path.insert(0, _os.path.dirname(__file__))
+from qp_reference import dual_bruteforce, dual_objective, rbf_matrix
+
+
+# every run is capped: a wrong oracle may never converge
+MAXIT = 200000
+
+
+def _dense(X):
+    return X.to_dense().astype(np.float64)
+
+
+def check_dot_and_norm(lib=None):
+    p = synth.random_sparse(40, 30, 0.3, seed=11, min_nnz=1)
+    D = _dense(p.X)
+    for i in range(0, 40, 3):
+        for j in range(0, 40, 7):
+            ref = D[i] @ D[j]
+            got = oracle.dot(p.X, i, p.X, j, lib=lib)
+            assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref)), (i, j, got, ref)
+        assert abs(oracle.sqnorm(p.X, i, lib=lib) - D[i] @ D[i]) <= 1e-12 * max(1, D[i] @ D[i])
+
+
+def check_kernel_closed_form(lib=None):
+    # K(x,z) = exp(-g ||x-z||^2): distance 2 from norms 1, 3 and dot 1
+    for g in (0.05, 0.5, 2.0):
+        got = oracle.kernel(g, 1.0, 3.0, 1.0, lib=lib)
+        assert abs(got - np.exp(-2.0 * g)) <= 1e-15, (g, got)
+        assert oracle.kernel(g, 2.0, 2.0, 2.0, lib=lib) == 1.0
+        # rounding below zero is clamped
+        assert oracle.kernel(g, 1.0, 1.0, 1.0 + 1e-15, lib=lib) == 1.0
+
+
+def _two_point(dist, C, gamma):
+    x = np.array([[0.0], [dist]], dtype=np.float32)
+    X = synth.csr_from_dense(x, keep_zeros=True)
+    y = np.array([1, -1], dtype=np.int8)
+    return X, y
+
+
+def check_two_point_closed_form(lib=None):
+    for dist, C, gamma in [(1.0, 100.0, 0.5), (0.25, 100.0, 1.0), (3.0, 0.4, 0.1),
+                           (2.0, 1.0, 0.05), (0.5, 5.0, 0.3)]:
+        X, y = _two_point(dist, C, gamma)
+        k = np.exp(-gamma * float(np.float32(dist)) ** 2)
+        a_star = min(C, 2.0 / (2.0 - 2.0 * k))
+        r = oracle.smo(X, y, C, gamma, 1e-6, max_iter=10, lib=lib)
+        assert r["iters"] == 1, r["iters"]
+        assert np.allclose(r["alpha"], a_star, rtol=1e-14, atol=0), (r["alpha"], a_star)
+        if a_star < C:
+            assert np.abs(r["f"]).max() <= 1e-13
+            assert abs(r["b"]) <= 1e-13
+        else:
+            # both at C: b is the midpoint of b_up = f_2 and b_low = f_1
+            f1 = C * (1 - k) - 1.0
+            assert abs(r["f"][0] - f1) <= 1e-13 and abs(r["f"][1] + f1) <= 1e-13
+            assert abs(r["b"]) <= 1e-13
+
+
+def _tiny(n, seed, C, d=3, gamma=0.5):
+    p = synth.small_dense(n, d, seed, sep=0.3, C=C, gamma=gamma, tau=1e-10)
+    return p
+
+
+def check_bruteforce(lib=None, cases=((4, 1, 1.0), (6, 2, 0.5), (7, 3, 10.0),
+                                      (8, 4, 1.0), (9, 5, 2.0))):
+    for n, seed, C in cases:
+        p = _tiny(n, seed, C)
+        D = _dense(p.X)
+        K = rbf_matrix(D, D, p.gamma)
+        w_star, a_star = dual_bruteforce(K, p.y.astype(np.float64), C)
+        r = oracle.smo(p.X, p.y, C, p.gamma, 1e-10, max_iter=MAXIT, lib=lib)
+        w = dual_objective(r["alpha"], p.y.astype(np.float64), K)
+        assert abs(w - w_star) <= 1e-9 * max(1.0, abs(w_star)), (n, seed, w, w_star)
+        assert np.abs(r["alpha"] - a_star).max() <= 1e-6, (n, seed, r["alpha"], a_star)
+        assert abs(r["objective"] - w_star) <= 1e-9 * max(1.0, abs(w_star))
+
+
+def check_invariants(lib=None):
+    for seed, C, gamma in [(21, 1.0, 0.1), (22, 0.3, 0.5), (23, 5.0, 0.05)]:
+        p = synth.small_dense(60, 4, seed, sep=0.4, C=C, gamma=gamma, tau=1e-4)
+        D = _dense(p.X)
+        K = rbf_matrix(D, D, gamma)
+        y = p.y.astype(np.float64)
+        r = oracle.smo(p.X, p.y, C, gamma, 1e-4, max_iter=MAXIT, trace_len=MAXIT,
+                       record_objective=True, lib=lib)
+        a = r["alpha"]
+        assert r["status"] == 0
+        assert abs(y @ a) <= 1e-12 * len(a) * C
+        assert (a >= 0).all() and (a <= C).all()
+        objs = r["objectives"]
+        assert (np.diff(objs) >= -1e-12 * np.abs(objs[1:]).max()).all(), "objective decreased"
+        # maintained f equals Eq. (fcache) from scratch (dense numpy)
+        f_ref = K @ (a * y) - y
+        assert np.abs(r["f"] - f_ref).max() <= 1e-10 * max(1.0, np.abs(f_ref).max())
+        # objective equals the dual objective of alpha (numpy)
+        assert abs(r["objective"] - dual_objective(a, y, K)) <= 1e-10 * max(1.0, abs(r["objective"]))
+        # KKT at exit over all samples, from the recomputed f
+        up = ((a > 0) & (a < C)) | ((y > 0) & (a == 0)) | ((y < 0) & (a == C))
+        low = ((a > 0) & (a < C)) | ((y > 0) & (a == C)) | ((y < 0) & (a == 0))
+        assert f_ref[low].max() - f_ref[up].min() <= 2e-4 + 1e-12
+        # the first pair at alpha = 0 follows Eq. (bminmax) with lowest index
+        assert r["trace"][0, 0] == int(np.nonzero(p.y > 0)[0][0])
+        assert r["trace"][0, 1] == int(np.nonzero(p.y < 0)[0][0])
+        # threshold: mean of f over the free set
+        free = (a > 0) & (a < C)
+        if free.any():
+            assert abs(r["b"] - f_ref[free].mean()) <= 1e-10
+
+
+def check_gradient_and_decision(lib=None):
+    p = synth.random_sparse(80, 25, 0.25, seed=31, min_nnz=1, C=2.0, gamma=0.2)
+    r = oracle.smo(p.X, p.y, p.C, p.gamma, 1e-3, max_iter=MAXIT, lib=lib)
+    assert r["status"] == 0
+    D = _dense(p.X)
+    K = rbf_matrix(D, D, p.gamma)
+    y = p.y.astype(np.float64)
+    a = r["alpha"]
+    g = oracle.gradient(p.X, p.y, a, p.gamma, lib=lib)
+    assert np.abs(g - (K @ (a * y) - y)).max() <= 1e-12 * max(1, np.abs(g).max())
+    # Algorithm 6 on a subset equals the definition; other entries kept
+    rows = np.arange(0, 80, 5)
+    f_in = np.full(80, 7.0)
+    fr = oracle.reconstruct(p.X, p.y, a, p.gamma, rows, f_in, lib=lib)
+    assert np.abs(fr[rows] - (K @ (a * y) - y)[rows]).max() <= 1e-12
+    keep = np.setdiff1d(np.arange(80), rows)
+    assert (fr[keep] == 7.0).all()
+    # decision at the training points: sum a y K - b = f + y - b
+    dv = oracle.decision(p.X, p.y, a, r["b"], p.gamma, p.X, lib=lib)
+    assert np.abs(dv - (K @ (a * y) - r["b"])).max() <= 1e-12 * max(1, np.abs(dv).max())
+    # held-out points against a dense Gram matrix
+    q = synth.random_sparse(30, 25, 0.25, seed=32, min_nnz=1)
+    Kz = rbf_matrix(_dense(q.X), D, p.gamma)
+    dz = oracle.decision(p.X, p.y, a, r["b"], p.gamma, q.X, lib=lib)
+    assert np.abs(dz - (Kz @ (a * y) - r["b"])).max() <= 1e-12 * max(1, np.abs(dz).max())
+    # free support vectors lie on the margin up to the stopping tolerance
+    free = (a > 0) & (a < p.C)
+    if free.any():
+        assert np.abs(dv[free] - y[free]).max() <= 2 * p.tau + 1e-9
+    # kkt() agrees with the numpy gap
+    kk = oracle.kkt(p.X, p.y, a, p.C, p.gamma, lib=lib)
+    assert kk["gap"] <= 2 * p.tau + 1e-12
+
+
+SHRINK_POLICIES = [
+    # Table 3 rows 2-13: (kind, value, reconstruction)
+    (oracle.SHRINK_FIXED, 2, oracle.RECON_SINGLE),
+    (oracle.SHRINK_FIXED, 500, oracle.RECON_SINGLE),
+    (oracle.SHRINK_FIXED, 1000, oracle.RECON_SINGLE),
+    (oracle.SHRINK_FRACTION, 0.05, oracle.RECON_SINGLE),
+    (oracle.SHRINK_FRACTION, 0.10, oracle.RECON_SINGLE),
+    (oracle.SHRINK_FRACTION, 0.50, oracle.RECON_SINGLE),
+    (oracle.SHRINK_FIXED, 2, oracle.RECON_MULTI),
+    (oracle.SHRINK_FIXED, 500, oracle.RECON_MULTI),
+    (oracle.SHRINK_FIXED, 1000, oracle.RECON_MULTI),
+    (oracle.SHRINK_FRACTION, 0.05, oracle.RECON_MULTI),
+    (oracle.SHRINK_FRACTION, 0.10, oracle.RECON_MULTI),
+    (oracle.SHRINK_FRACTION, 0.50, oracle.RECON_MULTI),
+]
+
+
+def _shrink_problem():
+    return synth.onehot_sparse(n=1500, n_test=0, seed=41)
+
+
+def check_shrink_same_optimum(lib=None, policies=SHRINK_POLICIES):
+    p = _shrink_problem()
+    plain = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=MAXIT, lib=lib)
+    assert plain["status"] == 0
+    for kind, value, rec in policies:
+        s = oracle.smo_shrink(p.X, p.y, p.C, p.gamma, p.tau, kind, value, rec,
+                              max_iter=MAXIT, lib=lib)
+        assert s["status"] == 0
+        kk = oracle.kkt(p.X, p.y, s["alpha"], p.C, p.gamma, lib=lib)
+        assert kk["gap"] <= 2 * p.tau + 1e-9, (kind, value, rec, kk["gap"])
+        assert abs(kk["objective"] - plain["objective"]) <= 1e-5 * abs(plain["objective"]), \
+            (kind, value, rec, kk["objective"], plain["objective"])
+        # the f the run ends with equals f recomputed from its alpha
+        assert np.abs(s["f"] - kk["f"]).max() <= 1e-9
+
+
+def check_shrink_none_is_plain(lib=None):
+    p = synth.small_dense(200, 5, 51, C=1.0, gamma=0.1)
+    a = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=MAXIT, lib=lib)
+    b = oracle.smo_shrink(p.X, p.y, p.C, p.gamma, p.tau, oracle.SHRINK_NONE, 0, 0,
+                          max_iter=MAXIT, lib=lib)
+    assert a["status"] == 0
+    assert a["iters"] == b["iters"]
+    assert np.array_equal(a["alpha"], b["alpha"]) and np.array_equal(a["f"], b["f"])
+
+
+def check_shrink_keeps_path(lib=None):
+    """A sample removed by Eq. (shrink) is at a bound and on the right side of
+    both thresholds, so it is not the next maximal violator: the shrunk run
+    must select exactly the plain run's pairs until late in the run."""
+    p = _shrink_problem()
+    n_it = MAXIT
+    plain = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=n_it, trace_len=n_it, lib=lib)
+    s = oracle.smo_shrink(p.X, p.y, p.C, p.gamma, p.tau, oracle.SHRINK_FRACTION, 0.05,
+                          oracle.RECON_MULTI, max_iter=n_it, trace_len=n_it, lib=lib)
+    assert plain["status"] == 0 and s["status"] == 0
+    m = min(len(plain["trace"]), len(s["trace"]))
+    diff = np.nonzero((plain["trace"][:m] != s["trace"][:m]).any(axis=1))[0]
+    first = int(diff[0]) if len(diff) else m
+    assert s["n_shrink"] >= 1
+    assert s["active"].min() < p.X.n // 2, "shrinking removed too little"
+    assert first >= 0.5 * plain["iters"], (first, plain["iters"])
+
+
+ALL_CHECKS = [
+    check_dot_and_norm,
+    check_kernel_closed_form,
+    check_two_point_closed_form,
+    check_bruteforce,
+    check_invariants,
+    check_gradient_and_decision,
+    check_shrink_same_optimum,
+    check_shrink_none_is_plain,
+    check_shrink_keeps_path,
+]
