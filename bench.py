@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 SVM trainer on the a9a-shaped one-hot workload.
+
+Workload: n = 32,561 training rows, d = 123 binary columns (14 one-hot
+groups, exactly 14 ones per row), labels from an RBF teacher (24% positive,
+5% flipped), RBF gamma = 0.05, C = 1, tau = 1e-3, plus 10,000 held-out rows.
+All inputs are seeded synthetic data (paper_1406_5161_gb300.synth); the
+paper's own datasets are not used.
+
+One step = one full training to the KKT tolerance through the C ABI
+(svm_train: ingest, fused SMO steps with adaptive shrinking, gradient
+reconstruction, threshold b) followed by the decision function on the 10,000
+held-out rows (svm_decision). The metric is SMO iterations per second over
+the timed steps; time-to-KKT is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank trains its own
+replica (the solve does not shard); the value is the sum of all ranks'
+iterations divided by the slowest rank's time. `--impl reference` times the
+FP64 CPU oracle (plain SMO, no shrinking) on a bounded prefix of the same
+workload on the host cores; only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SMO iter/s"
+UNIT = "iter/s"
+WORKLOAD = ("onehot_sparse (a9a-shaped): n=32561, d=123, 14 ones/row, C=1, gamma=0.05, "
+            "tau=1e-3; train to KKT + decision on 10000 held-out rows")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--policy", default="Multi5pc")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("smo_step.cuh", "svm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1406_5161_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the fused step kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "smo_step_c2_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def workload():
+    from paper_1406_5161_gb300 import synth
+    return synth.onehot_sparse()
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    p = workload()
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    m = 400  # SMO steps per timed step: a bounded prefix of the solve
+    for _ in range(args.warmup):
+        oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=m)
+    t0 = time.perf_counter()
+    iters = 0
+    for _ in range(args.steps):
+        r = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=m)
+        iters += r["iters"]
+    dt = time.perf_counter() - t0
+    value = iters / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "policy": "Original (oracle has no shrinking)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {m} SMO steps of the workload per step (FP64 oracle, Algorithm 1)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(p):
+    """The oracle as it stands on the host cores, on a bounded prefix."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=100)
+    per = (time.perf_counter() - t0) / 100
+    m = int(max(100, min(15000, 12.0 / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    r = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=m)
+    dt = time.perf_counter() - t0
+    return {"value": r["iters"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {r['iters']} SMO steps of the same workload (FP64 oracle, no shrinking), "
+                      f"{dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gb300(args, rank, world, local):
+    import numpy as np
+    import torch
+    import paper_1406_5161_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.load()
+    p = workload()
+    policy = pkg.POLICIES[args.policy]
+    Xd = pkg.to_device(p.X)
+    yd = torch.as_tensor(p.y, device="cuda")
+    Zd = pkg.to_device(p.Z)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step():
+        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream)
+        dz = pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
+        return r, dz
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = pkg.svm_kernel_launches()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e2 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iters = row_visits = 0
+    ms_smo = ms_recon = 0.0
+    smo_launch_count = 0
+    stats = None
+    for k in range(args.steps):
+        flush.zero_()                    # L2 flushed between timed steps
+        e0[k].record(stream)
+        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream)
+        e1[k].record(stream)
+        pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
+        e2[k].record(stream)
+        stats = r["stats"]
+        iters += r["iters"]
+        row_visits += stats["row_visits"]
+        ms_smo += stats["ms_smo"]
+        ms_recon += stats["ms_recon"]
+    torch.cuda.synchronize()
+    launches = pkg.svm_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, c in zip(e0, e2)]
+    kkt_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    t_total = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+        it = torch.tensor([iters], dtype=torch.float64, device="cuda")
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        iters_all = float(it.item())
+    else:
+        iters_all = float(iters)
+    value = iters_all / t_total
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 or world > 1:
+        from paper_1406_5161_gb300 import synth
+
+        def pinned(a):
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t.numpy()[...] = a
+            return t.numpy()
+
+        def pinned_csr(X):
+            return synth.CSR(X.n, X.d, pinned(X.indptr), pinned(X.indices), pinned(X.values))
+
+        Xh, Zh, yh = pinned_csr(p.X), pinned_csr(p.Z), pinned(p.y)
+        alpha_h = pinned(np.zeros(p.X.n))
+        out_h = pinned(np.zeros(p.Z.n))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_iters = 0
+        n_e2e = max(1, min(3, args.steps))
+        for _ in range(n_e2e):
+            r = pkg.svm_train(Xh, yh, p.C, p.gamma, p.tau, shrink=policy, alpha_out=alpha_h)
+            pkg.svm_decision(Xh, yh, alpha_h, r["b"], p.gamma, Zh, out=out_h)
+            e2e_iters += r["iters"]
+        dt = time.perf_counter() - t0
+        nbytes = lambda X: X.indptr.nbytes + X.indices.nbytes + X.values.nbytes  # noqa: E731
+        h2d = (nbytes(p.X) + p.y.nbytes) * 2 + 8 * p.X.n + nbytes(p.Z)
+        d2h = 8 * p.X.n + 8 * p.Z.n
+        e2e = {"value": e2e_iters / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * dt / n_e2e}
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the fused step kernel
+    nnz_row = p.X.nnz / p.X.n
+    b_row = 4 * nnz_row + 8 + 16 + 1
+    alg_bytes = row_visits * b_row + iters * 2 * 4 * nnz_row
+    achieved = alg_bytes / (ms_smo / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = measured_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "smo_persistent_kernel",
+                "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "bytes_per_row_visit": b_row, "row_visits_per_step": row_visits / args.steps,
+                "kernel_ms_per_step": ms_smo / args.steps}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "policy": args.policy,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "n": int(p.X.n), "d": int(p.X.d), "held_out": int(p.Z.n)},
+            "time_to_kkt_ms": statistics.mean(kkt_ms),
+            "iters_per_solve": iters / args.steps,
+            "recon_ms_per_step": ms_recon / args.steps,
+            "gpu_launches": int(launches),
+            "clocks": clk, "roofline": roofline, "e2e": e2e}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_gb300(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

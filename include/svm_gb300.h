@@ -1,0 +1,201 @@
+/*
+ * svm_gb300.h -- C ABI of a GB300-native (sm_103a) kernel-SVM trainer.
+ *
+ * The library trains a two-class soft-margin SVM with an RBF kernel by the
+ * SMO method of "Fast Support Vector Machines Using Parallel Adaptive
+ * Shrinking on Distributed Systems" (arXiv:1406.5161):
+ *   - the dual problem of Section II-A, Eq. (lagdual) under Eq. (eqconst);
+ *   - Keerthi's two-threshold SMO, Algorithm 1, with the gradient cache f of
+ *     Eq. (fcache), its update Eq. (fup), the index sets Eq. (setinfo), the
+ *     maximal-violating pair Eq. (bminmax), the stop test Eq. (kktterm) and
+ *     the pair step Eqs. (alphaup)/(rho);
+ *   - adaptive shrinking (Eq. (shrink), Algorithms 4 and 5, the counter
+ *     heuristics of Section III-C and Table 3) with gradient reconstruction
+ *     (Algorithm 6);
+ *   - the classifier Eq. (classi) with the threshold b of Section III-A.
+ *
+ * Conventions shared by every call:
+ *   - Kernel: K(x, z) = exp(-gamma * ||x - z||^2); gamma = 1 / (2 sigma^2)
+ *     in the paper's notation (Section V-A).
+ *   - f_i = sum_j alpha_j y_j K(x_i, x_j) - y_i (Eq. fcache).
+ *   - Pair selection takes the lowest index on ties (both argmin and argmax).
+ *   - Every call returns an int status (enum svm_status). No call aborts or
+ *     throws; svm_last_error() gives a message for the last failing call of
+ *     the calling thread.
+ *   - All calls are synchronous with respect to the host unless stated: on
+ *     return, outputs are written and the library's device work is done.
+ *   - The library allocates its own device workspace (stream-ordered) and
+ *     frees it before returning; inputs are only read, never kept.
+ */
+#ifndef SVM_GB300_H
+#define SVM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status codes */
+enum svm_status {
+    SVM_OK = 0,
+    SVM_NOT_CONVERGED = 1,   /* max_iter reached; outputs are valid but not optimal */
+    SVM_PENDING = 2,         /* server: job still queued or running */
+    SVM_ERR_ARG = -1,        /* invalid argument (see svm_last_error) */
+    SVM_ERR_OOM = -2,        /* device or host allocation failed */
+    SVM_ERR_BUDGET = -3,     /* server: job larger than the device-memory budget */
+    SVM_ERR_TIMEOUT = -4,    /* a device-side wait exceeded its limit; the kernel
+                                gave up and returned, the context stays usable */
+    SVM_ERR_CUDA = -5,       /* a CUDA runtime call failed */
+    SVM_ERR_CANCELLED = -6,  /* server: job cancelled */
+    SVM_ERR_UNSUPPORTED = -7 /* valid input outside this build's limits
+                                (e.g. more columns than the on-chip target rows hold) */
+};
+
+/* ------------------------------------------------------------- precision */
+enum svm_precision {
+    /* FP64 everywhere the result depends on it: inner products, kernel
+     * values, f, the pair step, b and the gap. Binary (all values 1.0) CSR
+     * input is detected at ingest and its kernel values are taken from an
+     * exact FP64 table of exp(-gamma * k), k the integer squared distance. */
+    SVM_FP64 = 0,
+    /* Inner products and exp in FP32 on BF16-rounded feature values (the
+     * reconstruction and decision contractions on the tcgen05 tensor cores
+     * with FP32 accumulation); f, the pair step, b and the gap stay FP64. */
+    SVM_MIXED_BF16 = 1
+};
+
+/* ----------------------------------------------------------- shrinking */
+enum svm_shrink_kind {
+    SVM_SHRINK_NONE = 0,     /* Table 3 row 1, "Original" (Algorithm 3's loop) */
+    SVM_SHRINK_FIXED = 1,    /* counter h = value (Table 3 "random: k" rows, read
+                                as the fixed constant k) */
+    SVM_SHRINK_FRACTION = 2  /* counter h = ceil(value * N) (Table 3 "numsamples") */
+};
+
+enum svm_recon {
+    SVM_RECON_SINGLE = 0,    /* Algorithm 5: one reconstruction, then no shrinking */
+    SVM_RECON_MULTI = 1      /* shrinking throughout; reconstruct at first_factor*tau
+                                the first time and at 2*tau afterwards */
+};
+
+/* CSR matrix. Row i holds columns indices[indptr[i] .. indptr[i+1]) with
+ * values at the same positions. Column indices must be strictly increasing
+ * within a row and in [0, d). values == NULL means every stored value is 1.0
+ * (binary pattern). When on_device != 0 every pointer of the call that
+ * receives this matrix (indptr, indices, values, labels, alpha, outputs of
+ * length n or m) is device memory of the current device; otherwise host. */
+typedef struct svm_csr {
+    int64_t n;               /* rows */
+    int64_t d;               /* columns */
+    const int64_t *indptr;   /* n + 1 entries, indptr[0] == 0 */
+    const int32_t *indices;  /* indptr[n] entries */
+    const float *values;     /* indptr[n] entries, or NULL */
+    int32_t on_device;
+    int32_t reserved;
+} svm_csr;
+
+typedef struct svm_params {
+    double C;                /* box bound, > 0 (Eq. eqconst) */
+    double gamma;            /* RBF width, > 0 */
+    double tau;              /* stop when b_low - b_up <= 2 tau (Eq. kktterm), > 0 */
+    int64_t max_iter;        /* SMO step limit (<= 0: 100 * n + 1e6) */
+    int32_t precision;       /* enum svm_precision */
+    int32_t tie_break;       /* 0: lowest index (the only rule) */
+    void *stream;            /* cudaStream_t to run on; NULL = legacy default stream */
+    int32_t *trace;          /* optional HOST buffer: (i_up, i_low) of the first
+                                trace_len steps, 2 ints per step; -1 if not reached */
+    int64_t trace_len;
+    int32_t flags;           /* bitwise OR of SVM_FLAG_* */
+    int32_t ctas;            /* CTAs (= row segments) of the fused step; 0 = one per
+                                SM (capped by n / 16); larger values are clamped */
+} svm_params;
+
+/* Keep every row segment in global memory even when it would fit in the
+ * SM's shared memory (the default holds rows, f, alpha and the index sets of
+ * each segment on chip for the whole solve when they fit). */
+#define SVM_FLAG_STREAM_ROWS 1
+/* Record the SM cycles one CTA spends in each phase of a step
+ * (svm_stats.phase_ms, converted at the device's maximum clock). */
+#define SVM_FLAG_PHASE_TIMES 2
+
+typedef struct svm_shrink_policy {
+    int32_t kind;            /* enum svm_shrink_kind */
+    int32_t recon;           /* enum svm_recon */
+    double value;            /* k (FIXED) or fraction of N (FRACTION) */
+    double first_factor;     /* first reconstruction when the active gap <=
+                                first_factor * tau; <= 0 means 20 (Algorithm 5) */
+} svm_shrink_policy;
+
+typedef struct svm_stats {
+    int64_t iters;           /* SMO steps */
+    int64_t shrink_events;
+    int64_t reconstructions;
+    int64_t final_active;    /* active-set size when the last phase ended */
+    int64_t n_sv;            /* alpha > 0 */
+    int64_t n_bound;         /* alpha == C */
+    int64_t row_visits;      /* sum over steps of the active-set size */
+    double b_up, b_low;      /* Eq. (bminmax) over all samples at exit */
+    double objective;        /* dual objective W at exit */
+    double ms_total;         /* wall time of the call */
+    double ms_smo;           /* device time in the fused SMO kernel(s) */
+    double ms_recon;         /* device time in reconstruction (Algorithm 6) */
+    int32_t binary_input;    /* 1 when the binary-pattern path was used */
+    int32_t launches;        /* kernel launches issued by the call */
+    int32_t resident;        /* 1 when row segments were held in shared memory */
+    int32_t ctas;            /* CTAs (= row segments) of the fused step */
+    int32_t lanes_per_row;   /* lanes that share one row in the row pass */
+    int32_t reserved;
+    double phase_ms[6];      /* with SVM_FLAG_PHASE_TIMES: time of CTA 0 per step
+                                phase, summed over steps: target rows, pair step,
+                                row pass + CTA reduction, publish, grid exchange,
+                                other */
+    double cta_busy_ms_min;  /* with SVM_FLAG_PHASE_TIMES: least and most time a */
+    double cta_busy_ms_max;  /* CTA spent from step start to publishing its candidate */
+} svm_stats;
+
+/*
+ * svm_train -- solve the dual QP (Eq. lagdual) by SMO (Algorithm 1) with the
+ * given shrinking policy (Algorithms 4-6).
+ *   X         training rows (n >= 2, d >= 1); see svm_csr for memory space
+ *   y         n labels, +1 or -1, both classes present (same space as X)
+ *   params    C, gamma, tau, max_iter, precision, stream, trace
+ *   policy    shrinking policy; NULL = SVM_SHRINK_NONE
+ *   alpha_out n doubles written with the multipliers (same space as X;
+ *             caller-owned)
+ *   b_out     threshold b of Section III-A (host)
+ *   iters_out SMO steps (host, may be NULL)
+ *   stats     optional (host, may be NULL)
+ * Returns SVM_OK, SVM_NOT_CONVERGED (outputs valid), or an error; on error the
+ * outputs are unspecified.
+ */
+int svm_train(const svm_csr *X, const int8_t *y, const svm_params *params,
+              const svm_shrink_policy *policy, double *alpha_out, double *b_out,
+              int64_t *iters_out, svm_stats *stats);
+
+/*
+ * svm_decision -- Eq. (classi) before the sign:
+ *   out[k] = sum_{j : alpha_j > 0} alpha_j y_j K(x_j, z_k) - b.
+ *   X, y, alpha  training rows, labels and multipliers (space of X)
+ *   Z            m query rows with Z->d == X->d (space of Z; out in that space)
+ *   precision    enum svm_precision (SVM_MIXED_BF16 uses the tensor cores)
+ *   stream       cudaStream_t or NULL
+ */
+int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double b,
+                 double gamma, const svm_csr *Z, int32_t precision, void *stream,
+                 double *out);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all calls), for accounting of device work. */
+int64_t svm_kernel_launches(void);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *svm_last_error(void);
+
+/* Library version string. */
+const char *svm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVM_GB300_H */

@@ -1,0 +1,253 @@
+"""ctypes binding of the C ABI in include/svm_gb300.h.
+
+Argument marshalling only: numpy arrays are passed as host pointers, CUDA
+torch tensors as device pointers. Every step of training and prediction runs
+in the CUDA library; when the library cannot be built or loaded, every call
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+SVM_OK, SVM_NOT_CONVERGED, SVM_PENDING = 0, 1, 2
+SVM_ERR_ARG, SVM_ERR_OOM, SVM_ERR_BUDGET, SVM_ERR_TIMEOUT = -1, -2, -3, -4
+SVM_ERR_CUDA, SVM_ERR_CANCELLED, SVM_ERR_UNSUPPORTED = -5, -6, -7
+SVM_FP64, SVM_MIXED_BF16 = 0, 1
+SVM_SHRINK_NONE, SVM_SHRINK_FIXED, SVM_SHRINK_FRACTION = 0, 1, 2
+SVM_RECON_SINGLE, SVM_RECON_MULTI = 0, 1
+SVM_FLAG_STREAM_ROWS = 1
+SVM_FLAG_PHASE_TIMES = 2
+
+STATUS_NAMES = {0: "SVM_OK", 1: "SVM_NOT_CONVERGED", 2: "SVM_PENDING", -1: "SVM_ERR_ARG",
+                -2: "SVM_ERR_OOM", -3: "SVM_ERR_BUDGET", -4: "SVM_ERR_TIMEOUT",
+                -5: "SVM_ERR_CUDA", -6: "SVM_ERR_CANCELLED", -7: "SVM_ERR_UNSUPPORTED"}
+
+
+class svm_csr(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("d", ct.c_int64), ("indptr", ct.c_void_p),
+                ("indices", ct.c_void_p), ("values", ct.c_void_p),
+                ("on_device", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class svm_params(ct.Structure):
+    _fields_ = [("C", ct.c_double), ("gamma", ct.c_double), ("tau", ct.c_double),
+                ("max_iter", ct.c_int64), ("precision", ct.c_int32), ("tie_break", ct.c_int32),
+                ("stream", ct.c_void_p), ("trace", ct.c_void_p), ("trace_len", ct.c_int64),
+                ("flags", ct.c_int32), ("ctas", ct.c_int32)]
+
+
+class svm_shrink_policy(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("recon", ct.c_int32), ("value", ct.c_double),
+                ("first_factor", ct.c_double)]
+
+
+class svm_stats(ct.Structure):
+    _fields_ = [("iters", ct.c_int64), ("shrink_events", ct.c_int64),
+                ("reconstructions", ct.c_int64), ("final_active", ct.c_int64),
+                ("n_sv", ct.c_int64), ("n_bound", ct.c_int64), ("row_visits", ct.c_int64),
+                ("b_up", ct.c_double), ("b_low", ct.c_double), ("objective", ct.c_double),
+                ("ms_total", ct.c_double), ("ms_smo", ct.c_double), ("ms_recon", ct.c_double),
+                ("binary_input", ct.c_int32), ("launches", ct.c_int32),
+                ("resident", ct.c_int32), ("ctas", ct.c_int32), ("lanes_per_row", ct.c_int32),
+                ("reserved", ct.c_int32), ("phase_ms", ct.c_double * 6),
+                ("cta_busy_ms_min", ct.c_double), ("cta_busy_ms_max", ct.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
+        d["phase_ms"] = list(self.phase_ms)
+        return d
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SvmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsvmgb.so (building it with nvcc when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("CUDA library libsvmgb.so is missing and could not be built")
+            lib = ct.CDLL(_build.LIB)
+            P = ct.c_void_p
+            lib.svm_train.restype = ct.c_int
+            lib.svm_train.argtypes = [P, P, P, P, P, P, P, P]
+            lib.svm_decision.restype = ct.c_int
+            lib.svm_decision.argtypes = [P, P, P, ct.c_double, ct.c_double, P, ct.c_int32, P, P]
+            lib.svm_last_error.restype = ct.c_char_p
+            lib.svm_last_error.argtypes = []
+            lib.svm_version.restype = ct.c_char_p
+            lib.svm_version.argtypes = []
+            lib.svm_kernel_launches.restype = ct.c_int64
+            lib.svm_kernel_launches.argtypes = []
+            _lib = lib
+    return _lib
+
+
+def svm_kernel_launches() -> int:
+    return int(load().svm_kernel_launches())
+
+
+def svm_last_error() -> str:
+    return load().svm_last_error().decode()
+
+
+def svm_version() -> str:
+    return load().svm_version().decode()
+
+
+# ------------------------------------------------------------ marshalling
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class _Hold:
+    """Keeps the buffers behind raw pointers alive during a call."""
+
+    def __init__(self):
+        self.keep = []
+
+    def np(self, a, dtype):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self.keep.append(a)
+        return a.ctypes.data
+
+    def tensor(self, t, dtype_name: str):
+        import torch
+        dt = getattr(torch, dtype_name)
+        if t.dtype != dt or not t.is_contiguous():
+            t = t.to(dt).contiguous()
+        self.keep.append(t)
+        return t.data_ptr()
+
+
+@dataclass
+class DeviceCSR:
+    """CSR matrix whose arrays are CUDA torch tensors."""
+    n: int
+    d: int
+    indptr: object
+    indices: object
+    values: object  # or None for binary rows
+
+
+def to_device(X, device="cuda") -> DeviceCSR:
+    """Copy a host CSR (numpy) into CUDA tensors."""
+    import torch
+    vals = None if X.values is None else torch.as_tensor(np.ascontiguousarray(X.values, np.float32), device=device)
+    return DeviceCSR(int(X.n), int(X.d),
+                     torch.as_tensor(np.ascontiguousarray(X.indptr, np.int64), device=device),
+                     torch.as_tensor(np.ascontiguousarray(X.indices, np.int32), device=device),
+                     vals)
+
+
+def _csr(h: _Hold, X) -> tuple:
+    if isinstance(X, DeviceCSR) or _is_torch_cuda(getattr(X, "indptr", None)):
+        c = svm_csr(int(X.n), int(X.d), h.tensor(X.indptr, "int64"), h.tensor(X.indices, "int32"),
+                    None if X.values is None else h.tensor(X.values, "float32"), 1, 0)
+        return c, True
+    c = svm_csr(int(X.n), int(X.d), h.np(X.indptr, np.int64), h.np(X.indices, np.int32),
+                None if X.values is None else h.np(X.values, np.float32), 0, 0)
+    return c, False
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ct.c_void_p(stream.cuda_stream)
+    return ct.c_void_p(int(stream))
+
+
+def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int = 0,
+              precision: int = SVM_FP64, shrink: tuple | None = None, stream=None,
+              trace_len: int = 0, alpha_out=None, flags: int = 0, ctas: int = 0,
+              check: bool = True) -> dict:
+    """Train by SMO. ``shrink`` = (kind, value, recon[, first_factor]) or None.
+    X is a host CSR (numpy arrays) or a DeviceCSR; y matches X's memory space.
+    Returns dict(status, alpha, b, iters, stats, trace)."""
+    lib = load()
+    h = _Hold()
+    cx, dev = _csr(h, X)
+    n = int(X.n)
+    if dev:
+        import torch
+        yp = h.tensor(y, "int8")
+        if alpha_out is None:
+            alpha_out = torch.empty(n, dtype=torch.float64, device=X.indptr.device)
+        ap = alpha_out.data_ptr()
+    else:
+        yp = h.np(y, np.int8)
+        if alpha_out is None:
+            alpha_out = np.zeros(n)
+        ap = alpha_out.ctypes.data
+    trace = np.full((max(trace_len, 0), 2), -1, dtype=np.int32)
+    p = svm_params(float(C), float(gamma), float(tau), int(max_iter), int(precision), 0,
+                   _stream_ptr(stream), trace.ctypes.data if trace_len else None, int(trace_len),
+                   int(flags), int(ctas))
+    pol = None
+    if shrink is not None:
+        kind, value, recon = shrink[:3]
+        ff = shrink[3] if len(shrink) > 3 else 20.0
+        pol = svm_shrink_policy(int(kind), int(recon), float(value), float(ff))
+    b = ct.c_double(0.0)
+    it = ct.c_int64(0)
+    st = svm_stats()
+    rc = lib.svm_train(ct.byref(cx), yp, ct.byref(p), ct.byref(pol) if pol is not None else None,
+                       ap, ct.byref(b), ct.byref(it), ct.byref(st))
+    if check and rc < 0:
+        raise SvmError(rc, svm_last_error())
+    out = {"status": rc, "alpha": alpha_out, "b": b.value, "iters": it.value, "stats": st.as_dict()}
+    if trace_len:
+        out["trace"] = trace[: min(trace_len, it.value)]
+    return out
+
+
+def svm_decision(X, y, alpha, b: float, gamma: float, Z, *, precision: int = SVM_FP64,
+                 stream=None, out=None, check: bool = True):
+    """Eq. (classi) before the sign for the rows of Z."""
+    lib = load()
+    h = _Hold()
+    cx, devx = _csr(h, X)
+    cz, devz = _csr(h, Z)
+    if devx:
+        yp = h.tensor(y, "int8")
+        ap = h.tensor(alpha, "float64")
+    else:
+        yp = h.np(y, np.int8)
+        ap = h.np(alpha, np.float64)
+    m = int(Z.n)
+    if devz:
+        import torch
+        if out is None:
+            out = torch.empty(m, dtype=torch.float64, device=Z.indptr.device)
+        op = out.data_ptr()
+    else:
+        if out is None:
+            out = np.zeros(m)
+        op = out.ctypes.data
+    rc = lib.svm_decision(ct.byref(cx), yp, ap, float(b), float(gamma), ct.byref(cz),
+                          int(precision), _stream_ptr(stream), op)
+    if check and rc < 0:
+        raise SvmError(rc, svm_last_error())
+    return out

@@ -1,0 +1,854 @@
+// Fused, persistent SMO step for sm_103a (kernel template; instantiated per
+// row-pass arithmetic in smo_step_{binary,fp64,mixed}.cu).
+//
+// One cooperative launch runs many SMO iterations (Algorithm 1 / the loop of
+// Algorithm 3 and, with shrinking, Algorithm 4) without returning to the
+// host. Each CTA owns a contiguous segment of the samples (the sample
+// partitioning of Algorithm 3, one segment per SM instead of one per MPI
+// rank) and its active list pi_q (Algorithm 4). When the segment fits, its
+// rows, f, alpha and index sets stay in shared memory for the whole launch
+// ("resident" mode); otherwise they are streamed from global memory.
+//
+// One iteration:
+//   1. every CTA loads x_up and x_low into a dense shared-memory target
+//      buffer (the paper's MPI_Bcast of the two rows becomes two L2 reads);
+//   2. every CTA computes K(up, low) from that buffer and the pair step of
+//      Eq. (alphaup) with rho = -eta (Eq. rho) in FP64, identically, so no
+//      exchange is needed;
+//   3. the row pass: for each active sample i of the segment, the kernel
+//      values K(up, i), K(low, i) (RBF via ||x||^2 + ||z||^2 - 2<x,z>), the
+//      FP64 gradient update of Eq. (fup), on shrink iterations the rule of
+//      Eq. (shrink), and the CTA's best I_up / I_low candidates;
+//   4. a grid-wide exchange of the CTA candidates (the paper's
+//      MPI_Allreduce "GlobalMinMax") through release/acquire flags in global
+//      memory; every CTA reduces the candidates in the same order and gets
+//      the same next pair (Eq. bminmax, lowest index on ties);
+//   5. on shrink iterations each CTA compacts its active list in place.
+//
+// All waits on other CTAs are bounded by a time limit; on expiry the kernel
+// records an error and returns so the host can report SVM_ERR_TIMEOUT.
+#pragma once
+
+#include <climits>
+#include <cuda_runtime.h>
+
+#include "svm_internal.cuh"
+
+namespace svmgb {
+namespace smo {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// named barrier 1 between the pair-step warp (arrives) and the row warps (wait)
+__device__ __forceinline__ void step_bar_arrive(int n) { asm volatile("bar.arrive 1, %0;" ::"r"(n) : "memory"); }
+__device__ __forceinline__ void step_bar_sync(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// status byte: bits 0-2 = index set (Eq. setinfo), bit 7 = label is +1
+__device__ __forceinline__ uint8_t set_bits(uint8_t b) { return b & 7; }
+__device__ __forceinline__ int8_t y_of(uint8_t b) { return (b & 0x80) ? 1 : -1; }
+// One side (I_up or I_low) of a candidate: the sample and what the pair
+// step needs about it, so that no CTA has to read another CTA's data.
+struct Side {
+    double f;       // gradient value
+    double a;       // alpha
+    double nrm;     // ||x||^2 (unused on binary input)
+    int64_t p0;     // global CSR start of the row
+    int32_t i;      // global sample index (INT_MAX when empty)
+    int32_t len;    // CSR length of the row
+    int32_t y;
+    int32_t pad;
+};
+
+struct __align__(16) CandFull {
+    Side up, low;
+    int32_t count;
+    int32_t pad[3];
+};
+static_assert(sizeof(CandFull) % 16 == 0, "candidate slots are read with vector loads");
+
+// FP64 compares and selects are long-latency on sm_103a; comparisons here
+// use an order-preserving integer image of the double instead:
+// dkey(a) < dkey(b) exactly when a < b (finite values, -0 taken as +0).
+__device__ __forceinline__ unsigned long long dkey(double f)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(f);
+    if ((b << 1) == 0) b = 0;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ bool dless(double a, double b) { return dkey(a) < dkey(b); }
+__device__ __forceinline__ double neg_if(double v, bool neg)
+{
+    return neg ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull) : v;
+}
+// index set of a snapped alpha (exactly 0, exactly C, or in between)
+__device__ __forceinline__ uint8_t status_of(bool ypos, double a, double C)
+{
+    const long long b = __double_as_longlong(a);
+    uint8_t set;
+    if (b == 0) set = ypos ? ST_I1 : ST_I4;
+    else if (b == __double_as_longlong(C)) set = ypos ? ST_I3 : ST_I2;
+    else set = ST_I0;
+    return (uint8_t)(set | (ypos ? 0x80 : 0));
+}
+
+// Selection keys: the I_up side minimises f, the I_low side maximises it;
+// both become a minimum over (key, index), so ties go to the lowest index.
+__device__ __forceinline__ unsigned long long key_up(double f) { return dkey(f); }
+__device__ __forceinline__ unsigned long long key_low(double f) { return ~dkey(f); }
+constexpr unsigned long long kNoKey = ~0ull;
+
+__device__ __forceinline__ bool ki_less(unsigned long long k, int i, unsigned long long bk, int bi)
+{
+    return k < bk || (k == bk && i < bi);
+}
+
+// Warp minimum of (key, index); every lane ends with the winner.
+__device__ __forceinline__ void warp_min_ki(unsigned long long &k, int &i)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        unsigned long long ko = __shfl_xor_sync(0xffffffffu, k, off);
+        int io = __shfl_xor_sync(0xffffffffu, i, off);
+        if (ki_less(ko, io, k, i)) {
+            k = ko;
+            i = io;
+        }
+    }
+}
+
+__device__ __forceinline__ void side_empty(Side &s, bool up)
+{
+    s.f = up ? __longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0xfff0000000000000ll);
+    s.a = 0.0;
+    s.nrm = 0.0;
+    s.p0 = 0;
+    s.i = INT_MAX;
+    s.len = 0;
+    s.y = 0;
+    s.pad = 0;
+}
+
+// Block-wide exclusive scan of 0/1 flags; returns the prefix, total in *tot.
+__device__ __forceinline__ int block_scan_flag(bool flag, int *warp_sums, int *tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned m = __ballot_sync(0xffffffffu, flag);
+    int pre = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) warp_sums[w] = __popc(m);
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < kWarps ? warp_sums[lane] : 0;
+        int incl = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane < kWarps) warp_sums[lane] = incl - v;
+        if (lane == 31) *tot = incl;
+    }
+    __syncthreads();
+    return pre + warp_sums[w];
+}
+
+template <int MODE>
+struct RowMath;
+template <>
+struct RowMath<MODE_BINARY> {
+    using Acc = int;
+    using Tgt = unsigned short;  // byte 0: column of x_up set, byte 1: of x_low
+    using Nrm = float;           // unused
+};
+template <>
+struct RowMath<MODE_FP64> {
+    using Acc = double;
+    using Tgt = double2;         // .x value of x_up, .y value of x_low
+    using Nrm = double;
+};
+template <>
+struct RowMath<MODE_MIXED> {
+    using Acc = float;
+    using Tgt = float2;
+    using Nrm = float;
+};
+
+struct Shared {
+    Side wup[kWarps], wlow[kWarps];           // per-warp winners of the row pass
+    unsigned long long wkup[kWarps], wklow[kWarps];
+    int wiup[kWarps], wilow[kWarps];
+    Side rup[8], rlow[8];                     // per-warp winners of the exchange
+    unsigned long long rkup[8], rklow[8];
+    int riup[8], rilow[8];
+    long long rcount[8];
+    int scan[kWarps];
+    int scan_tot;
+    double du, dl;        // y_up * delta alpha_up, y_low * delta alpha_low
+    double au_new, al_new;
+    unsigned char st_u, st_l;
+    int flag_timeout;
+};
+
+template <int MODE>
+__device__ __forceinline__ void tgt_clear(typename RowMath<MODE>::Tgt &t)
+{
+    if constexpr (MODE == MODE_BINARY) t = 0;
+    else if constexpr (MODE == MODE_FP64) t = make_double2(0.0, 0.0);
+    else t = make_float2(0.f, 0.f);
+}
+
+template <int MODE, int LPR, bool RES>
+__global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
+{
+    using Tgt = typename RowMath<MODE>::Tgt;
+    using Acc = typename RowMath<MODE>::Acc;
+    using Nrm = typename RowMath<MODE>::Nrm;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ Shared sh;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = A.G, cta = blockIdx.x;
+    const int d = A.d;
+    const SmoLayout L = smo_layout(MODE, d, A.ktab_len, A.maxnnz, RES ? 1 : 0, A.seg_rows_max,
+                                   A.seg_nnz_max);
+    Tgt *tbuf = reinterpret_cast<Tgt *>(dsm + L.tgt);            // [2][d]
+    int *tcol = reinterpret_cast<int *>(dsm + L.tcol);           // [2 buf][2 side][maxnnz]
+    double *ktab = reinterpret_cast<double *>(dsm + L.ktab);
+    double *f_s = reinterpret_cast<double *>(dsm + L.f);
+    double *a_s = reinterpret_cast<double *>(dsm + L.alpha);
+    Nrm *nrm_s = reinterpret_cast<Nrm *>(dsm + L.nrm);
+    int *rp_s = reinterpret_cast<int *>(dsm + L.rowptr);
+    int *act_s = reinterpret_cast<int *>(dsm + L.act);
+    uint8_t *st_s = reinterpret_cast<uint8_t *>(dsm + L.st);
+    unsigned short *col_s = reinterpret_cast<unsigned short *>(dsm + L.col);
+    float *val_s = reinterpret_cast<float *>(dsm + L.val);
+    const int maxnnz = A.maxnnz > 0 ? A.maxnnz : 1;
+
+    const int64_t lo = seg_lo(A.n, G, cta);
+    const int nseg = (int)(seg_lo(A.n, G, cta + 1) - lo);
+    const int64_t base = A.indptr[lo];   // global CSR offset of the segment
+
+    // ---- set-up
+    for (int c = tid; c < 2 * d; c += kThreads) tgt_clear<MODE>(tbuf[c]);
+    if constexpr (MODE == MODE_BINARY) {
+        for (int c = tid; c < 2 * A.ktab_len; c += kThreads) ktab[c] = A.ktab[c];
+    }
+    const double *rtab = ktab + A.ktab_len;
+    int cnt = A.seg_cnt[cta];
+    if constexpr (RES) {
+        for (int r = tid; r < nseg; r += kThreads) {
+            f_s[r] = A.f[lo + r];
+            a_s[r] = A.alpha[lo + r];
+            st_s[r] = A.status[lo + r];
+            rp_s[r] = (int)(A.indptr[lo + r] - base);
+            if constexpr (MODE == MODE_FP64) nrm_s[r] = A.norm[lo + r];
+            if constexpr (MODE == MODE_MIXED) nrm_s[r] = A.normf[lo + r];
+        }
+        if (tid == 0) rp_s[nseg] = (int)(A.indptr[lo + nseg] - base);
+        const int64_t segnnz = A.indptr[lo + nseg] - base;
+        for (int64_t p = tid; p < segnnz; p += kThreads) {
+            col_s[p] = (unsigned short)A.indices[base + p];
+            if constexpr (MODE == MODE_FP64) val_s[p] = A.values[base + p];
+            if constexpr (MODE == MODE_MIXED) val_s[p] = A.vmix[base + p];
+        }
+        for (int k = tid; k < cnt; k += kThreads) act_s[k] = A.act[lo + k];
+    }
+    SmoCtrl C0 = *A.ctrl;
+    int64_t iter = C0.iter, counter = C0.counter, row_visits = C0.row_visits;
+    int64_t shrink_events = C0.shrink_events;
+    long long total = C0.active;
+    int64_t ph[6] = {0, 0, 0, 0, 0, 0};
+    if (tid == 0) sh.flag_timeout = 0;
+    Side up, low;
+    side_empty(up, true);
+    side_empty(low, false);
+    bool first = A.select_only != 0;
+    if (!first) {
+        up.f = C0.b_up; up.a = C0.a_up; up.i = C0.i_up;
+        low.f = C0.b_low; low.a = C0.a_low; low.i = C0.i_low;
+        if (up.i >= 0 && up.i < A.n) {
+            up.p0 = A.indptr[up.i];
+            up.len = (int)(A.indptr[up.i + 1] - up.p0);
+            up.y = A.y[up.i];
+            up.nrm = MODE == MODE_MIXED ? (double)A.normf[up.i] : (MODE == MODE_FP64 ? A.norm[up.i] : 0.0);
+        }
+        if (low.i >= 0 && low.i < A.n) {
+            low.p0 = A.indptr[low.i];
+            low.len = (int)(A.indptr[low.i + 1] - low.p0);
+            low.y = A.y[low.i];
+            low.nrm = MODE == MODE_MIXED ? (double)A.normf[low.i] : (MODE == MODE_FP64 ? A.norm[low.i] : 0.0);
+        }
+    }
+    __syncthreads();
+
+    // ---- accessors (segment-local row r, global sample lo + r)
+    auto ACT = [&](int k) -> int {
+        if constexpr (RES) return act_s[k];
+        else return A.act[lo + k];
+    };
+    auto SET_ACT = [&](int k, int v) {
+        if constexpr (RES) act_s[k] = v;
+        else A.act[lo + k] = v;
+    };
+    auto ROWP = [&](int r, int64_t &p0, int64_t &p1) {
+        if constexpr (RES) { p0 = rp_s[r]; p1 = rp_s[r + 1]; }
+        else { p0 = A.indptr[lo + r]; p1 = A.indptr[lo + r + 1]; }
+    };
+    auto COL = [&](int64_t p) -> int {
+        if constexpr (RES) return (int)col_s[p];
+        else return A.indices[p];
+    };
+    auto VAL = [&](int64_t p) -> float {
+        if constexpr (RES) return val_s[p];
+        else if constexpr (MODE == MODE_FP64) return A.values[p];
+        else return A.vmix[p];
+    };
+    auto GETF = [&](int r) -> double {
+        if constexpr (RES) return f_s[r];
+        else return A.f[lo + r];
+    };
+    auto PUTF = [&](int r, double v) {
+        if constexpr (RES) f_s[r] = v;
+        else A.f[lo + r] = v;
+    };
+    auto GETST = [&](int r) -> uint8_t {
+        if constexpr (RES) return st_s[r];
+        else return A.status[lo + r];
+    };
+    auto PUTST = [&](int r, uint8_t v) {
+        if constexpr (RES) st_s[r] = v;
+        else A.status[lo + r] = v;
+    };
+    auto GETA = [&](int r) -> double {
+        if constexpr (RES) return a_s[r];
+        else return A.alpha[lo + r];
+    };
+    auto PUTA = [&](int r, double v) {
+        if constexpr (RES) a_s[r] = v;
+        else A.alpha[lo + r] = v;
+    };
+    auto NRM = [&](int r) -> double {
+        if constexpr (MODE == MODE_BINARY) return 0.0;
+        else if constexpr (RES) return (double)nrm_s[r];
+        else if constexpr (MODE == MODE_FP64) return A.norm[lo + r];
+        else return (double)A.normf[lo + r];
+    };
+
+    const double C = A.C;
+    const double snap = 1e-12 * C, c_snap = C - snap;
+    const float gammaf = (float)A.gamma;
+    unsigned epoch = 0;
+    int exit_reason = 0;
+    int prev_valid = 0;              // buffer (1 - buf) holds the previous targets
+    int prev_len_u = 0, prev_len_l = 0;
+    // optional per-phase cycle counts of CTA 0 (one clock read per phase)
+    const bool timed = A.phase_times && cta == 0;
+    uint64_t tp = (timed && tid == 0) ? clock64() : 0;
+    // with phase_times every CTA counts the cycles from step start to publish
+    const bool busy_on = A.phase_times && A.cta_cycles;
+    uint64_t cta_t0 = 0, busy = 0;
+
+    for (;;) {
+        const int buf = (int)(iter & 1);
+        Tgt *T = tbuf + (size_t)buf * d;
+        int *tcu = tcol + (size_t)(buf * 2 + 0) * maxnnz;
+        int *tcl = tcol + (size_t)(buf * 2 + 1) * maxnnz;
+        bool shrink_now = false;
+        const double bup_sel = up.f, blow_sel = low.f;   // values that chose this pair
+        if (busy_on && tid == 0) cta_t0 = clock64();
+        if (!first) {
+            if (!dless(A.thr, low.f - up.f)) { exit_reason = 0; break; }
+            if (iter >= A.iter_limit) { exit_reason = 1; break; }
+            // ---- 1. targets: x_up into .x / byte 0, x_low into .y / byte 1
+            for (int k = tid; k < up.len; k += kThreads) {
+                int c = A.indices[up.p0 + k];
+                tcu[k] = c;
+                if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
+                else if constexpr (MODE == MODE_FP64) T[c].x = (double)A.values[up.p0 + k];
+                else T[c].x = A.vmix[up.p0 + k];
+            }
+            for (int k = tid; k < low.len; k += kThreads) {
+                int c = A.indices[low.p0 + k];
+                tcl[k] = c;
+                if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
+                else if constexpr (MODE == MODE_FP64) T[c].y = (double)A.values[low.p0 + k];
+                else T[c].y = A.vmix[low.p0 + k];
+            }
+            if (A.h > 0) {
+                counter -= 1;
+                shrink_now = counter <= 0;
+            }
+            row_visits += total;
+            __syncthreads();
+            if (timed && tid == 0) { uint64_t t = clock64(); ph[0] += t - tp; tp = t; }
+        }
+
+        // ---- 2. the pair step (warp 0) runs while warps 1.. compute the
+        //         row sums and kernel values; the f updates wait for it on a
+        //         named barrier.
+        unsigned long long bku = kNoKey, bkl = kNoKey;   // this thread's best keys
+        int biu = INT_MAX, bil = INT_MAX;                // ... their sample indices
+        int bru = 0, brl = 0;                            // ... and segment rows
+        if (warp == 0) {
+            if (!first) {
+                Acc s = 0;
+                for (int k = lane; k < low.len; k += 32) {
+                    const Tgt t = T[tcl[k]];
+                    if constexpr (MODE == MODE_BINARY) s += (int)(t & 1);
+                    else if constexpr (MODE == MODE_FP64) s = fma(t.y, t.x, s);
+                    else s = fmaf(t.y, t.x, s);
+                }
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                if (lane == 0) {
+                    double kul, rinv = 0.0;
+                    if constexpr (MODE == MODE_BINARY) {
+                        int dist = up.len + low.len - 2 * s;
+                        dist = dist < 0 ? 0 : dist;
+                        kul = ktab[dist];
+                        rinv = rtab[dist];
+                    } else if constexpr (MODE == MODE_FP64) {
+                        double d2 = up.nrm + low.nrm - 2.0 * s;
+                        kul = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                    } else {
+                        float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
+                        kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
+                    }
+                    // Eq. (alphaup) with rho = -eta (Eq. rho), K(x,x) = 1,
+                    // clipped to the feasible segment [L, H]; end-point rule
+                    // for a flat curvature. The FP64 arithmetic is the
+                    // oracle's operation for operation; comparisons, clamps
+                    // and multiplications by y = +-1 are done on the bit
+                    // patterns (exact, and short-latency on this part).
+                    const bool yu_neg = up.y < 0, yl_neg = low.y < 0;
+                    const double au = up.a, al = low.a;
+                    const double eta = 2.0 - 2.0 * kul;
+                    const bool opposite = yu_neg != yl_neg;
+                    double Lo, Hi;
+                    if (opposite) {
+                        const double x = al - au;
+                        Lo = dless(x, 0.0) ? 0.0 : x;
+                        const double h = C + al - au;
+                        Hi = dless(h, C) ? h : C;
+                    } else {
+                        const double x = al + au - C;
+                        Lo = dless(x, 0.0) ? 0.0 : x;
+                        const double h = al + au;
+                        Hi = dless(h, C) ? h : C;
+                    }
+                    const double slope = neg_if(up.f - low.f, yl_neg);
+                    double aln;
+                    if (dless(1e-12, eta)) {
+                        double q;
+                        if constexpr (MODE == MODE_BINARY) {
+                            // slope / eta from the correctly rounded 1/eta of
+                            // the table: one Markstein correction gives the
+                            // correctly rounded quotient
+                            const double q0 = slope * rinv;
+                            const double r = fma(-eta, q0, slope);
+                            q = fma(r, rinv, q0);
+                        } else {
+                            q = slope / eta;
+                        }
+                        const double t = al + q;
+                        aln = dless(t, Lo) ? Lo : (dless(Hi, t) ? Hi : t);
+                    } else {
+                        aln = dless(0.0, slope) ? Hi : Lo;
+                    }
+                    double aun = au + neg_if(al - aln, opposite);
+                    if (dless(aln, snap)) aln = 0.0;
+                    if (dless(c_snap, aln)) aln = C;
+                    if (dless(aun, snap)) aun = 0.0;
+                    if (dless(c_snap, aun)) aun = C;
+                    sh.du = neg_if(aun - au, yu_neg);
+                    sh.dl = neg_if(aln - al, yl_neg);
+                    sh.au_new = aun;
+                    sh.al_new = aln;
+                    sh.st_u = status_of(!yu_neg, aun, C);
+                    sh.st_l = status_of(!yl_neg, aln, C);
+                }
+                __syncwarp();
+                step_bar_arrive(kThreads);
+                if (timed && tid == 0) { uint64_t t = clock64(); ph[1] += t - tp; tp = t; }
+            }
+        } else {
+            // ---- 3. row pass over the segment's active list (warps 1..)
+            constexpr int RPW = 32 / LPR;
+            constexpr int kRowWarps = kWarps - 1;
+            const int gl = lane & (LPR - 1);
+            const int gw = lane / LPR;
+            double du = 0.0, dl = 0.0, au_new = 0.0, al_new = 0.0;
+            unsigned char st_u = 0, st_l = 0;
+            bool have_step = first;
+            for (int kb = (warp - 1) * RPW;; kb += kRowWarps * RPW) {
+                const bool round0 = kb == (warp - 1) * RPW;
+                if (!round0 && kb >= cnt) break;
+                const int k = kb + gw;
+                const bool valid = k < cnt;
+                int r = 0;
+                int64_t p0 = 0, p1 = 0;
+                double fi = 0.0;
+                uint8_t sb = 0;
+                if (valid) {
+                    r = ACT(k);
+                    ROWP(r, p0, p1);
+                    if (gl == 0) {
+                        fi = GETF(r);
+                        sb = GETST(r);
+                    }
+                }
+                Acc su = 0, sl = 0;
+                if (!first) {
+                    for (int64_t p = p0 + gl; p < p1; p += LPR) {
+                        const int c = COL(p);
+                        if constexpr (MODE == MODE_BINARY) {
+                            unsigned short t = T[c];
+                            su += (int)(t & 0xff);
+                            sl += (int)(t >> 8);
+                        } else if constexpr (MODE == MODE_FP64) {
+                            double v = (double)VAL(p);
+                            double2 t = T[c];
+                            su = fma(v, t.x, su);
+                            sl = fma(v, t.y, sl);
+                        } else {
+                            float v = VAL(p);
+                            float2 t = T[c];
+                            su = fmaf(v, t.x, su);
+                            sl = fmaf(v, t.y, sl);
+                        }
+                    }
+#pragma unroll
+                    for (int off = LPR / 2; off >= 1; off >>= 1) {
+                        su += __shfl_xor_sync(0xffffffffu, su, off);
+                        sl += __shfl_xor_sync(0xffffffffu, sl, off);
+                    }
+                }
+                double ku = 0.0, kl = 0.0;
+                if (!first && valid && gl == 0) {
+                    const int len = (int)(p1 - p0);
+                    if constexpr (MODE == MODE_BINARY) {
+                        int du2 = up.len + len - 2 * su, dl2 = low.len + len - 2 * sl;
+                        ku = ktab[du2 < 0 ? 0 : du2];
+                        kl = ktab[dl2 < 0 ? 0 : dl2];
+                    } else if constexpr (MODE == MODE_FP64) {
+                        const double nrm_i = NRM(r);
+                        double d2u = up.nrm + nrm_i - 2.0 * su;
+                        double d2l = low.nrm + nrm_i - 2.0 * sl;
+                        ku = exp(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
+                        kl = exp(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
+                    } else {
+                        const float nf = (float)NRM(r);
+                        float d2u = (float)up.nrm + nf - 2.0f * su;
+                        float d2l = (float)low.nrm + nf - 2.0f * sl;
+                        ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
+                        kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
+                    }
+                }
+                if (!have_step) {
+                    step_bar_sync(kThreads);
+                    du = sh.du; dl = sh.dl;
+                    st_u = sh.st_u; st_l = sh.st_l;
+                    au_new = sh.au_new; al_new = sh.al_new;
+                    have_step = true;
+                }
+                if (valid && gl == 0) {
+                    const int i = (int)(lo + r);
+                    if (!first) {
+                        // Eq. (fup), FP64 accumulation
+                        fi = fma(dl, kl, fma(du, ku, fi));
+                        PUTF(r, fi);
+                        if (i == up.i) {
+                            sb = st_u;
+                            PUTST(r, sb);
+                            PUTA(r, au_new);
+                        } else if (i == low.i) {
+                            sb = st_l;
+                            PUTST(r, sb);
+                            PUTA(r, al_new);
+                        }
+                    }
+                    const uint8_t set = set_bits(sb);
+                    bool keep = true;
+                    if (shrink_now) {
+                        // Eq. (shrink), with the thresholds that chose this pair
+                        keep = !(((set == ST_I3 || set == ST_I4) && dless(fi, bup_sel)) ||
+                                 ((set == ST_I1 || set == ST_I2) && dless(blow_sel, fi)));
+                        if (!keep) SET_ACT(k, ~r);
+                    }
+                    if (keep) {
+                        const unsigned long long kup = key_up(fi), klo = key_low(fi);
+                        if (st_up(set) && ki_less(kup, i, bku, biu)) { bku = kup; biu = i; bru = r; }
+                        if (st_low(set) && ki_less(klo, i, bkl, bil)) { bkl = klo; bil = i; brl = r; }
+                    }
+                }
+            }
+        }
+        // payload of a segment row for the exchange (read after this
+        // thread's own updates of f, alpha and the index set)
+        auto make_side = [&](int r) {
+            Side sd;
+            int64_t p0, p1;
+            ROWP(r, p0, p1);
+            const uint8_t sb = GETST(r);
+            sd.f = GETF(r);
+            sd.a = GETA(r);
+            sd.nrm = NRM(r);
+            sd.p0 = RES ? base + p0 : p0;
+            sd.i = (int)(lo + r);
+            sd.len = (int)(p1 - p0);
+            sd.y = y_of(sb);
+            sd.pad = 0;
+            return sd;
+        };
+        // ---- CTA reduction: warp minima of (key, index); winners' payloads
+        {
+            unsigned long long k1 = bku, k2 = bkl;
+            int i1 = biu, i2 = bil;
+            warp_min_ki(k1, i1);
+            warp_min_ki(k2, i2);
+            if (lane == 0) {
+                sh.wkup[warp] = k1; sh.wiup[warp] = i1;
+                sh.wklow[warp] = k2; sh.wilow[warp] = i2;
+            }
+            if (i1 != INT_MAX && biu == i1) sh.wup[warp] = make_side(bru);
+            if (i2 != INT_MAX && bil == i2) sh.wlow[warp] = make_side(brl);
+        }
+        __syncthreads();
+        // ---- 5. compaction of the active list on shrink steps
+        if (shrink_now) {
+            int kept = 0;
+            for (int b0 = 0; b0 < cnt; b0 += kThreads) {
+                int k = b0 + tid;
+                int v = k < cnt ? ACT(k) : -1;
+                bool keepv = v >= 0;
+                int pos = block_scan_flag(keepv, sh.scan, &sh.scan_tot);
+                int tot = sh.scan_tot;
+                if (keepv) SET_ACT(kept + pos, v);
+                kept += tot;
+                __syncthreads();
+            }
+            cnt = kept;
+        }
+        if (timed && tid == 0) { uint64_t t = clock64(); ph[2] += t - tp; tp = t; }
+        // ---- 4. grid-wide exchange (release/acquire flags, bounded waits)
+        ++epoch;
+        const int par = (int)(epoch & 1);
+        if (warp == 0) {
+            unsigned long long k1 = lane < kWarps ? sh.wkup[lane] : kNoKey;
+            unsigned long long k2 = lane < kWarps ? sh.wklow[lane] : kNoKey;
+            int i1 = lane < kWarps ? sh.wiup[lane] : INT_MAX;
+            int i2 = lane < kWarps ? sh.wilow[lane] : INT_MAX;
+            const unsigned long long k1s = k1, k2s = k2;
+            const int i1s = i1, i2s = i2;
+            warp_min_ki(k1, i1);
+            warp_min_ki(k2, i2);
+            const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
+            const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
+            if (lane == 0) {
+                Side a, b;
+                if (mu) a = sh.wup[__ffs(mu) - 1]; else side_empty(a, true);
+                if (ml) b = sh.wlow[__ffs(ml) - 1]; else side_empty(b, false);
+                CandFull *slot = reinterpret_cast<CandFull *>(A.cand) + (size_t)par * G + cta;
+                slot->up = a;
+                slot->low = b;
+                slot->count = cnt;
+                if (busy_on) busy += clock64() - cta_t0;
+                st_release_u32(A.seq + (size_t)par * G + cta, epoch);
+                if (timed) { uint64_t t = clock64(); ph[3] += t - tp; tp = t; }
+            }
+        }
+        // the previous step's target rows are cleared while others wait
+        if (prev_valid && warp >= 8) {
+            Tgt *P = tbuf + (size_t)(1 - buf) * d;
+            const int *pcu = tcol + (size_t)((1 - buf) * 2 + 0) * maxnnz;
+            const int *pcl = tcol + (size_t)((1 - buf) * 2 + 1) * maxnnz;
+            for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) tgt_clear<MODE>(P[pcu[k]]);
+            for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) tgt_clear<MODE>(P[pcl[k]]);
+        }
+        const int rwarps = (G + 31) / 32;
+        if (warp < rwarps) {
+            const int c = warp * 32 + lane;
+            Side a, b;
+            side_empty(a, true);
+            side_empty(b, false);
+            long long cc = 0;
+            int timed_out = 0;
+            if (c < G) {
+                const unsigned *sp = A.seq + (size_t)par * G + c;
+                uint64_t t0 = 0;
+                int spins = 0;
+                while (ld_relaxed_u32(sp) < epoch) {
+                    if (++spins >= 256) {
+                        spins = 0;
+                        uint64_t now = global_ns();
+                        if (t0 == 0) t0 = now;
+                        else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
+                        if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+                    }
+                }
+                if (!timed_out) {
+                    fence_acq_rel_gpu();   // acquire: the slot written before the flag
+
+                    // L2 reads (bypass L1, which is not coherent across SMs)
+                    union {
+                        CandFull c;
+                        int4 v[sizeof(CandFull) / 16];
+                    } u;
+                    const int4 *q = reinterpret_cast<const int4 *>(
+                        reinterpret_cast<const CandFull *>(A.cand) + (size_t)par * G + c);
+#pragma unroll
+                    for (int j = 0; j < (int)(sizeof(CandFull) / 16); ++j) u.v[j] = __ldcg(q + j);
+                    a = u.c.up;
+                    b = u.c.low;
+                    cc = u.c.count;
+                }
+            }
+            if (__any_sync(0xffffffffu, timed_out)) {
+                if (lane == 0) {
+                    atomicExch(&A.ctrl->err, 1);
+                    sh.flag_timeout = 1;
+                }
+            }
+            unsigned long long k1 = a.i == INT_MAX ? kNoKey : key_up(a.f);
+            unsigned long long k2 = b.i == INT_MAX ? kNoKey : key_low(b.f);
+            int i1 = a.i, i2 = b.i;
+            warp_min_ki(k1, i1);
+            warp_min_ki(k2, i2);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
+            if (lane == 0) {
+                sh.rkup[warp] = k1; sh.riup[warp] = i1;
+                sh.rklow[warp] = k2; sh.rilow[warp] = i2;
+                sh.rcount[warp] = cc;
+            }
+            if (i1 != INT_MAX && a.i == i1) sh.rup[warp] = a;
+            if (i2 != INT_MAX && b.i == i2) sh.rlow[warp] = b;
+        }
+        __syncthreads();
+        if (timed && tid == 0) { uint64_t t = clock64(); ph[4] += t - tp; tp = t; }
+        if (sh.flag_timeout) break;
+        {
+            unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
+            int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0;
+            long long cc = sh.rcount[0];
+            for (int w = 1; w < rwarps; ++w) {
+                if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
+                if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
+                cc += sh.rcount[w];
+            }
+            prev_valid = first ? 0 : 1;
+            prev_len_u = up.len;
+            prev_len_l = low.len;
+            if (iu != INT_MAX) up = sh.rup[wu]; else side_empty(up, true);
+            if (il != INT_MAX) low = sh.rlow[wl]; else side_empty(low, false);
+            total = cc;
+        }
+        if (!first) {
+            ++iter;
+            if (shrink_now) {
+                counter = A.h < total ? A.h : total;
+                if (counter < 1) counter = 1;
+                ++shrink_events;
+            }
+        }
+        first = false;
+        if (cta == 0 && tid == 0 && iter < A.trace_len) {
+            A.trace[2 * iter] = up.i == INT_MAX ? -1 : up.i;
+            A.trace[2 * iter + 1] = low.i == INT_MAX ? -1 : low.i;
+        }
+        __syncthreads();   // every thread has read sh.* before it is reused
+        if (timed && tid == 0) { uint64_t t = clock64(); ph[5] += t - tp; tp = t; }
+    }
+
+    if constexpr (RES) {
+        for (int r = tid; r < nseg; r += kThreads) {
+            A.f[lo + r] = f_s[r];
+            A.alpha[lo + r] = a_s[r];
+            A.status[lo + r] = st_s[r];
+        }
+        for (int k = tid; k < cnt; k += kThreads) A.act[lo + k] = act_s[k];
+    }
+    if (tid == 0) A.seg_cnt[cta] = cnt;
+    if (busy_on && tid == 0) A.cta_cycles[cta] += (int64_t)busy;
+    if (cta == 0 && tid == 0) {
+        // field by field: ctrl->err may be set concurrently by another CTA
+        SmoCtrl *c = A.ctrl;
+        c->b_up = up.f;
+        c->b_low = low.f;
+        c->a_up = up.a;
+        c->a_low = low.a;
+        c->i_up = up.i == INT_MAX ? -1 : up.i;
+        c->i_low = low.i == INT_MAX ? -1 : low.i;
+        c->iter = iter;
+        c->counter = counter;
+        c->active = total;
+        c->row_visits = row_visits;
+        c->exit_reason = exit_reason;
+        c->shrink_events = shrink_events;
+        for (int k = 0; k < 6; ++k) c->phase_cycles[k] += ph[k];
+    }
+}
+
+template <int MODE, bool RES>
+void *kernel_for(int lpr)
+{
+    switch (lpr) {
+    case 1: return (void *)smo_persistent_kernel<MODE, 1, RES>;
+    case 2: return (void *)smo_persistent_kernel<MODE, 2, RES>;
+    case 4: return (void *)smo_persistent_kernel<MODE, 4, RES>;
+    case 8: return (void *)smo_persistent_kernel<MODE, 8, RES>;
+    case 16: return (void *)smo_persistent_kernel<MODE, 16, RES>;
+    case 32: return (void *)smo_persistent_kernel<MODE, 32, RES>;
+    default: return nullptr;
+    }
+}
+
+template <int MODE>
+cudaError_t launch_mode(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st)
+{
+    void *fn = a.resident ? kernel_for<MODE, true>(lpr) : kernel_for<MODE, false>(lpr);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1 || a.G > per_sm * sms || a.G > 256) return cudaErrorCooperativeLaunchTooLarge;
+    SmoArgs args = a;
+    void *params[] = {&args};
+    return cudaLaunchCooperativeKernel(fn, dim3(a.G), dim3(kThreads), params, smem, st);
+}
+
+}  // namespace smo
+}  // namespace svmgb

@@ -1,0 +1,904 @@
+// C ABI of the GB300 SVM library: ingest, the SMO driver (Algorithms 1, 4,
+// 5 and 6 of arXiv:1406.5161), the decision function and utilities.
+//
+// Host code here only orchestrates: every arithmetic step of training and
+// prediction runs in the library's CUDA kernels. The host reads a small
+// control block between phases (after each persistent launch) to apply the
+// phase logic of Algorithm 5.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "svm_internal.cuh"
+
+using namespace svmgb;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<long long> g_launches{0};
+
+void set_err(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+struct Fail {
+    int code;
+};
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                    __LINE__);                                                           \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? SVM_ERR_OOM : SVM_ERR_CUDA};   \
+        }                                                                                \
+    } while (0)
+
+#define ARG_FAIL(...)                 \
+    do {                              \
+        set_err(__VA_ARGS__);         \
+        throw Fail{SVM_ERR_ARG};      \
+    } while (0)
+
+// Stream-ordered device allocations released when the scope ends.
+struct Arena {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit Arena(cudaStream_t s) : st(s) {}
+    template <class T>
+    T *alloc(size_t count)
+    {
+        void *p = nullptr;
+        if (count == 0) count = 1;
+        CK(cudaMallocAsync(&p, count * sizeof(T), st));
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    ~Arena()
+    {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+        cudaStreamSynchronize(st);
+    }
+};
+
+// --------------------------------------------------------------- kernels
+
+struct IngestInfo {
+    int bad_indptr;
+    int bad_index;
+    int bad_y;
+    int nonfinite;
+    int not_binary;
+    int pad;
+    unsigned long long npos;
+    int maxnnz;
+    int pad2;
+};
+
+// Validates the CSR structure and labels; detects binary (all 1.0) values.
+__global__ void k_validate(int64_t n, int64_t d, const int64_t *indptr, const int32_t *indices,
+                           const float *values, const int8_t *y, IngestInfo *info)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t p0 = indptr[i], p1 = indptr[i + 1];
+    if (p1 < p0 || (i == 0 && p0 != 0)) {
+        atomicOr(&info->bad_indptr, 1);
+        return;
+    }
+    int prev = -1;
+    bool nb = false, nf = false, bi = false;
+    for (int64_t p = p0; p < p1; ++p) {
+        int c = indices[p];
+        if (c <= prev || c >= d) bi = true;
+        prev = c;
+        if (values) {
+            float v = values[p];
+            if (!isfinite(v)) nf = true;
+            if (v != 1.0f) nb = true;
+        }
+    }
+    if (bi) atomicOr(&info->bad_index, 1);
+    if (nf) atomicOr(&info->nonfinite, 1);
+    if (nb) atomicOr(&info->not_binary, 1);
+    atomicMax(&info->maxnnz, (int)(p1 - p0));
+    if (y) {
+        int8_t v = y[i];
+        if (v != 1 && v != -1) atomicOr(&info->bad_y, 1);
+        if (v == 1) atomicAdd(&info->npos, 1ull);
+    }
+}
+
+// ||x_i||^2 in FP64 (row order), and the BF16-rounded copy with its FP32 norm.
+__global__ void k_norms(int64_t n, const int64_t *indptr, const float *values, double *norm,
+                        float *vmix, float *normf)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t p0 = indptr[i], p1 = indptr[i + 1];
+    double s = 0.0;
+    float sf = 0.f;
+    for (int64_t p = p0; p < p1; ++p) {
+        float v = values ? values[p] : 1.0f;
+        s += (double)v * (double)v;
+        if (vmix) {
+            float r = __bfloat162float(__float2bfloat16_rn(v));
+            vmix[p] = r;
+            sf = fmaf(r, r, sf);
+        }
+    }
+    if (norm) norm[i] = s;
+    if (normf) normf[i] = sf;
+}
+
+// exp(-gamma * k) for the integer squared distances of binary rows, and
+// (second half) the correctly rounded reciprocal of eta = 2 - 2 exp(-gamma k)
+// used by the pair step (0 where eta <= 1e-12).
+__global__ void k_ktab(double gamma, int len, double *ktab)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < len) {
+        const double kv = exp(-gamma * (double)k);
+        const double eta = 2.0 - 2.0 * kv;
+        ktab[k] = kv;
+        ktab[len + k] = eta > 1e-12 ? 1.0 / eta : 0.0;
+    }
+}
+
+// alpha = 0, f = -y (Algorithm 1 initialisation), index sets from y.
+__global__ void k_init(int64_t n, const int8_t *y, double *alpha, double *f, uint8_t *status)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int8_t yi = y[i];
+    alpha[i] = 0.0;
+    f[i] = -(double)yi;
+    status[i] = (uint8_t)(st_of(yi, 0.0, 1.0) | (yi > 0 ? 0x80 : 0));
+}
+
+// Active lists back to all samples: segment s holds local indices 0..size-1.
+__global__ void k_reset_active(int64_t n, int G, int32_t *act, int32_t *seg_cnt)
+{
+    const int s = blockIdx.x;
+    const int64_t lo = seg_lo(n, G, s);
+    const int m = (int)(seg_lo(n, G, s + 1) - lo);
+    for (int r = threadIdx.x; r < m; r += blockDim.x) act[lo + r] = r;
+    if (threadIdx.x == 0) seg_cnt[s] = m;
+}
+
+// mark[i] = 1 for samples in an active list.
+__global__ void k_mark_active(int64_t n, int G, const int32_t *act, const int32_t *seg_cnt,
+                              uint8_t *mark)
+{
+    const int s = blockIdx.x;
+    const int64_t lo = seg_lo(n, G, s);
+    for (int k = threadIdx.x; k < seg_cnt[s]; k += blockDim.x) mark[lo + act[lo + k]] = 1;
+}
+
+// stored entries per segment
+__global__ void k_seg_nnz(int64_t n, int G, const int64_t *indptr, int64_t *out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < G) out[s] = indptr[seg_lo(n, G, s + 1)] - indptr[seg_lo(n, G, s)];
+}
+
+// ---- deterministic, order-preserving compaction by predicate
+enum { PRED_UNMARKED = 0, PRED_ALPHA_POS = 1 };
+constexpr int kChunk = 4096;
+constexpr int kCT = 256;
+
+__device__ __forceinline__ bool pred_at(int pred, int64_t i, const uint8_t *mark, const double *alpha)
+{
+    return pred == PRED_UNMARKED ? mark[i] == 0 : alpha[i] > 0.0;
+}
+
+__global__ void k_count(int pred, int64_t n, const uint8_t *mark, const double *alpha, int *counts)
+{
+    __shared__ int s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    int64_t b0 = (int64_t)blockIdx.x * kChunk;
+    int c = 0;
+    for (int64_t i = b0 + threadIdx.x; i < n && i < b0 + kChunk; i += kCT) c += pred_at(pred, i, mark, alpha);
+    atomicAdd(&s, c);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = s;
+}
+
+__global__ void k_scan(const int *counts, int nb, int *offsets, long long *total)
+{
+    if (threadIdx.x != 0) return;
+    long long acc = 0;
+    for (int b = 0; b < nb; ++b) {
+        offsets[b] = (int)acc;
+        acc += counts[b];
+    }
+    *total = acc;
+}
+
+__global__ void k_scatter(int pred, int64_t n, const uint8_t *mark, const double *alpha,
+                          const int8_t *y, const int *offsets, int32_t *list, double *coef)
+{
+    __shared__ int wsum[kCT / 32];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = offsets[blockIdx.x];
+    __syncthreads();
+    int64_t b0 = (int64_t)blockIdx.x * kChunk;
+    for (int64_t s0 = b0; s0 < n && s0 < b0 + kChunk; s0 += kCT) {
+        int64_t i = s0 + threadIdx.x;
+        bool p = i < n && i < b0 + kChunk && pred_at(pred, i, mark, alpha);
+        unsigned m = __ballot_sync(0xffffffffu, p);
+        if (lane == 0) wsum[w] = __popc(m);
+        __syncthreads();
+        int pre = __popc(m & ((1u << lane) - 1u));
+        for (int k = 0; k < w; ++k) pre += wsum[k];
+        int tot = 0;
+        for (int k = 0; k < kCT / 32; ++k) tot += wsum[k];
+        if (p) {
+            list[base + pre] = (int32_t)i;
+            if (coef) coef[base + pre] = alpha[i] * (double)y[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+}
+
+// ---- final reductions (fixed order): objective, threshold b, counts
+struct FinishPart {
+    double sum_a;        // sum alpha
+    double sum_ayfy;     // sum alpha_i y_i (f_i + y_i)
+    double sum_f0;       // sum f over I0
+    long long n0, nsv, nbound;
+};
+
+__global__ void k_finish_part(int64_t n, double C, const double *alpha, const double *f,
+                              const uint8_t *status, FinishPart *parts)
+{
+    __shared__ FinishPart sp[kCT];
+    int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    FinishPart p = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kCT) {
+        double a = alpha[i];
+        uint8_t sb = status[i];
+        double yi = (sb & 0x80) ? 1.0 : -1.0;
+        p.sum_a += a;
+        p.sum_ayfy += a * yi * (f[i] + yi);
+        if ((sb & 7) == ST_I0) {
+            p.sum_f0 += f[i];
+            p.n0 += 1;
+        }
+        if (a > 0.0) p.nsv += 1;
+        if (a == C) p.nbound += 1;
+    }
+    sp[threadIdx.x] = p;
+    __syncthreads();
+    for (int s = kCT / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            FinishPart &a = sp[threadIdx.x];
+            const FinishPart &b = sp[threadIdx.x + s];
+            a.sum_a += b.sum_a;
+            a.sum_ayfy += b.sum_ayfy;
+            a.sum_f0 += b.sum_f0;
+            a.n0 += b.n0;
+            a.nsv += b.nsv;
+            a.nbound += b.nbound;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[blockIdx.x] = sp[0];
+}
+
+__global__ void k_finish_total(const FinishPart *parts, int nb, FinishPart *out)
+{
+    if (threadIdx.x != 0) return;
+    FinishPart t = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b) {
+        t.sum_a += parts[b].sum_a;
+        t.sum_ayfy += parts[b].sum_ayfy;
+        t.sum_f0 += parts[b].sum_f0;
+        t.n0 += parts[b].n0;
+        t.nsv += parts[b].nsv;
+        t.nbound += parts[b].nbound;
+    }
+    *out = t;
+}
+
+// --------------------------------------------------------------- helpers
+
+int grid1(int64_t n, int t = 256) { return (int)((n + t - 1) / t); }
+
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+}
+
+// Device-resident copy of one CSR matrix (+ labels) with its derived data.
+struct DevCSR {
+    int64_t n = 0, d = 0, nnz = 0;
+    const int64_t *indptr = nullptr;
+    const int32_t *indices = nullptr;
+    const float *values = nullptr;   // NULL for binary input
+    const int8_t *y = nullptr;
+    double *norm = nullptr;
+    float *vmix = nullptr;
+    float *normf = nullptr;
+    bool binary = false;
+    int maxnnz = 0;
+    int64_t npos = 0;
+};
+
+void ingest(Arena &ar, const svm_csr *X, const int8_t *y, bool need_fp64, bool need_mixed,
+            cudaStream_t st, DevCSR &out, int *launches)
+{
+    if (!X) ARG_FAIL("matrix is NULL");
+    if (X->n < 1 || X->d < 1) ARG_FAIL("n and d must be >= 1 (n=%lld d=%lld)", (long long)X->n, (long long)X->d);
+    if (X->n >= (int64_t)INT32_MAX) ARG_FAIL("n must be < 2^31");
+    if (X->d >= (int64_t)INT32_MAX) ARG_FAIL("d must be < 2^31");
+    if (!X->indptr || (!X->indices && X->n > 0)) ARG_FAIL("indptr/indices must not be NULL");
+    out.n = X->n;
+    out.d = X->d;
+    int64_t nnz = 0;
+    if (X->on_device) {
+        CK(cudaMemcpyAsync(&nnz, X->indptr + X->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        nnz = X->indptr[X->n];
+    }
+    if (nnz < 0 || nnz >= ((int64_t)1 << 40)) ARG_FAIL("indptr[n] out of range");
+    out.nnz = nnz;
+    if (X->on_device) {
+        out.indptr = X->indptr;
+        out.indices = X->indices;
+        out.values = X->values;
+        out.y = y;
+    } else {
+        int64_t *ip = ar.alloc<int64_t>(X->n + 1);
+        CK(cudaMemcpyAsync(ip, X->indptr, sizeof(int64_t) * (X->n + 1), cudaMemcpyHostToDevice, st));
+        int32_t *ix = ar.alloc<int32_t>(nnz);
+        if (nnz) CK(cudaMemcpyAsync(ix, X->indices, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+        out.indptr = ip;
+        out.indices = ix;
+        if (X->values) {
+            float *v = ar.alloc<float>(nnz);
+            if (nnz) CK(cudaMemcpyAsync(v, X->values, sizeof(float) * nnz, cudaMemcpyHostToDevice, st));
+            out.values = v;
+        }
+        if (y) {
+            int8_t *yd = ar.alloc<int8_t>(X->n);
+            CK(cudaMemcpyAsync(yd, y, X->n, cudaMemcpyHostToDevice, st));
+            out.y = yd;
+        }
+    }
+    IngestInfo *info = ar.alloc<IngestInfo>(1);
+    CK(cudaMemsetAsync(info, 0, sizeof(IngestInfo), st));
+    k_validate<<<grid1(X->n), 256, 0, st>>>(X->n, X->d, out.indptr, out.indices, out.values, out.y, info);
+    CK(cudaGetLastError());
+    ++*launches;
+    IngestInfo h;
+    CK(cudaMemcpyAsync(&h, info, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h.bad_indptr) ARG_FAIL("indptr is not non-decreasing from 0");
+    if (h.bad_index) ARG_FAIL("column indices must be strictly increasing within a row and < d");
+    if (h.nonfinite) ARG_FAIL("values must be finite");
+    if (y && h.bad_y) ARG_FAIL("labels must be +1 or -1");
+    out.binary = !h.not_binary;
+    out.maxnnz = h.maxnnz;
+    out.npos = (int64_t)h.npos;
+    if (!out.binary && need_fp64) out.norm = ar.alloc<double>(X->n);
+    if (!out.binary && need_mixed) {
+        out.vmix = ar.alloc<float>(nnz);
+        out.normf = ar.alloc<float>(X->n);
+    }
+    if (out.norm || out.vmix) {
+        k_norms<<<grid1(X->n), 256, 0, st>>>(X->n, out.indptr, out.values, out.norm, out.vmix, out.normf);
+        CK(cudaGetLastError());
+        ++*launches;
+    }
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// order-preserving compaction; returns the count
+int64_t compact(Arena &ar, int pred, int64_t n, const uint8_t *mark, const double *alpha,
+                const int8_t *y, int32_t *list, double *coef, cudaStream_t st, int *launches)
+{
+    int nb = (int)((n + kChunk - 1) / kChunk);
+    int *counts = ar.alloc<int>(nb);
+    int *offs = ar.alloc<int>(nb);
+    long long *tot = ar.alloc<long long>(1);
+    k_count<<<nb, kCT, 0, st>>>(pred, n, mark, alpha, counts);
+    k_scan<<<1, 32, 0, st>>>(counts, nb, offs, tot);
+    k_scatter<<<nb, kCT, 0, st>>>(pred, n, mark, alpha, y, offs, list, coef);
+    CK(cudaGetLastError());
+    *launches += 3;
+    long long h = 0;
+    CK(cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return h;
+}
+
+size_t smem_limit()
+{
+    int dev = 0, v = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    return (size_t)v;
+}
+
+double elapsed_ms(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm_shrink_policy *pol,
+               double *alpha_out, double *b_out, int64_t *iters_out, svm_stats *stats)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    if (!P) ARG_FAIL("params is NULL");
+    if (!y) ARG_FAIL("labels are NULL");
+    if (!alpha_out || !b_out) ARG_FAIL("alpha_out and b_out must not be NULL");
+    if (!(P->C > 0) || !std::isfinite(P->C)) ARG_FAIL("C must be > 0");
+    if (!(P->gamma > 0) || !std::isfinite(P->gamma)) ARG_FAIL("gamma must be > 0");
+    if (!(P->tau > 0) || !std::isfinite(P->tau)) ARG_FAIL("tau must be > 0");
+    if (P->precision != SVM_FP64 && P->precision != SVM_MIXED_BF16) ARG_FAIL("unknown precision %d", P->precision);
+    if (P->tie_break != 0) ARG_FAIL("only the lowest-index tie-break (0) is implemented");
+    if (X && X->n < 2) ARG_FAIL("need at least two samples");
+    svm_shrink_policy none = {SVM_SHRINK_NONE, SVM_RECON_SINGLE, 0.0, 20.0};
+    const svm_shrink_policy &sp = pol ? *pol : none;
+    if (sp.kind < SVM_SHRINK_NONE || sp.kind > SVM_SHRINK_FRACTION) ARG_FAIL("unknown shrink kind %d", sp.kind);
+    if (sp.recon != SVM_RECON_SINGLE && sp.recon != SVM_RECON_MULTI) ARG_FAIL("unknown reconstruction mode %d", sp.recon);
+    if (sp.kind != SVM_SHRINK_NONE && !(sp.value > 0)) ARG_FAIL("shrink value must be > 0");
+    cudaStream_t st = as_stream(P->stream);
+    int launches = 0;
+    Arena ar(st);
+    DevCSR D;
+    const bool mixed = P->precision == SVM_MIXED_BF16;
+    ingest(ar, X, y, !mixed, mixed, st, D, &launches);
+    const int64_t n = D.n;
+    if (D.npos == 0 || D.npos == n) ARG_FAIL("both classes must be present");
+
+    // row-pass arithmetic and its shared-memory footprint
+    int mode = D.binary ? MODE_BINARY : (mixed ? MODE_MIXED : MODE_FP64);
+    int ktab_len = 2 * D.maxnnz + 1;
+    const size_t lim = smem_limit() - 8192;
+    if (mode == MODE_BINARY && smo_layout(MODE_BINARY, (int)D.d, ktab_len, D.maxnnz, 0, 0, 0).total > lim) {
+        // too many columns for the binary tables: use the generic path
+        mode = mixed ? MODE_MIXED : MODE_FP64;
+        if (mode == MODE_FP64 && !D.norm) D.norm = ar.alloc<double>(n);
+        if (mode == MODE_MIXED && !D.vmix) {
+            D.vmix = ar.alloc<float>(D.nnz);
+            D.normf = ar.alloc<float>(n);
+        }
+        k_norms<<<grid1(n), 256, 0, st>>>(n, D.indptr, D.values, D.norm, D.vmix, D.normf);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    // lanes per row from the mean row length; one CTA per SM
+    double avg = (double)D.nnz / (double)n;
+    int lpr = 1;
+    while (lpr < 32 && lpr * 4 < avg) lpr <<= 1;
+    const int sms = device_sms();
+    int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 15) / 16));
+    if (P->ctas > 0) G = (int)std::min<int64_t>(std::min<int64_t>(P->ctas, sms), n);
+    if (G > 256) G = 256;
+    // segment sizes decide whether the rows stay in shared memory
+    int64_t *segnnz_d = ar.alloc<int64_t>(G);
+    k_seg_nnz<<<grid1(G), 256, 0, st>>>(n, G, D.indptr, segnnz_d);
+    CK(cudaGetLastError());
+    ++launches;
+    std::vector<int64_t> segnnz(G);
+    CK(cudaMemcpyAsync(segnnz.data(), segnnz_d, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int64_t seg_nnz_max = 0;
+    for (int64_t v : segnnz) seg_nnz_max = std::max(seg_nnz_max, v);
+    const int seg_rows_max = (int)((n + G - 1) / G);
+    const int kt = mode == MODE_BINARY ? ktab_len : 0;
+    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
+    const SmoLayout Ls = smo_layout(mode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max, seg_nnz_max);
+    const SmoLayout Lr = smo_layout(mode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max, seg_nnz_max);
+    int resident = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 && seg_nnz_max < ((int64_t)1 << 31) &&
+                   Lr.total <= lim_dyn;
+    const size_t smem = resident ? Lr.total : Ls.total;
+    if (smem > lim_dyn) {
+        set_err("d = %lld exceeds the shared-memory target rows of this mode", (long long)D.d);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+    double *ktab = nullptr;
+    if (mode == MODE_BINARY) {
+        ktab = ar.alloc<double>(2 * (size_t)ktab_len);
+        k_ktab<<<grid1(ktab_len), 256, 0, st>>>(P->gamma, ktab_len, ktab);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    const float *vals_fp32 = D.values;
+
+    // solver state
+    double *alpha = ar.alloc<double>(n);
+    double *f = ar.alloc<double>(n);
+    uint8_t *status = ar.alloc<uint8_t>(n);
+    int32_t *act = ar.alloc<int32_t>(n);
+    int32_t *seg_cnt = ar.alloc<int32_t>(G);
+    void *cand = ar.alloc<unsigned char>(2 * (size_t)G * smo_cand_bytes());
+    unsigned *seq = ar.alloc<unsigned>(2 * (size_t)G);
+    SmoCtrl *ctrl = ar.alloc<SmoCtrl>(1);
+    const int64_t trace_len = (P->trace && P->trace_len > 0) ? P->trace_len : 0;
+    int32_t *trace = ar.alloc<int32_t>(2 * std::max<int64_t>(trace_len, 1));
+    if (trace_len) CK(cudaMemsetAsync(trace, 0xff, sizeof(int32_t) * 2 * trace_len, st));
+    k_init<<<grid1(n), 256, 0, st>>>(n, D.y, alpha, f, status);
+    k_reset_active<<<G, 256, 0, st>>>(n, G, act, seg_cnt);
+    CK(cudaGetLastError());
+    launches += 2;
+
+    const bool shrink_on = sp.kind != SVM_SHRINK_NONE;
+    int64_t h = 0;
+    if (sp.kind == SVM_SHRINK_FIXED) h = (int64_t)sp.value;
+    if (sp.kind == SVM_SHRINK_FRACTION) h = (int64_t)std::ceil(sp.value * (double)n);
+    if (shrink_on && h < 1) h = 1;
+    const double ff = sp.first_factor > 0 ? sp.first_factor : 20.0;
+    const int64_t max_iter = P->max_iter > 0 ? P->max_iter : 100 * n + 1000000;
+
+    SmoCtrl hc;
+    std::memset(&hc, 0, sizeof hc);
+    hc.counter = h;
+    hc.active = n;
+    hc.i_up = hc.i_low = -1;
+
+    SmoArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.n = n;
+    A.d = (int32_t)D.d;
+    A.G = G;
+    A.indptr = D.indptr;
+    A.indices = D.indices;
+    A.values = vals_fp32;
+    A.vmix = D.vmix;
+    A.y = D.y;
+    A.norm = D.norm;
+    A.normf = D.normf;
+    A.alpha = alpha;
+    A.f = f;
+    A.status = status;
+    A.act = act;
+    A.seg_cnt = seg_cnt;
+    A.cand = cand;
+    A.seq = seq;
+    A.ctrl = ctrl;
+    A.trace = trace;
+    A.trace_len = trace_len;
+    A.ktab = ktab;
+    A.ktab_len = ktab_len;
+    A.maxnnz = D.maxnnz;
+    A.resident = resident;
+    A.seg_rows_max = seg_rows_max;
+    A.seg_nnz_max = seg_nnz_max;
+    A.C = P->C;
+    A.gamma = P->gamma;
+    A.phase_times = (P->flags & SVM_FLAG_PHASE_TIMES) != 0;
+    int64_t *cta_cycles = nullptr;
+    if (A.phase_times) {
+        cta_cycles = ar.alloc<int64_t>(G);
+        CK(cudaMemsetAsync(cta_cycles, 0, sizeof(int64_t) * G, st));
+    }
+    A.cta_cycles = cta_cycles;
+    A.timeout_ns = 10ll * 1000 * 1000 * 1000;
+
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double ms_smo = 0.0, ms_recon = 0.0;
+    auto run = [&](int select_only, double thr, int64_t hh, int64_t limit) {
+        CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(seq, 0, 2 * sizeof(unsigned) * G, st));
+        A.thr = thr;
+        A.h = hh;
+        A.iter_limit = limit;
+        A.select_only = select_only;
+        CK(cudaEventRecord(e0, st));
+        CK(launch_smo_persistent(mode, lpr, A, smem, st));
+        CK(cudaEventRecord(e1, st));
+        ++launches;
+        CK(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms_smo += ms;
+        if (hc.err) {
+            set_err("a grid-wide wait in the SMO kernel exceeded its time limit");
+            throw Fail{SVM_ERR_TIMEOUT};
+        }
+    };
+
+    bool shrinking = shrink_on;
+    double thr = shrinking ? ff * P->tau : 2.0 * P->tau;
+    int64_t n_recon = 0;
+    int status_code = SVM_OK;
+    uint8_t *mark = nullptr;
+    int32_t *list_w = nullptr, *list_sv = nullptr;
+    double *coef = nullptr;
+    for (;;) {
+        run(1, thr, shrinking ? h : 0, max_iter);
+        if (hc.exit_reason == 1) {
+            status_code = SVM_NOT_CONVERGED;
+            break;
+        }
+        if (!shrinking) break;
+        // Algorithm 6: reconstruct f of the shrunk samples from all alpha > 0
+        if (hc.active < n) {
+            if (!mark) {
+                mark = ar.alloc<uint8_t>(n);
+                list_w = ar.alloc<int32_t>(n);
+                list_sv = ar.alloc<int32_t>(n);
+                coef = ar.alloc<double>(n);
+            }
+            CK(cudaEventRecord(e0, st));
+            CK(cudaMemsetAsync(mark, 0, n, st));
+            k_mark_active<<<G, 256, 0, st>>>(n, G, act, seg_cnt, mark);
+            CK(cudaGetLastError());
+            ++launches;
+            int64_t nw = compact(ar, PRED_UNMARKED, n, mark, alpha, D.y, list_w, nullptr, st, &launches);
+            int64_t nsv = compact(ar, PRED_ALPHA_POS, n, mark, alpha, D.y, list_sv, coef, st, &launches);
+            RbfContract c;
+            std::memset(&c, 0, sizeof c);
+            c.x_indptr = D.indptr;
+            c.x_indices = D.indices;
+            c.x_values = mode == MODE_MIXED ? D.vmix : D.values;
+            c.x_norm = D.norm;
+            c.x_normf = D.normf;
+            c.sv = list_sv;
+            c.coef = coef;
+            c.nsv = nsv;
+            c.z_indptr = D.indptr;
+            c.z_indices = D.indices;
+            c.z_values = c.x_values;
+            c.z_norm = D.norm;
+            c.z_normf = D.normf;
+            c.q = list_w;
+            c.nq = nw;
+            c.d = (int32_t)D.d;
+            c.mode = mode;
+            c.gamma = P->gamma;
+            c.ktab = ktab;
+            c.ktab_len = ktab_len;
+            c.out_by_row = 1;
+            c.out = f;
+            c.yq = D.y;
+            c.add_scalar = 0.0;
+            CK(launch_rbf_contract(c, st));
+            ++launches;
+            CK(cudaEventRecord(e1, st));
+            CK(cudaStreamSynchronize(st));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms_recon += ms;
+        }
+        ++n_recon;
+        k_reset_active<<<G, 256, 0, st>>>(n, G, act, seg_cnt);
+        CK(cudaGetLastError());
+        ++launches;
+        hc.active = n;
+        // b_up / b_low over all samples (a selection pass, no steps)
+        run(1, 2.0 * P->tau, 0, hc.iter);
+        if (!(hc.b_low - hc.b_up > 2.0 * P->tau)) break;
+        if (sp.recon == SVM_RECON_SINGLE) shrinking = false;
+        else hc.counter = h;
+        thr = 2.0 * P->tau;
+    }
+
+    // threshold b (Section III-A), objective, counts
+    const int nbf = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 4095) / 4096));
+    FinishPart *parts = ar.alloc<FinishPart>(nbf);
+    FinishPart *tot = ar.alloc<FinishPart>(1);
+    k_finish_part<<<nbf, kCT, 0, st>>>(n, P->C, alpha, f, status, parts);
+    k_finish_total<<<1, 32, 0, st>>>(parts, nbf, tot);
+    CK(cudaGetLastError());
+    launches += 2;
+    FinishPart fp;
+    CK(cudaMemcpyAsync(&fp, tot, sizeof fp, cudaMemcpyDeviceToHost, st));
+    if (X->on_device) CK(cudaMemcpyAsync(alpha_out, alpha, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemcpyAsync(alpha_out, alpha, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> tr;
+    if (trace_len) {
+        tr.resize(2 * trace_len);
+        CK(cudaMemcpyAsync(tr.data(), trace, sizeof(int32_t) * 2 * trace_len, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if (trace_len) {
+        for (int64_t t = 0; t < trace_len; ++t) {
+            bool done = t < hc.iter;
+            P->trace[2 * t] = done ? tr[2 * t] : -1;
+            P->trace[2 * t + 1] = done ? tr[2 * t + 1] : -1;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double b = fp.n0 > 0 ? fp.sum_f0 / (double)fp.n0 : 0.5 * (hc.b_up + hc.b_low);
+    *b_out = b;
+    if (iters_out) *iters_out = hc.iter;
+    if (stats) {
+        stats->iters = hc.iter;
+        stats->shrink_events = hc.shrink_events;
+        stats->reconstructions = n_recon;
+        stats->final_active = hc.active;
+        stats->n_sv = fp.nsv;
+        stats->n_bound = fp.nbound;
+        stats->row_visits = hc.row_visits;
+        stats->b_up = hc.b_up;
+        stats->b_low = hc.b_low;
+        stats->objective = fp.sum_a - 0.5 * fp.sum_ayfy;
+        stats->ms_smo = ms_smo;
+        stats->ms_recon = ms_recon;
+        stats->binary_input = mode == MODE_BINARY;
+        stats->resident = resident;
+        stats->ctas = G;
+        stats->lanes_per_row = lpr;
+        int dev = 0, khz = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        for (int k = 0; k < 6; ++k) stats->phase_ms[k] = khz > 0 ? (double)hc.phase_cycles[k] / (double)khz : 0.0;
+        stats->cta_busy_ms_min = stats->cta_busy_ms_max = 0.0;
+        if (cta_cycles && khz > 0) {
+            std::vector<int64_t> cc(G);
+            CK(cudaMemcpy(cc.data(), cta_cycles, sizeof(int64_t) * G, cudaMemcpyDeviceToHost));
+            int64_t mn = cc[0], mx = cc[0];
+            for (int64_t v : cc) { mn = std::min(mn, v); mx = std::max(mx, v); }
+            stats->cta_busy_ms_min = (double)mn / khz;
+            stats->cta_busy_ms_max = (double)mx / khz;
+        }
+        stats->launches = launches;
+        stats->ms_total = elapsed_ms(t_start);
+    }
+    g_launches += launches;
+    return status_code;
+}
+
+int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double b, double gamma,
+                  const svm_csr *Z, int32_t precision, void *stream, double *out)
+{
+    if (!X || !Z || !y || !alpha || !out) ARG_FAIL("NULL argument");
+    if (!(gamma > 0)) ARG_FAIL("gamma must be > 0");
+    if (Z->d != X->d) ARG_FAIL("Z->d (%lld) must equal X->d (%lld)", (long long)Z->d, (long long)X->d);
+    if (precision != SVM_FP64 && precision != SVM_MIXED_BF16) ARG_FAIL("unknown precision %d", precision);
+    if (Z->n == 0) return SVM_OK;
+    cudaStream_t st = as_stream(stream);
+    int launches = 0;
+    Arena ar(st);
+    const bool mixed = precision == SVM_MIXED_BF16;
+    DevCSR DX, DZ;
+    ingest(ar, X, y, !mixed, mixed, st, DX, &launches);
+    ingest(ar, Z, nullptr, !mixed, mixed, st, DZ, &launches);
+    const int64_t n = DX.n;
+    const double *alpha_d = alpha;
+    if (!X->on_device) {
+        double *a = ar.alloc<double>(n);
+        CK(cudaMemcpyAsync(a, alpha, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        alpha_d = a;
+    }
+    int mode = (DX.binary && DZ.binary) ? MODE_BINARY : (mixed ? MODE_MIXED : MODE_FP64);
+    if (mode != MODE_BINARY && (DX.binary || DZ.binary)) {
+        // one side binary, the other not: derive the missing norms
+        for (DevCSR *D : {&DX, &DZ}) {
+            if (mode == MODE_FP64 && !D->norm) D->norm = ar.alloc<double>(D->n);
+            if (mode == MODE_MIXED && !D->vmix) {
+                D->vmix = ar.alloc<float>(D->nnz);
+                D->normf = ar.alloc<float>(D->n);
+            }
+            k_norms<<<grid1(D->n), 256, 0, st>>>(D->n, D->indptr, D->values, D->norm, D->vmix, D->normf);
+            CK(cudaGetLastError());
+            ++launches;
+        }
+    }
+    int ktab_len = DX.maxnnz + DZ.maxnnz + 1;
+    double *ktab = nullptr;
+    if (mode == MODE_BINARY) {
+        ktab = ar.alloc<double>(2 * (size_t)ktab_len);
+        k_ktab<<<grid1(ktab_len), 256, 0, st>>>(gamma, ktab_len, ktab);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    size_t need = mode == MODE_BINARY ? 4 * (size_t)DX.d : (mode == MODE_FP64 ? 8 * 8 : 4 * 8) * (size_t)DX.d;
+    if (need > smem_limit() - 8192) {
+        set_err("d = %lld exceeds the shared-memory query tile of this mode", (long long)DX.d);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+    int32_t *list_sv = ar.alloc<int32_t>(n);
+    double *coef = ar.alloc<double>(n);
+    int64_t nsv = compact(ar, PRED_ALPHA_POS, n, nullptr, alpha_d, DX.y, list_sv, coef, st, &launches);
+    double *out_d = out;
+    if (!Z->on_device) out_d = ar.alloc<double>(DZ.n);
+    RbfContract c;
+    std::memset(&c, 0, sizeof c);
+    c.x_indptr = DX.indptr;
+    c.x_indices = DX.indices;
+    c.x_values = mode == MODE_MIXED ? DX.vmix : DX.values;
+    c.x_norm = DX.norm;
+    c.x_normf = DX.normf;
+    c.sv = list_sv;
+    c.coef = coef;
+    c.nsv = nsv;
+    c.z_indptr = DZ.indptr;
+    c.z_indices = DZ.indices;
+    c.z_values = mode == MODE_MIXED ? DZ.vmix : DZ.values;
+    c.z_norm = DZ.norm;
+    c.z_normf = DZ.normf;
+    c.q = nullptr;
+    c.nq = DZ.n;
+    c.d = (int32_t)DX.d;
+    c.mode = mode;
+    c.gamma = gamma;
+    c.ktab = ktab;
+    c.ktab_len = ktab_len;
+    c.out_by_row = 0;
+    c.out = out_d;
+    c.yq = nullptr;
+    c.add_scalar = -b;
+    CK(launch_rbf_contract(c, st));
+    ++launches;
+    g_launches += launches;
+    if (!Z->on_device) CK(cudaMemcpyAsync(out, out_d, sizeof(double) * DZ.n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SVM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int svm_train(const svm_csr *X, const int8_t *y, const svm_params *params,
+              const svm_shrink_policy *policy, double *alpha_out, double *b_out,
+              int64_t *iters_out, svm_stats *stats)
+{
+    g_err.clear();
+    try {
+        if (!X) ARG_FAIL("X is NULL");
+        return train_impl(X, y, params, policy, alpha_out, b_out, iters_out, stats);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double b, double gamma,
+                 const svm_csr *Z, int32_t precision, void *stream, double *out)
+{
+    g_err.clear();
+    try {
+        return decision_impl(X, y, alpha, b, gamma, Z, precision, stream, out);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+const char *svm_last_error(void) { return g_err.c_str(); }
+
+int64_t svm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+const char *svm_version(void) { return "svm_gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

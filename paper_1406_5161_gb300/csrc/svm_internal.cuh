@@ -1,0 +1,160 @@
+// Internal declarations of the GB300 SVM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "svm_gb300.h"
+
+namespace svmgb {
+
+// Index sets of Eq. (setinfo), one byte per sample.
+enum : uint8_t { ST_I0 = 0, ST_I1 = 1, ST_I2 = 2, ST_I3 = 3, ST_I4 = 4 };
+
+__host__ __device__ __forceinline__ bool st_up(uint8_t s) { return s <= ST_I2; }
+__host__ __device__ __forceinline__ bool st_low(uint8_t s) { return s == ST_I0 || s >= ST_I3; }
+__host__ __device__ __forceinline__ uint8_t st_of(int8_t y, double a, double C)
+{
+    if (a > 0.0 && a < C) return ST_I0;
+    if (a == 0.0) return y > 0 ? ST_I1 : ST_I4;
+    return y > 0 ? ST_I3 : ST_I2;
+}
+
+// Row-pass arithmetic of the fused step.
+enum { MODE_BINARY = 0, MODE_FP64 = 1, MODE_MIXED = 2 };
+
+// Solver state carried between launches of the persistent step kernel.
+struct SmoCtrl {
+    double b_up, b_low;        // f at i_up / i_low over the active set
+    double a_up, a_low;        // alpha of i_up / i_low
+    int64_t iter;              // SMO steps done
+    int64_t counter;           // shrink counter
+    int64_t active;            // active-set size
+    int64_t row_visits;        // sum of active-set sizes over the steps
+    int32_t i_up, i_low;
+    int32_t exit_reason;       // 0: gap <= thr, 1: iteration limit
+    int32_t err;               // 0 ok, 1 timeout in a grid-wide wait
+    int64_t shrink_events;
+    // SM cycles spent by CTA 0 in each phase of a step (summed over steps,
+    // recorded only when SmoArgs::phase_times is set):
+    // 0 target rows, 1 pair step, 2 row pass + CTA reduction, 3 publish,
+    // 4 grid exchange, 5 other
+    int64_t phase_cycles[6];
+};
+
+// Kernel arguments. Sample indices in the active lists are local to their
+// segment (global index = seg_lo(segment) + local index).
+struct SmoArgs {
+    int64_t n;
+    int32_t d;
+    int32_t G;                 // CTAs = row segments
+    const int64_t *indptr;
+    const int32_t *indices;
+    const float *values;       // FP64 mode
+    const float *vmix;         // mixed mode: values rounded to BF16, held as FP32
+    const int8_t *y;
+    const double *norm;        // ||x_i||^2 (FP64 / binary: exact)
+    const float *normf;        // mixed: ||x_i||^2 of the rounded values
+    double *alpha;
+    double *f;
+    uint8_t *status;           // bits 0-2 index set, bit 7 label is +1
+    int32_t *act;              // active lists, segment s at [lo(s), lo(s) + cnt(s))
+    int32_t *seg_cnt;
+    void *cand;                // [2][G] candidate slots of smo_cand_bytes() each
+    unsigned *seq;             // [2][G], zeroed before each launch
+    SmoCtrl *ctrl;
+    int32_t *trace;            // [2 * trace_len]
+    int64_t trace_len;
+    const double *ktab;        // binary: exp(-gamma * k), k = 0 .. ktab_len - 1, followed by
+                               // the correctly rounded 1 / (2 - 2 exp(-gamma * k)) (0 if <= 1e-12)
+    int32_t ktab_len;
+    int32_t maxnnz;            // longest row
+    int32_t resident;          // segments held in shared memory
+    int32_t seg_rows_max;      // largest segment (rows)
+    int64_t seg_nnz_max;       // largest segment (stored entries)
+    double C, gamma, thr;
+    int64_t iter_limit;
+    int64_t h;                 // shrink counter reset value (0: no shrinking)
+    int32_t select_only;       // start with a selection pass
+    int32_t phase_times;       // record per-phase cycle counts (CTA 0)
+    int64_t *cta_cycles;       // with phase_times: per-CTA cycles of work per launch (G)
+    int64_t timeout_ns;
+};
+
+// Dynamic shared-memory layout of the step kernel (byte offsets).
+struct SmoLayout {
+    size_t tgt, tcol, ktab, f, alpha, nrm, rowptr, act, st, col, val, total;
+};
+
+__host__ __device__ inline size_t smo_align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline SmoLayout smo_layout(int mode, int d, int ktab_len, int maxnnz,
+                                                int resident, int rows, int64_t nnz)
+{
+    SmoLayout L;
+    size_t tgt_sz = mode == 0 ? 2 : (mode == 1 ? 16 : 8);
+    size_t o = 0;
+    L.tgt = o;    o = smo_align16(o + 2 * (size_t)d * tgt_sz);
+    L.tcol = o;   o = smo_align16(o + 4 * (size_t)(maxnnz > 0 ? maxnnz : 1) * 4);
+    L.ktab = o;   o = smo_align16(o + (mode == 0 ? (size_t)ktab_len * 16 : 0));  // exp and 1/eta tables
+    if (!resident) rows = 0, nnz = 0;
+    L.f = o;      o = smo_align16(o + (size_t)rows * 8);
+    L.alpha = o;  o = smo_align16(o + (size_t)rows * 8);
+    L.nrm = o;    o = smo_align16(o + (size_t)rows * (mode == 1 ? 8 : (mode == 2 ? 4 : 0)));
+    L.rowptr = o; o = smo_align16(o + (size_t)(resident ? rows + 1 : 0) * 4);
+    L.act = o;    o = smo_align16(o + (size_t)rows * 4);
+    L.st = o;     o = smo_align16(o + (size_t)rows);
+    L.col = o;    o = smo_align16(o + (size_t)nnz * 2);
+    L.val = o;    o = smo_align16(o + (size_t)nnz * (mode == 0 ? 0 : 4));
+    L.total = o;
+    return L;
+}
+
+__host__ __device__ __forceinline__ int64_t seg_lo(int64_t n, int G, int s)
+{
+    return (n * (int64_t)s) / G;
+}
+
+// ---------------------------------------------------------------- launchers
+// (each returns a cudaError_t; kernels live in their own translation units)
+cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem,
+                                  cudaStream_t st);
+size_t smo_cand_bytes();
+size_t smo_static_smem();
+int smo_threads();
+
+// Contraction of query rows against support vectors with the RBF epilogue:
+//   out[q] = sum_k coef[k] * K(x_sv[k], z_q) + add_scalar - (yq ? yq[row] : 0)
+// Gradient reconstruction (Algorithm 6) and the decision function
+// (Eq. classi) are both this contraction.
+struct RbfContract {
+    // support vectors: rows sv[0..nsv) of X with coefficients alpha_k y_k
+    const int64_t *x_indptr;
+    const int32_t *x_indices;
+    const float *x_values;     // FP64 mode: input values; mixed: BF16-rounded
+    const double *x_norm;
+    const float *x_normf;
+    const int32_t *sv;
+    const double *coef;
+    int64_t nsv;
+    // queries: rows q[0..nq) of Z, or rows 0..nq-1 when q == NULL
+    const int64_t *z_indptr;
+    const int32_t *z_indices;
+    const float *z_values;
+    const double *z_norm;
+    const float *z_normf;
+    const int32_t *q;
+    int64_t nq;
+    int32_t d;
+    int32_t mode;              // MODE_BINARY / MODE_FP64 / MODE_MIXED
+    double gamma;
+    const double *ktab;        // binary: exp(-gamma * k)
+    int32_t ktab_len;
+    int32_t out_by_row;        // 1: out[row id], 0: out[list position]
+    double *out;
+    const int8_t *yq;          // subtract yq[row] when non-NULL
+    double add_scalar;
+};
+cudaError_t launch_rbf_contract(const RbfContract &c, cudaStream_t st);
+
+}  // namespace svmgb

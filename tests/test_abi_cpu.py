@@ -1,0 +1,64 @@
+"""The C ABI library builds, loads and exports what include/*.h declares;
+argument errors are reported without touching a GPU."""
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1406_5161_gb300 as pkg
+from paper_1406_5161_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(svm_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    assert "svm_train" in names and "svm_decision" in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = pkg.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.lib_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    for name in declared_functions():
+        assert name in exported, f"{name} declared but not exported"
+        assert hasattr(lib, name)
+
+
+def test_version_string():
+    assert "sm_103a" in pkg.svm_version()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(C=0.0), "C must be"),
+    (dict(gamma=-1.0), "gamma must be"),
+    (dict(tau=0.0), "tau must be"),
+    (dict(precision=7), "unknown precision"),
+])
+def test_argument_errors_are_reported(kw, msg):
+    p = synth.small_dense(10, 3, seed=1)
+    args = dict(C=1.0, gamma=0.1, tau=1e-3)
+    args.update(kw)
+    r = pkg.svm_train(p.X, p.y, check=False, **args)
+    assert r["status"] == pkg.SVM_ERR_ARG
+    assert msg in pkg.svm_last_error()
+
+
+def test_bad_shrink_policy_is_reported():
+    p = synth.small_dense(10, 3, seed=1)
+    r = pkg.svm_train(p.X, p.y, 1.0, 0.1, 1e-3, shrink=(9, 1, 0), check=False)
+    assert r["status"] == pkg.SVM_ERR_ARG
