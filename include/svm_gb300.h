@@ -109,6 +109,9 @@ typedef struct svm_params {
     int32_t flags;           /* bitwise OR of SVM_FLAG_* */
     int32_t ctas;            /* CTAs (= row segments) of the fused step; 0 = one per
                                 SM (capped by n / 16); larger values are clamped */
+    int32_t lanes_per_row;   /* lanes sharing one row in the row pass (rounded up to
+                                a power of two <= 32); 0 = from the mean row length */
+    int32_t reserved;
 } svm_params;
 
 /* Keep every row segment in global memory even when it would fit in the
@@ -118,6 +121,10 @@ typedef struct svm_params {
 /* Record the SM cycles one CTA spends in each phase of a step
  * (svm_stats.phase_ms, converted at the device's maximum clock). */
 #define SVM_FLAG_PHASE_TIMES 2
+/* Exchange the per-step candidates of all CTAs through global memory only
+ * (by default CTAs form thread-block clusters of 8 that reduce through
+ * distributed shared memory, and only cluster leaders use global memory). */
+#define SVM_FLAG_NO_CLUSTERS 4
 
 typedef struct svm_shrink_policy {
     int32_t kind;            /* enum svm_shrink_kind */
@@ -145,11 +152,12 @@ typedef struct svm_stats {
     int32_t resident;        /* 1 when row segments were held in shared memory */
     int32_t ctas;            /* CTAs (= row segments) of the fused step */
     int32_t lanes_per_row;   /* lanes that share one row in the row pass */
-    int32_t reserved;
-    double phase_ms[6];      /* with SVM_FLAG_PHASE_TIMES: time of CTA 0 per step
-                                phase, summed over steps: target rows, pair step,
-                                row pass + CTA reduction, publish, grid exchange,
-                                other */
+    int32_t cluster_size;    /* CTAs per thread-block cluster of the fused step */
+    double phase_ms[8];      /* with SVM_FLAG_PHASE_TIMES: time of CTA 0 per step
+                                phase, summed over steps: target rows, pair step
+                                (FP64 part), row pass + CTA reduction, publish,
+                                grid exchange, other, pair step (K(up,low) part),
+                                unused */
     double cta_busy_ms_min;  /* with SVM_FLAG_PHASE_TIMES: least and most time a */
     double cta_busy_ms_max;  /* CTA spent from step start to publishing its candidate */
 } svm_stats;

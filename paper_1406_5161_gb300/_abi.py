@@ -24,6 +24,7 @@ SVM_SHRINK_NONE, SVM_SHRINK_FIXED, SVM_SHRINK_FRACTION = 0, 1, 2
 SVM_RECON_SINGLE, SVM_RECON_MULTI = 0, 1
 SVM_FLAG_STREAM_ROWS = 1
 SVM_FLAG_PHASE_TIMES = 2
+SVM_FLAG_NO_CLUSTERS = 4
 
 STATUS_NAMES = {0: "SVM_OK", 1: "SVM_NOT_CONVERGED", 2: "SVM_PENDING", -1: "SVM_ERR_ARG",
                 -2: "SVM_ERR_OOM", -3: "SVM_ERR_BUDGET", -4: "SVM_ERR_TIMEOUT",
@@ -40,7 +41,8 @@ class svm_params(ct.Structure):
     _fields_ = [("C", ct.c_double), ("gamma", ct.c_double), ("tau", ct.c_double),
                 ("max_iter", ct.c_int64), ("precision", ct.c_int32), ("tie_break", ct.c_int32),
                 ("stream", ct.c_void_p), ("trace", ct.c_void_p), ("trace_len", ct.c_int64),
-                ("flags", ct.c_int32), ("ctas", ct.c_int32)]
+                ("flags", ct.c_int32), ("ctas", ct.c_int32),
+                ("lanes_per_row", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class svm_shrink_policy(ct.Structure):
@@ -56,7 +58,7 @@ class svm_stats(ct.Structure):
                 ("ms_total", ct.c_double), ("ms_smo", ct.c_double), ("ms_recon", ct.c_double),
                 ("binary_input", ct.c_int32), ("launches", ct.c_int32),
                 ("resident", ct.c_int32), ("ctas", ct.c_int32), ("lanes_per_row", ct.c_int32),
-                ("reserved", ct.c_int32), ("phase_ms", ct.c_double * 6),
+                ("cluster_size", ct.c_int32), ("phase_ms", ct.c_double * 8),
                 ("cta_busy_ms_min", ct.c_double), ("cta_busy_ms_max", ct.c_double)]
 
     def as_dict(self) -> dict:
@@ -182,7 +184,7 @@ def _stream_ptr(stream):
 def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int = 0,
               precision: int = SVM_FP64, shrink: tuple | None = None, stream=None,
               trace_len: int = 0, alpha_out=None, flags: int = 0, ctas: int = 0,
-              check: bool = True) -> dict:
+              lanes_per_row: int = 0, check: bool = True) -> dict:
     """Train by SMO. ``shrink`` = (kind, value, recon[, first_factor]) or None.
     X is a host CSR (numpy arrays) or a DeviceCSR; y matches X's memory space.
     Returns dict(status, alpha, b, iters, stats, trace)."""
@@ -204,7 +206,7 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
     trace = np.full((max(trace_len, 0), 2), -1, dtype=np.int32)
     p = svm_params(float(C), float(gamma), float(tau), int(max_iter), int(precision), 0,
                    _stream_ptr(stream), trace.ctypes.data if trace_len else None, int(trace_len),
-                   int(flags), int(ctas))
+                   int(flags), int(ctas), int(lanes_per_row), 0)
     pol = None
     if shrink is not None:
         kind, value, recon = shrink[:3]

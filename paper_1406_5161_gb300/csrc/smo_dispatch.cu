@@ -3,21 +3,35 @@
 
 namespace svmgb {
 
-cudaError_t launch_smo_binary(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st);
-cudaError_t launch_smo_fp64(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st);
-cudaError_t launch_smo_mixed(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st);
+cudaError_t launch_smo_binary(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st, int cs);
+cudaError_t launch_smo_fp64(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st, int cs);
+cudaError_t launch_smo_mixed(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st, int cs);
+int max_clusters_binary(int lpr, int resident, size_t smem, int cs);
+int max_clusters_fp64(int lpr, int resident, size_t smem, int cs);
+int max_clusters_mixed(int lpr, int resident, size_t smem, int cs);
 
 int smo_threads() { return smo::kThreads; }
 size_t smo_cand_bytes() { return sizeof(smo::CandFull); }
 size_t smo_static_smem() { return sizeof(smo::Shared); }
 
-cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem, cudaStream_t st)
+cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem, cudaStream_t st,
+                                  int cs)
 {
     switch (mode) {
-    case MODE_BINARY: return launch_smo_binary(lpr, a, smem, st);
-    case MODE_FP64: return launch_smo_fp64(lpr, a, smem, st);
-    case MODE_MIXED: return launch_smo_mixed(lpr, a, smem, st);
+    case MODE_BINARY: return launch_smo_binary(lpr, a, smem, st, cs);
+    case MODE_FP64: return launch_smo_fp64(lpr, a, smem, st, cs);
+    case MODE_MIXED: return launch_smo_mixed(lpr, a, smem, st, cs);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+int smo_max_clusters(int mode, int lpr, int resident, size_t smem, int cs)
+{
+    switch (mode) {
+    case MODE_BINARY: return max_clusters_binary(lpr, resident, smem, cs);
+    case MODE_FP64: return max_clusters_fp64(lpr, resident, smem, cs);
+    case MODE_MIXED: return max_clusters_mixed(lpr, resident, smem, cs);
+    default: return 0;
     }
 }
 

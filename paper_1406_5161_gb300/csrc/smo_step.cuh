@@ -30,6 +30,7 @@
 #pragma once
 
 #include <climits>
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "svm_internal.cuh"
@@ -94,6 +95,14 @@ struct __align__(16) CandFull {
     int32_t pad[3];
 };
 static_assert(sizeof(CandFull) % 16 == 0, "candidate slots are read with vector loads");
+
+// Result of a step's exchange, written into every CTA of a cluster.
+struct __align__(16) ResultArea {
+    Side up, low;
+    long long total;   // active-set size over all segments
+    int flag;          // a wait timed out
+    int pad;
+};
 
 // FP64 compares and selects are long-latency on sm_103a; comparisons here
 // use an order-preserving integer image of the double instead:
@@ -207,7 +216,9 @@ struct Shared {
     int wiup[kWarps], wilow[kWarps];
     Side rup[8], rlow[8];                     // per-warp winners of the exchange
     unsigned long long rkup[8], rklow[8];
-    int riup[8], rilow[8];
+    int riup[8], rilow[8], rto[8];
+    CandFull ccand[8];                        // cluster leader: its CTAs' candidates
+    ResultArea res;                           // exchange result pushed by the leader
     long long rcount[8];
     int scan[kWarps];
     int scan_tot;
@@ -236,6 +247,12 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = A.G, cta = blockIdx.x;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int csize = (int)cluster.num_blocks();   // CTAs per cluster (1 without clusters)
+    const int crank = (int)cluster.block_rank();
+    const int cid = cta / csize;                   // cluster index = leader slot
+    const int nlead = G / csize;
     const int d = A.d;
     const SmoLayout L = smo_layout(MODE, d, A.ktab_len, A.maxnnz, RES ? 1 : 0, A.seg_rows_max,
                                    A.seg_nnz_max);
@@ -285,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     int64_t iter = C0.iter, counter = C0.counter, row_visits = C0.row_visits;
     int64_t shrink_events = C0.shrink_events;
     long long total = C0.active;
-    int64_t ph[6] = {0, 0, 0, 0, 0, 0};
+    int64_t ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (tid == 0) sh.flag_timeout = 0;
     Side up, low;
     side_empty(up, true);
@@ -428,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 }
 #pragma unroll
                 for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                if (timed && tid == 0) { uint64_t t = clock64(); ph[6] += t - tp; tp = t; }
                 if (lane == 0) {
                     double kul, rinv = 0.0;
                     if constexpr (MODE == MODE_BINARY) {
@@ -658,7 +676,11 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             cnt = kept;
         }
         if (timed && tid == 0) { uint64_t t = clock64(); ph[2] += t - tp; tp = t; }
-        // ---- 4. grid-wide exchange (release/acquire flags, bounded waits)
+        // ---- 4. grid-wide exchange, hierarchical: the CTAs of a thread-block
+        //         cluster hand their candidates to the cluster's first CTA
+        //         through distributed shared memory; only those leaders
+        //         exchange through global memory (release/acquire flags,
+        //         bounded waits) and push the result back to their cluster.
         ++epoch;
         const int par = (int)(epoch & 1);
         if (warp == 0) {
@@ -673,15 +695,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
             const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
             if (lane == 0) {
-                Side a, b;
-                if (mu) a = sh.wup[__ffs(mu) - 1]; else side_empty(a, true);
-                if (ml) b = sh.wlow[__ffs(ml) - 1]; else side_empty(b, false);
-                CandFull *slot = reinterpret_cast<CandFull *>(A.cand) + (size_t)par * G + cta;
-                slot->up = a;
-                slot->low = b;
-                slot->count = cnt;
+                CandFull cf;
+                if (mu) cf.up = sh.wup[__ffs(mu) - 1]; else side_empty(cf.up, true);
+                if (ml) cf.low = sh.wlow[__ffs(ml) - 1]; else side_empty(cf.low, false);
+                cf.count = cnt;
+                cf.pad[0] = cf.pad[1] = cf.pad[2] = 0;
+                CandFull *dst = cluster.map_shared_rank(sh.ccand, 0);
+                dst[crank] = cf;
                 if (busy_on) busy += clock64() - cta_t0;
-                st_release_u32(A.seq + (size_t)par * G + cta, epoch);
                 if (timed) { uint64_t t = clock64(); ph[3] += t - tp; tp = t; }
             }
         }
@@ -693,84 +714,122 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) tgt_clear<MODE>(P[pcu[k]]);
             for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) tgt_clear<MODE>(P[pcl[k]]);
         }
-        const int rwarps = (G + 31) / 32;
-        if (warp < rwarps) {
-            const int c = warp * 32 + lane;
-            Side a, b;
-            side_empty(a, true);
-            side_empty(b, false);
-            long long cc = 0;
-            int timed_out = 0;
-            if (c < G) {
-                const unsigned *sp = A.seq + (size_t)par * G + c;
-                uint64_t t0 = 0;
-                int spins = 0;
-                while (ld_relaxed_u32(sp) < epoch) {
-                    if (++spins >= 256) {
-                        spins = 0;
-                        uint64_t now = global_ns();
-                        if (t0 == 0) t0 = now;
-                        else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
-                        if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+        cluster.sync();
+        const int rwarps = (nlead + 31) / 32;
+        if (crank == 0) {
+            if (warp == 0) {
+                // cluster winner -> this leader's global slot
+                CandFull c;
+                if (lane < csize) c = sh.ccand[lane];
+                else { side_empty(c.up, true); side_empty(c.low, false); c.count = 0; }
+                unsigned long long k1 = c.up.i == INT_MAX ? kNoKey : key_up(c.up.f);
+                unsigned long long k2 = c.low.i == INT_MAX ? kNoKey : key_low(c.low.f);
+                int i1 = c.up.i, i2 = c.low.i;
+                const unsigned long long k1s = k1, k2s = k2;
+                const int i1s = i1, i2s = i2;
+                long long cc = c.count;
+                warp_min_ki(k1, i1);
+                warp_min_ki(k2, i2);
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
+                const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
+                const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
+                if (lane == 0) {
+                    CandFull out;
+                    if (mu) out.up = sh.ccand[__ffs(mu) - 1].up; else side_empty(out.up, true);
+                    if (ml) out.low = sh.ccand[__ffs(ml) - 1].low; else side_empty(out.low, false);
+                    out.count = (int32_t)cc;
+                    out.pad[0] = out.pad[1] = out.pad[2] = 0;
+                    *(reinterpret_cast<CandFull *>(A.cand) + (size_t)par * nlead + cid) = out;
+                    st_release_u32(A.seq + (size_t)par * nlead + cid, epoch);
+                }
+            }
+            if (warp < rwarps) {
+                const int c = warp * 32 + lane;
+                Side a, b;
+                side_empty(a, true);
+                side_empty(b, false);
+                long long cc = 0;
+                int timed_out = 0;
+                if (c < nlead) {
+                    const unsigned *sp = A.seq + (size_t)par * nlead + c;
+                    uint64_t t0 = 0;
+                    int spins = 0;
+                    while (ld_relaxed_u32(sp) < epoch) {
+                        if (++spins >= 256) {
+                            spins = 0;
+                            uint64_t now = global_ns();
+                            if (t0 == 0) t0 = now;
+                            else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
+                            if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+                        }
+                    }
+                    if (!timed_out) {
+                        fence_acq_rel_gpu();   // acquire: the slot written before the flag
+                        // L2 reads (bypass L1, which is not coherent across SMs)
+                        union {
+                            CandFull c;
+                            int4 v[sizeof(CandFull) / 16];
+                        } u;
+                        const int4 *q = reinterpret_cast<const int4 *>(
+                            reinterpret_cast<const CandFull *>(A.cand) + (size_t)par * nlead + c);
+#pragma unroll
+                        for (int j = 0; j < (int)(sizeof(CandFull) / 16); ++j) u.v[j] = __ldcg(q + j);
+                        a = u.c.up;
+                        b = u.c.low;
+                        cc = u.c.count;
                     }
                 }
-                if (!timed_out) {
-                    fence_acq_rel_gpu();   // acquire: the slot written before the flag
-
-                    // L2 reads (bypass L1, which is not coherent across SMs)
-                    union {
-                        CandFull c;
-                        int4 v[sizeof(CandFull) / 16];
-                    } u;
-                    const int4 *q = reinterpret_cast<const int4 *>(
-                        reinterpret_cast<const CandFull *>(A.cand) + (size_t)par * G + c);
+                const int any_to = __any_sync(0xffffffffu, timed_out);
+                if (any_to && lane == 0) atomicExch(&A.ctrl->err, 1);
+                unsigned long long k1 = a.i == INT_MAX ? kNoKey : key_up(a.f);
+                unsigned long long k2 = b.i == INT_MAX ? kNoKey : key_low(b.f);
+                int i1 = a.i, i2 = b.i;
+                warp_min_ki(k1, i1);
+                warp_min_ki(k2, i2);
 #pragma unroll
-                    for (int j = 0; j < (int)(sizeof(CandFull) / 16); ++j) u.v[j] = __ldcg(q + j);
-                    a = u.c.up;
-                    b = u.c.low;
-                    cc = u.c.count;
-                }
-            }
-            if (__any_sync(0xffffffffu, timed_out)) {
+                for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
                 if (lane == 0) {
-                    atomicExch(&A.ctrl->err, 1);
-                    sh.flag_timeout = 1;
+                    sh.rkup[warp] = k1; sh.riup[warp] = i1;
+                    sh.rklow[warp] = k2; sh.rilow[warp] = i2;
+                    sh.rcount[warp] = cc;
+                    sh.rto[warp] = any_to;
+                }
+                if (i1 != INT_MAX && a.i == i1) sh.rup[warp] = a;
+                if (i2 != INT_MAX && b.i == i2) sh.rlow[warp] = b;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // final winner, pushed to every CTA of the cluster
+                unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
+                int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0, to = sh.rto[0];
+                long long cc = sh.rcount[0];
+                for (int w = 1; w < rwarps; ++w) {
+                    if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
+                    if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
+                    cc += sh.rcount[w];
+                    to |= sh.rto[w];
+                }
+                if (lane < csize) {
+                    ResultArea res;
+                    if (iu != INT_MAX) res.up = sh.rup[wu]; else side_empty(res.up, true);
+                    if (il != INT_MAX) res.low = sh.rlow[wl]; else side_empty(res.low, false);
+                    res.total = cc;
+                    res.flag = to;
+                    res.pad = 0;
+                    *cluster.map_shared_rank(&sh.res, lane) = res;
                 }
             }
-            unsigned long long k1 = a.i == INT_MAX ? kNoKey : key_up(a.f);
-            unsigned long long k2 = b.i == INT_MAX ? kNoKey : key_low(b.f);
-            int i1 = a.i, i2 = b.i;
-            warp_min_ki(k1, i1);
-            warp_min_ki(k2, i2);
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
-            if (lane == 0) {
-                sh.rkup[warp] = k1; sh.riup[warp] = i1;
-                sh.rklow[warp] = k2; sh.rilow[warp] = i2;
-                sh.rcount[warp] = cc;
-            }
-            if (i1 != INT_MAX && a.i == i1) sh.rup[warp] = a;
-            if (i2 != INT_MAX && b.i == i2) sh.rlow[warp] = b;
         }
-        __syncthreads();
+        cluster.sync();
         if (timed && tid == 0) { uint64_t t = clock64(); ph[4] += t - tp; tp = t; }
-        if (sh.flag_timeout) break;
-        {
-            unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
-            int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0;
-            long long cc = sh.rcount[0];
-            for (int w = 1; w < rwarps; ++w) {
-                if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
-                if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
-                cc += sh.rcount[w];
-            }
-            prev_valid = first ? 0 : 1;
-            prev_len_u = up.len;
-            prev_len_l = low.len;
-            if (iu != INT_MAX) up = sh.rup[wu]; else side_empty(up, true);
-            if (il != INT_MAX) low = sh.rlow[wl]; else side_empty(low, false);
-            total = cc;
-        }
+        if (sh.res.flag) break;
+        prev_valid = first ? 0 : 1;
+        prev_len_u = up.len;
+        prev_len_l = low.len;
+        up = sh.res.up;
+        low = sh.res.low;
+        total = sh.res.total;
         if (!first) {
             ++iter;
             if (shrink_now) {
@@ -784,9 +843,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             A.trace[2 * iter] = up.i == INT_MAX ? -1 : up.i;
             A.trace[2 * iter + 1] = low.i == INT_MAX ? -1 : low.i;
         }
-        __syncthreads();   // every thread has read sh.* before it is reused
         if (timed && tid == 0) { uint64_t t = clock64(); ph[5] += t - tp; tp = t; }
     }
+    cluster.sync();   // no CTA leaves while its shared memory may still be written
 
     if constexpr (RES) {
         for (int r = tid; r < nseg; r += kThreads) {
@@ -813,7 +872,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         c->row_visits = row_visits;
         c->exit_reason = exit_reason;
         c->shrink_events = shrink_events;
-        for (int k = 0; k < 6; ++k) c->phase_cycles[k] += ph[k];
+        for (int k = 0; k < 8; ++k) c->phase_cycles[k] += ph[k];
     }
 }
 
@@ -832,22 +891,60 @@ void *kernel_for(int lpr)
 }
 
 template <int MODE>
-cudaError_t launch_mode(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st)
+cudaError_t launch_mode(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st, int cs)
 {
     void *fn = a.resident ? kernel_for<MODE, true>(lpr) : kernel_for<MODE, false>(lpr);
     if (!fn) return cudaErrorInvalidValue;
+    if (cs < 1 || a.G % cs != 0 || a.G / cs > 256 || cs > 8) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (per_sm < 1 || a.G > per_sm * sms || a.G > 256) return cudaErrorCooperativeLaunchTooLarge;
     SmoArgs args = a;
     void *params[] = {&args};
-    return cudaLaunchCooperativeKernel(fn, dim3(a.G), dim3(kThreads), params, smem, st);
+    cudaLaunchAttribute attrs[2];
+    attrs[0].id = cudaLaunchAttributeCooperative;
+    attrs[0].val.cooperative = 1;
+    attrs[1].id = cudaLaunchAttributeClusterDimension;
+    attrs[1].val.clusterDim.x = (unsigned)cs;
+    attrs[1].val.clusterDim.y = 1;
+    attrs[1].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.G);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attrs;
+    cfg.numAttrs = 2;
+    // all CTAs must be resident at once (they wait on one another)
+    int nclusters = 0;
+    cudaLaunchConfig_t q = cfg;
+    q.attrs = attrs + 1;
+    q.numAttrs = 1;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, fn, &q);
+    if (e != cudaSuccess) return e;
+    if (nclusters * cs < a.G) return cudaErrorCooperativeLaunchTooLarge;
+    return cudaLaunchKernelExC(&cfg, fn, params);
+}
+
+template <int MODE>
+int max_clusters(int lpr, int resident, size_t smem, int cs)
+{
+    void *fn = resident ? kernel_for<MODE, true>(lpr) : kernel_for<MODE, false>(lpr);
+    if (!fn) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)cs;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cudaLaunchConfig_t q = {};
+    q.gridDim = dim3(cs);
+    q.blockDim = dim3(kThreads);
+    q.dynamicSmemBytes = smem;
+    q.attrs = &attr;
+    q.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &q) != cudaSuccess) return 0;
+    return n;
 }
 
 }  // namespace smo

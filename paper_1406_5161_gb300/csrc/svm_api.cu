@@ -497,12 +497,32 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     }
     // lanes per row from the mean row length; one CTA per SM
     double avg = (double)D.nnz / (double)n;
+    // one thread per row up to 32 stored entries (the f updates then run on
+    // full warps of the weak FP64 pipe), more lanes for longer rows
     int lpr = 1;
-    while (lpr < 32 && lpr * 4 < avg) lpr <<= 1;
+    while (lpr < 32 && lpr * 32 < avg) lpr <<= 1;
+    if (P->lanes_per_row > 0) {
+        lpr = 1;
+        while (lpr < 32 && lpr < P->lanes_per_row) lpr <<= 1;
+    }
     const int sms = device_sms();
     int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 15) / 16));
     if (P->ctas > 0) G = (int)std::min<int64_t>(std::min<int64_t>(P->ctas, sms), n);
     if (G > 256) G = 256;
+    const int kt = mode == MODE_BINARY ? ktab_len : 0;
+    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
+    // thread-block clusters of 8 CTAs for the hierarchical exchange
+    int cs = 1;
+    {
+        const SmoLayout L0 = smo_layout(mode, (int)D.d, kt, D.maxnnz, 0, 0, 0);
+        if ((P->flags & SVM_FLAG_NO_CLUSTERS) == 0 && G >= 16 && L0.total <= lim_dyn) {
+            const int maxc = smo_max_clusters(mode, lpr, 0, L0.total, 8);
+            if (maxc >= 2) {
+                cs = 8;
+                G = 8 * std::min(maxc, G / 8);
+            }
+        }
+    }
     // segment sizes decide whether the rows stay in shared memory
     int64_t *segnnz_d = ar.alloc<int64_t>(G);
     k_seg_nnz<<<grid1(G), 256, 0, st>>>(n, G, D.indptr, segnnz_d);
@@ -514,12 +534,11 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     int64_t seg_nnz_max = 0;
     for (int64_t v : segnnz) seg_nnz_max = std::max(seg_nnz_max, v);
     const int seg_rows_max = (int)((n + G - 1) / G);
-    const int kt = mode == MODE_BINARY ? ktab_len : 0;
-    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
     const SmoLayout Ls = smo_layout(mode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max, seg_nnz_max);
     const SmoLayout Lr = smo_layout(mode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max, seg_nnz_max);
     int resident = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 && seg_nnz_max < ((int64_t)1 << 31) &&
                    Lr.total <= lim_dyn;
+    if (resident && cs > 1 && smo_max_clusters(mode, lpr, 1, Lr.total, cs) * cs < G) resident = 0;
     const size_t smem = resident ? Lr.total : Ls.total;
     if (smem > lim_dyn) {
         set_err("d = %lld exceeds the shared-memory target rows of this mode", (long long)D.d);
@@ -616,7 +635,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         A.iter_limit = limit;
         A.select_only = select_only;
         CK(cudaEventRecord(e0, st));
-        CK(launch_smo_persistent(mode, lpr, A, smem, st));
+        CK(launch_smo_persistent(mode, lpr, A, smem, st, cs));
         CK(cudaEventRecord(e1, st));
         ++launches;
         CK(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));
@@ -752,11 +771,12 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         stats->binary_input = mode == MODE_BINARY;
         stats->resident = resident;
         stats->ctas = G;
+        stats->cluster_size = cs;
         stats->lanes_per_row = lpr;
         int dev = 0, khz = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-        for (int k = 0; k < 6; ++k) stats->phase_ms[k] = khz > 0 ? (double)hc.phase_cycles[k] / (double)khz : 0.0;
+        for (int k = 0; k < 8; ++k) stats->phase_ms[k] = khz > 0 ? (double)hc.phase_cycles[k] / (double)khz : 0.0;
         stats->cta_busy_ms_min = stats->cta_busy_ms_max = 0.0;
         if (cta_cycles && khz > 0) {
             std::vector<int64_t> cc(G);

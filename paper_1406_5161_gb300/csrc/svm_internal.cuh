@@ -37,9 +37,9 @@ struct SmoCtrl {
     int64_t shrink_events;
     // SM cycles spent by CTA 0 in each phase of a step (summed over steps,
     // recorded only when SmoArgs::phase_times is set):
-    // 0 target rows, 1 pair step, 2 row pass + CTA reduction, 3 publish,
-    // 4 grid exchange, 5 other
-    int64_t phase_cycles[6];
+    // 0 target rows, 1 pair step (FP64 part), 2 row pass + CTA reduction,
+    // 3 publish, 4 grid exchange, 5 other, 6 pair step (K(up,low) part)
+    int64_t phase_cycles[8];
 };
 
 // Kernel arguments. Sample indices in the active lists are local to their
@@ -117,8 +117,11 @@ __host__ __device__ __forceinline__ int64_t seg_lo(int64_t n, int G, int s)
 
 // ---------------------------------------------------------------- launchers
 // (each returns a cudaError_t; kernels live in their own translation units)
+// cs = CTAs per thread-block cluster (1 or 8); G must be a multiple of cs
 cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int cs);
+// clusters of cs CTAs that can be resident at once (0 on error)
+int smo_max_clusters(int mode, int lpr, int resident, size_t smem, int cs);
 size_t smo_cand_bytes();
 size_t smo_static_smem();
 int smo_threads();
