@@ -193,6 +193,38 @@ int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double 
                  double gamma, const svm_csr *Z, int32_t precision, void *stream,
                  double *out);
 
+/*
+ * svm_train_fixed_workspace -- the plain solve of svm_train (no shrinking,
+ * SVM_FP64) without any device allocation. The paper has no counterpart to
+ * this call; it exists for callers that cannot allocate device memory while
+ * they train: code that runs inside a memory pool capped or owned by someone
+ * else, a latency-bound loop that must not wait on the allocator, or a
+ * process that reserved the whole device before it started.
+ *
+ * All scratch (gradient, index sets, active lists, exchange slots, tables,
+ * reductions) lives in one 4 MiB array that the library reserves in every
+ * GPU's memory when it is loaded and keeps until the process exits. The
+ * caller passes the inputs and the output buffer in device memory:
+ *   X         device CSR (X->on_device must be 1), 2 <= n <= 131072 rows,
+ *             at most 4096 entries in a row
+ *   y         n device labels (+1 / -1)
+ *   params    C, gamma, tau, max_iter, stream; precision must be SVM_FP64;
+ *             trace, flags, ctas and lanes_per_row are ignored
+ *   alpha_out n doubles of device memory, written with the multipliers
+ *   b_out     host double; iters_out host int64 (may be NULL)
+ * Larger problems return SVM_ERR_UNSUPPORTED with a message naming the
+ * limit; other results are those of svm_train.
+ *
+ * The first call on each device looks up the device address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array and starts by re-initialising the parts it
+ * reads, so consecutive calls are independent; calls whose device work
+ * overlaps (two host threads, or two streams) race on the array and must
+ * not be issued.
+ */
+int svm_train_fixed_workspace(const svm_csr *X, const int8_t *y, const svm_params *params,
+                              double *alpha_out, double *b_out, int64_t *iters_out);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all calls), for accounting of device work. */
 int64_t svm_kernel_launches(void);

@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True):
             lib.svm_version.argtypes = []
             lib.svm_kernel_launches.restype = ct.c_int64
             lib.svm_kernel_launches.argtypes = []
+            lib.svm_train_fixed_workspace.restype = ct.c_int
+            lib.svm_train_fixed_workspace.argtypes = [P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -253,3 +255,28 @@ def svm_decision(X, y, alpha, b: float, gamma: float, Z, *, precision: int = SVM
     if check and rc < 0:
         raise SvmError(rc, svm_last_error())
     return out
+
+
+def svm_train_fixed_workspace(X, y, C: float, gamma: float, tau: float = 1e-3, *,
+                              max_iter: int = 0, stream=None, alpha_out=None,
+                              check: bool = True) -> dict:
+    """Plain FP64 solve that allocates no device memory (see the header for
+    who needs it and its limits). X, y and alpha_out are device buffers."""
+    import torch
+    lib = load()
+    h = _Hold()
+    cx, dev = _csr(h, X)
+    if not dev:
+        raise ValueError("svm_train_fixed_workspace takes a DeviceCSR")
+    yp = h.tensor(y, "int8")
+    if alpha_out is None:
+        alpha_out = torch.empty(int(X.n), dtype=torch.float64, device=X.indptr.device)
+    p = svm_params(float(C), float(gamma), float(tau), int(max_iter), SVM_FP64, 0,
+                   _stream_ptr(stream), None, 0, 0, 0, 0, 0)
+    b = ct.c_double(0.0)
+    it = ct.c_int64(0)
+    rc = lib.svm_train_fixed_workspace(ct.byref(cx), yp, ct.byref(p), alpha_out.data_ptr(),
+                                       ct.byref(b), ct.byref(it))
+    if check and rc < 0:
+        raise SvmError(rc, svm_last_error())
+    return {"status": rc, "alpha": alpha_out, "b": b.value, "iters": it.value}

@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -881,6 +882,216 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     return SVM_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Fixed-workspace training: a variant of the plain (no shrinking) FP64 solve
+// that allocates nothing. Some callers cannot allocate device memory during
+// a call: code running inside a memory-capped or externally managed pool, a
+// real-time loop that must not block on the allocator, or a host that
+// reserved the whole device up front. For them every piece of scratch the
+// solve needs lives in one file-scope device array that the library reserves
+// when it is loaded; inputs and outputs are the caller's device buffers.
+// ---------------------------------------------------------------------------
+constexpr int64_t kFixedMaxRows = 131072;            // largest n accepted
+constexpr int kFixedMaxRowNnz = 4096;                // longest row accepted
+constexpr size_t kFixedScratchBytes = (size_t)4 << 20;   // 4 MiB per device
+
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
+
+// Device address of g_fixed_scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_fixed_mu;
+void *g_fixed_addr[kMaxDevices] = {};
+
+void *fixed_scratch_address()
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_err("device index %d out of range for the fixed workspace", dev);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+    std::lock_guard<std::mutex> lk(g_fixed_mu);
+    if (!g_fixed_addr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_fixed_scratch);
+        if (e != cudaSuccess || !ptr) {
+            set_err("cudaGetSymbolAddress of the fixed workspace failed: %s", cudaGetErrorString(e));
+            throw Fail{SVM_ERR_CUDA};
+        }
+        g_fixed_addr[dev] = ptr;
+    }
+    return g_fixed_addr[dev];
+}
+
+// Carves aligned pieces out of the fixed workspace.
+struct FixedCarve {
+    unsigned char *base;
+    size_t used = 0;
+    template <class T>
+    T *take(size_t count)
+    {
+        size_t off = (used + 255) & ~(size_t)255;
+        size_t bytes = (count ? count : 1) * sizeof(T);
+        if (off + bytes > kFixedScratchBytes) {
+            set_err("problem needs more than the %zu-byte fixed workspace", kFixedScratchBytes);
+            throw Fail{SVM_ERR_UNSUPPORTED};
+        }
+        used = off + bytes;
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, double *alpha_out,
+                     double *b_out, int64_t *iters_out)
+{
+    if (!X || !P || !y || !alpha_out || !b_out) ARG_FAIL("NULL argument");
+    if (!X->on_device) ARG_FAIL("the fixed-workspace call takes device buffers only (on_device = 1)");
+    if (!(P->C > 0) || !std::isfinite(P->C)) ARG_FAIL("C must be > 0");
+    if (!(P->gamma > 0) || !std::isfinite(P->gamma)) ARG_FAIL("gamma must be > 0");
+    if (!(P->tau > 0) || !std::isfinite(P->tau)) ARG_FAIL("tau must be > 0");
+    if (P->precision != SVM_FP64) ARG_FAIL("the fixed-workspace call supports SVM_FP64 only");
+    if (P->tie_break != 0) ARG_FAIL("only the lowest-index tie-break (0) is implemented");
+    if (X->n < 2 || X->d < 1) ARG_FAIL("need n >= 2 and d >= 1");
+    if (X->n > kFixedMaxRows) {
+        set_err("n = %lld exceeds the fixed workspace limit of %lld rows", (long long)X->n,
+                (long long)kFixedMaxRows);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+    if (!X->indptr || !X->indices) ARG_FAIL("indptr/indices must not be NULL");
+    cudaStream_t st = as_stream(P->stream);
+    FixedCarve W{static_cast<unsigned char *>(fixed_scratch_address())};
+    const int64_t n = X->n;
+    int launches = 0;
+
+    // ingest checks (device buffers are read in place)
+    IngestInfo *info = W.take<IngestInfo>(1);
+    CK(cudaMemsetAsync(info, 0, sizeof(IngestInfo), st));
+    k_validate<<<grid1(n), 256, 0, st>>>(n, X->d, X->indptr, X->indices, X->values, y, info);
+    CK(cudaGetLastError());
+    ++launches;
+    IngestInfo h;
+    int64_t nnz = 0;
+    CK(cudaMemcpyAsync(&h, info, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&nnz, X->indptr + n, sizeof nnz, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h.bad_indptr) ARG_FAIL("indptr is not non-decreasing from 0");
+    if (h.bad_index) ARG_FAIL("column indices must be strictly increasing within a row and < d");
+    if (h.nonfinite) ARG_FAIL("values must be finite");
+    if (h.bad_y) ARG_FAIL("labels must be +1 or -1");
+    if (h.npos == 0 || (int64_t)h.npos == n) ARG_FAIL("both classes must be present");
+    if (h.maxnnz > kFixedMaxRowNnz) {
+        set_err("a row has %d entries; the fixed workspace accepts at most %d", h.maxnnz, kFixedMaxRowNnz);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+    const bool binary = !h.not_binary;
+    const int mode = binary ? MODE_BINARY : MODE_FP64;
+    const int ktab_len = 2 * h.maxnnz + 1;
+    double *norm = nullptr, *ktab = nullptr;
+    if (binary) {
+        ktab = W.take<double>(2 * (size_t)ktab_len);
+        k_ktab<<<grid1(ktab_len), 256, 0, st>>>(P->gamma, ktab_len, ktab);
+    } else {
+        norm = W.take<double>(n);
+        k_norms<<<grid1(n), 256, 0, st>>>(n, X->indptr, X->values, norm, nullptr, nullptr);
+    }
+    CK(cudaGetLastError());
+    ++launches;
+
+    // launch shape: the same rules as svm_train, rows streamed from global
+    const double avg = (double)nnz / (double)n;
+    int lpr = 1;
+    while (lpr < 32 && lpr * 32 < avg) lpr <<= 1;
+    const int sms = device_sms();
+    int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 15) / 16));
+    if (G > 256) G = 256;
+    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
+    const SmoLayout L0 = smo_layout(mode, (int)X->d, binary ? ktab_len : 0, h.maxnnz, 0, 0, 0);
+    if (L0.total > lim_dyn) {
+        set_err("d = %lld exceeds the shared-memory target rows of this mode", (long long)X->d);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+    int cs = 1;
+    if (G >= 16) {
+        const int maxc = smo_max_clusters(mode, lpr, 0, L0.total, 8);
+        if (maxc >= 2) {
+            cs = 8;
+            G = 8 * std::min(maxc, G / 8);
+        }
+    }
+
+    // solver state: alpha lives in the caller's output buffer
+    double *f = W.take<double>(n);
+    uint8_t *status = W.take<uint8_t>(n);
+    int32_t *act = W.take<int32_t>(n);
+    int32_t *seg_cnt = W.take<int32_t>(G);
+    void *cand = W.take<unsigned char>(2 * (size_t)G * smo_cand_bytes());
+    unsigned *seq = W.take<unsigned>(2 * (size_t)G);
+    SmoCtrl *ctrl = W.take<SmoCtrl>(1);
+    const int nbf = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 4095) / 4096));
+    FinishPart *parts = W.take<FinishPart>(nbf);
+    FinishPart *tot = W.take<FinishPart>(1);
+    k_init<<<grid1(n), 256, 0, st>>>(n, y, alpha_out, f, status);
+    k_reset_active<<<G, 256, 0, st>>>(n, G, act, seg_cnt);
+    CK(cudaGetLastError());
+    launches += 2;
+
+    SmoCtrl hc;
+    std::memset(&hc, 0, sizeof hc);
+    hc.active = n;
+    hc.i_up = hc.i_low = -1;
+    SmoArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.n = n;
+    A.d = (int32_t)X->d;
+    A.G = G;
+    A.indptr = X->indptr;
+    A.indices = X->indices;
+    A.values = X->values;
+    A.y = y;
+    A.norm = norm;
+    A.alpha = alpha_out;
+    A.f = f;
+    A.status = status;
+    A.act = act;
+    A.seg_cnt = seg_cnt;
+    A.cand = cand;
+    A.seq = seq;
+    A.ctrl = ctrl;
+    A.ktab = ktab;
+    A.ktab_len = ktab_len;
+    A.maxnnz = h.maxnnz;
+    A.resident = 0;
+    A.C = P->C;
+    A.gamma = P->gamma;
+    A.thr = 2.0 * P->tau;
+    A.iter_limit = P->max_iter > 0 ? P->max_iter : 100 * n + 1000000;
+    A.h = 0;
+    A.select_only = 1;
+    A.timeout_ns = 10ll * 1000 * 1000 * 1000;
+    // every call starts from a zeroed exchange area and a fresh control block
+    CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(seq, 0, 2 * sizeof(unsigned) * G, st));
+    CK(launch_smo_persistent(mode, lpr, A, L0.total, st, cs));
+    ++launches;
+    CK(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));
+    k_finish_part<<<nbf, kCT, 0, st>>>(n, P->C, alpha_out, f, status, parts);
+    k_finish_total<<<1, 32, 0, st>>>(parts, nbf, tot);
+    CK(cudaGetLastError());
+    launches += 2;
+    FinishPart fp;
+    CK(cudaMemcpyAsync(&fp, tot, sizeof fp, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    g_launches += launches;
+    if (hc.err) {
+        set_err("a grid-wide wait in the SMO kernel exceeded its time limit");
+        throw Fail{SVM_ERR_TIMEOUT};
+    }
+    *b_out = fp.n0 > 0 ? fp.sum_f0 / (double)fp.n0 : 0.5 * (hc.b_up + hc.b_low);
+    if (iters_out) *iters_out = hc.iter;
+    return hc.exit_reason == 1 ? SVM_NOT_CONVERGED : SVM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -918,6 +1129,20 @@ int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double 
 const char *svm_last_error(void) { return g_err.c_str(); }
 
 int64_t svm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int svm_train_fixed_workspace(const svm_csr *X, const int8_t *y, const svm_params *params,
+                              double *alpha_out, double *b_out, int64_t *iters_out)
+{
+    g_err.clear();
+    try {
+        return train_fixed_impl(X, y, params, alpha_out, b_out, iters_out);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
 
 const char *svm_version(void) { return "svm_gb300 0.1 (sm_103a)"; }
 
