@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--policy", default="Multi5pc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="cap SMO steps per solve (profiling of small cases; not a bench value)")
     return ap.parse_args()
 
 
@@ -216,7 +218,8 @@ def run_gb300(args, rank, world, local):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def step():
-        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream)
+        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream,
+                          max_iter=args.max_iter)
         dz = pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
         return r, dz
 
@@ -239,7 +242,8 @@ def run_gb300(args, rank, world, local):
     for k in range(args.steps):
         flush.zero_()                    # L2 flushed between timed steps
         e0[k].record(stream)
-        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream)
+        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream,
+                          max_iter=args.max_iter)
         e1[k].record(stream)
         pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
         e2[k].record(stream)
@@ -286,7 +290,8 @@ def run_gb300(args, rank, world, local):
         e2e_iters = 0
         n_e2e = max(1, min(3, args.steps))
         for _ in range(n_e2e):
-            r = pkg.svm_train(Xh, yh, p.C, p.gamma, p.tau, shrink=policy, alpha_out=alpha_h)
+            r = pkg.svm_train(Xh, yh, p.C, p.gamma, p.tau, shrink=policy, alpha_out=alpha_h,
+                              max_iter=args.max_iter)
             pkg.svm_decision(Xh, yh, alpha_h, r["b"], p.gamma, Zh, out=out_h)
             e2e_iters += r["iters"]
         dt = time.perf_counter() - t0
@@ -327,6 +332,8 @@ def run_gb300(args, rank, world, local):
             "recon_ms_per_step": ms_recon / args.steps,
             "gpu_launches": int(launches),
             "clocks": clk, "roofline": roofline, "e2e": e2e}
+    if args.max_iter:
+        line["config"]["max_iter"] = args.max_iter
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)
