@@ -61,8 +61,13 @@ enum svm_precision {
     SVM_FP64 = 0,
     /* Inner products and exp in FP32 on BF16-rounded feature values (the
      * reconstruction and decision contractions on the tcgen05 tensor cores
-     * with FP32 accumulation); f, the pair step, b and the gap stay FP64. */
-    SVM_MIXED_BF16 = 1
+     * with FP32 accumulation, for d <= 256); f, the pair step, b and the gap
+     * stay FP64. */
+    SVM_MIXED_BF16 = 1,
+    /* The arithmetic of SVM_MIXED_BF16 with the contractions on the CUDA
+     * cores instead of the tensor cores (a reference for the tensor-core
+     * path, and the path used for d > 256). */
+    SVM_MIXED_BF16_SIMT = 2
 };
 
 /* ----------------------------------------------------------- shrinking */

@@ -19,7 +19,7 @@ from . import build as _build
 SVM_OK, SVM_NOT_CONVERGED, SVM_PENDING = 0, 1, 2
 SVM_ERR_ARG, SVM_ERR_OOM, SVM_ERR_BUDGET, SVM_ERR_TIMEOUT = -1, -2, -3, -4
 SVM_ERR_CUDA, SVM_ERR_CANCELLED, SVM_ERR_UNSUPPORTED = -5, -6, -7
-SVM_FP64, SVM_MIXED_BF16 = 0, 1
+SVM_FP64, SVM_MIXED_BF16, SVM_MIXED_BF16_SIMT = 0, 1, 2
 SVM_SHRINK_NONE, SVM_SHRINK_FIXED, SVM_SHRINK_FRACTION = 0, 1, 2
 SVM_RECON_SINGLE, SVM_RECON_MULTI = 0, 1
 SVM_FLAG_STREAM_ROWS = 1

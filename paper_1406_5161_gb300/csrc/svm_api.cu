@@ -463,7 +463,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     if (!(P->C > 0) || !std::isfinite(P->C)) ARG_FAIL("C must be > 0");
     if (!(P->gamma > 0) || !std::isfinite(P->gamma)) ARG_FAIL("gamma must be > 0");
     if (!(P->tau > 0) || !std::isfinite(P->tau)) ARG_FAIL("tau must be > 0");
-    if (P->precision != SVM_FP64 && P->precision != SVM_MIXED_BF16) ARG_FAIL("unknown precision %d", P->precision);
+    if (P->precision < SVM_FP64 || P->precision > SVM_MIXED_BF16_SIMT) ARG_FAIL("unknown precision %d", P->precision);
     if (P->tie_break != 0) ARG_FAIL("only the lowest-index tie-break (0) is implemented");
     if (X && X->n < 2) ARG_FAIL("need at least two samples");
     svm_shrink_policy none = {SVM_SHRINK_NONE, SVM_RECON_SINGLE, 0.0, 20.0};
@@ -475,7 +475,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     int launches = 0;
     Arena ar(st);
     DevCSR D;
-    const bool mixed = P->precision == SVM_MIXED_BF16;
+    const bool mixed = P->precision != SVM_FP64;
+    const bool use_tc = P->precision == SVM_MIXED_BF16;
     ingest(ar, X, y, !mixed, mixed, st, D, &launches);
     const int64_t n = D.n;
     if (D.npos == 0 || D.npos == n) ARG_FAIL("both classes must be present");
@@ -705,8 +706,20 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             c.out = f;
             c.yq = D.y;
             c.add_scalar = 0.0;
-            CK(launch_rbf_contract(c, st));
-            ++launches;
+            if (use_tc && mode == MODE_MIXED && nsv > 0 && tc_rbf_supported((int)D.d)) {
+                void *ws = ar.alloc<unsigned char>(tc_rbf_workspace_bytes(nw, nsv, (int)D.d));
+                int tc_err = 0;
+                CK(launch_rbf_contract_tc(c, ws, &tc_err, st));
+                launches += 3;
+                CK(cudaStreamSynchronize(st));
+                if (tc_err) {
+                    set_err("a wait in the tensor-core reconstruction exceeded its limit");
+                    throw Fail{SVM_ERR_TIMEOUT};
+                }
+            } else {
+                CK(launch_rbf_contract(c, st));
+                ++launches;
+            }
             CK(cudaEventRecord(e1, st));
             CK(cudaStreamSynchronize(st));
             float ms = 0.f;
@@ -800,12 +813,12 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     if (!X || !Z || !y || !alpha || !out) ARG_FAIL("NULL argument");
     if (!(gamma > 0)) ARG_FAIL("gamma must be > 0");
     if (Z->d != X->d) ARG_FAIL("Z->d (%lld) must equal X->d (%lld)", (long long)Z->d, (long long)X->d);
-    if (precision != SVM_FP64 && precision != SVM_MIXED_BF16) ARG_FAIL("unknown precision %d", precision);
+    if (precision < SVM_FP64 || precision > SVM_MIXED_BF16_SIMT) ARG_FAIL("unknown precision %d", precision);
     if (Z->n == 0) return SVM_OK;
     cudaStream_t st = as_stream(stream);
     int launches = 0;
     Arena ar(st);
-    const bool mixed = precision == SVM_MIXED_BF16;
+    const bool mixed = precision != SVM_FP64;
     DevCSR DX, DZ;
     ingest(ar, X, y, !mixed, mixed, st, DX, &launches);
     ingest(ar, Z, nullptr, !mixed, mixed, st, DZ, &launches);
@@ -874,8 +887,20 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     c.out = out_d;
     c.yq = nullptr;
     c.add_scalar = -b;
-    CK(launch_rbf_contract(c, st));
-    ++launches;
+    if (precision == SVM_MIXED_BF16 && mode == MODE_MIXED && nsv > 0 && tc_rbf_supported((int)DX.d)) {
+        void *ws = ar.alloc<unsigned char>(tc_rbf_workspace_bytes(DZ.n, nsv, (int)DX.d));
+        int tc_err = 0;
+        CK(launch_rbf_contract_tc(c, ws, &tc_err, st));
+        launches += 3;
+        CK(cudaStreamSynchronize(st));
+        if (tc_err) {
+            set_err("a wait in the tensor-core decision kernel exceeded its limit");
+            throw Fail{SVM_ERR_TIMEOUT};
+        }
+    } else {
+        CK(launch_rbf_contract(c, st));
+        ++launches;
+    }
     g_launches += launches;
     if (!Z->on_device) CK(cudaMemcpyAsync(out, out_d, sizeof(double) * DZ.n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -160,4 +160,11 @@ struct RbfContract {
 };
 cudaError_t launch_rbf_contract(const RbfContract &c, cudaStream_t st);
 
+// Tensor-core (tcgen05) version for MODE_MIXED inputs; d <= 256. `ws` holds
+// tc_rbf_workspace_bytes(nq, nsv, d); *err_host is written asynchronously (1
+// when a wait inside the kernel gave up) and is valid after a stream sync.
+bool tc_rbf_supported(int d);
+size_t tc_rbf_workspace_bytes(int64_t nq, int64_t nsv, int d);
+cudaError_t launch_rbf_contract_tc(const RbfContract &c, void *ws, int *err_host, cudaStream_t st);
+
 }  // namespace svmgb

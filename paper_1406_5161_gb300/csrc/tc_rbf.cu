@@ -1,0 +1,406 @@
+// RBF contraction on the 5th-generation tensor cores (tcgen05, sm_103a):
+//
+//   out[q] = sum_k coef_k * exp(-gamma * (||z_q||^2 + ||x_k||^2 - 2 <z_q, x_k>))
+//
+// the inner loop of gradient reconstruction (Algorithm 6: f of the shrunk
+// samples from all alpha > 0) and of the decision function (Eq. classi) in
+// the mixed-precision mode. The inner products are a dense contraction: query
+// rows and support vectors are densified once into BF16 row-major matrices
+// (K = columns padded to 64), a CTA keeps a 128-row query tile in shared
+// memory and streams 128-row support-vector tiles with TMA (128-byte
+// swizzle); one thread issues tcgen05.mma (M = N = 128, K = 16, BF16 inputs,
+// FP32 accumulators in tensor memory); the four warps then read the
+// 128 x 128 FP32 tile from tensor memory (tcgen05.ld), apply the exp
+// epilogue and accumulate coef * K per query row (FP32 within a tile, FP64
+// across tiles). Padding rows carry coef = 0.
+//
+// All waits on mbarriers are bounded; on expiry the CTA records an error,
+// waits (bounded) for its own asynchronous work, frees its tensor memory and
+// returns, and the host reports SVM_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "svm_internal.cuh"
+
+namespace svmgb {
+namespace {
+
+constexpr int kTile = 128;            // rows per query tile and per SV tile (M = N)
+constexpr int kKB = 64;               // BF16 elements per 128-byte swizzle row
+constexpr int kTcThreads = 128;       // 4 warps: one TMEM lane quadrant each
+constexpr int kMaxKBlocks = 4;        // d_pad <= 256
+constexpr uint32_t kTileBytes = kTile * kKB * 2;   // 16 KiB per k-block tile
+constexpr long long kWaitLimit = 1ll << 26;        // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// true when the phase with the given parity completed; bounded
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
+// of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: 8-row group
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // swizzle: 128-byte
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both
+// K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4)                  // D format F32
+                            | (1u << 7)                // A format BF16
+                            | (1u << 10)               // B format BF16
+                            | ((uint32_t)(kTile >> 3) << 17)   // N / 8
+                            | ((uint32_t)(kTile >> 4) << 24);  // M / 16
+
+struct TcArgs {
+    int64_t nq, nsv;
+    int kblocks;                 // d_pad / 64
+    const float *zc;             // per query: -gamma * log2(e) * ||z||^2
+    const float *xc;             // per SV (padded): -gamma * log2(e) * ||x||^2
+    const float *coef;           // per SV (padded): alpha * y (0 on padding)
+    float g2;                    // 2 * gamma * log2(e)
+    const int32_t *qrow;         // output index per query (row id or position)
+    const int8_t *yq;            // subtract yq[qrow] when non-NULL
+    double add_scalar;
+    double *out;
+    int *err;
+};
+
+__global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constant__ CUtensorMap mapZ,
+                                                            const __grid_constant__ CUtensorMap mapX,
+                                                            TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    // 1024-byte alignment for the swizzled tiles
+    unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *tileA = dsm;                                   // [kblocks][16 KiB]
+    unsigned char *tileB = dsm + (size_t)a.kblocks * kTileBytes;  // [kblocks][16 KiB]
+    __shared__ __align__(8) uint64_t bar_load, bar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ float s_xc[kTile], s_coef[kTile];
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t q0 = (int64_t)blockIdx.x * kTile;
+    if (tid == 0) {
+        mbar_init(&bar_load, 1);
+        mbar_init(&bar_mma, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(kTile) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    // query tile (all k-blocks) stays in shared memory
+    uint32_t ph_load = 0, ph_mma = 0;
+    if (tid == 0) {
+        mbar_expect_tx(&bar_load, (uint32_t)a.kblocks * kTileBytes);
+        for (int kb = 0; kb < a.kblocks; ++kb)
+            tma_load_2d(tileA + (size_t)kb * kTileBytes, &mapZ, kb * kKB, (int)q0, &bar_load);
+    }
+    bool ok = __syncthreads_and(mbar_wait(&bar_load, ph_load)) != 0;   // uniform decision
+    ph_load ^= 1;
+
+    const int my_row = warp * 32 + lane;                 // TMEM lane = query row in tile
+    const int64_t q = q0 + my_row;
+    const float zc = (q < a.nq) ? a.zc[q] : 0.f;
+    double acc = 0.0;
+    const int64_t ntiles = (a.nsv + kTile - 1) / kTile;
+    for (int64_t t = 0; t < ntiles && ok; ++t) {
+        // stage the per-SV constants of this tile; load the SV tile
+        for (int j = tid; j < kTile; j += kTcThreads) {
+            s_xc[j] = a.xc[t * kTile + j];
+            s_coef[j] = a.coef[t * kTile + j];
+        }
+        if (tid == 0) {
+            mbar_expect_tx(&bar_load, (uint32_t)a.kblocks * kTileBytes);
+            for (int kb = 0; kb < a.kblocks; ++kb)
+                tma_load_2d(tileB + (size_t)kb * kTileBytes, &mapX, kb * kKB, (int)(t * kTile), &bar_load);
+        }
+        ok = __syncthreads_and(mbar_wait(&bar_load, ph_load)) != 0;   // also publishes s_xc / s_coef
+        ph_load ^= 1;
+        if (!ok) break;
+        // one thread issues the MMAs: D = Z_tile * X_tile^T over all K
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int kb = 0; kb < a.kblocks; ++kb) {
+                const uint32_t sa = smem_u32(tileA + (size_t)kb * kTileBytes);
+                const uint32_t sb = smem_u32(tileB + (size_t)kb * kTileBytes);
+#pragma unroll
+                for (int ks = 0; ks < kKB / 16; ++ks) {
+                    const uint64_t da = smem_desc_sw128(sa + ks * 32);
+                    const uint64_t db = smem_desc_sw128(sb + ks * 32);
+                    const uint32_t accum = (kb | ks) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                        ::"r"(tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&bar_mma)) : "memory");
+        }
+        ok = __syncthreads_and(mbar_wait(&bar_mma, ph_mma)) != 0;
+        ph_mma ^= 1;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: this thread's row, 32 columns at a time
+        float part = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTile; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                  "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                  "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                  "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(addr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                // log2 K = -gamma log2(e) (||z||^2 + ||x||^2 - 2 <z, x>), clamped at 0
+                const float e = fminf(fmaf(__uint_as_float(r[j]), a.g2, zc + s_xc[c0 + j]), 0.f);
+                part = fmaf(s_coef[c0 + j], exp2f(e), part);
+            }
+        }
+        acc += (double)part;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();   // tile B and tensor memory free for the next tile
+    }
+    if (!ok && tid == 0) {
+        s_fail = 1;
+        atomicExch(a.err, 1);
+    }
+    __syncthreads();
+    if (s_fail) {
+        // let any outstanding MMA of this CTA finish before freeing its memory
+        if (tid == 0) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&bar_mma)) : "memory");
+        }
+        (void)mbar_wait(&bar_mma, ph_mma);
+    } else if (q < a.nq) {
+        const int32_t row = a.qrow[q];
+        double v = acc + a.add_scalar;
+        if (a.yq) v -= (double)a.yq[row];
+        a.out[row] = v;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------- preparation
+
+// Dense BF16 rows (row-major, ld = d_pad) from CSR rows (list or all) and the
+// scaled norms used by the epilogue; padding rows are zero.
+__global__ void k_densify(int64_t nrows, int64_t nrows_pad, int d_pad, const int32_t *list,
+                          const int64_t *indptr, const int32_t *indices, const float *vmix,
+                          const float *normf, float nscale, __nv_bfloat16 *dense, float *cnorm,
+                          const double *coef_in, float *coef_out, int32_t *outrow, int out_by_row)
+{
+    const int64_t r = blockIdx.x;
+    if (r >= nrows_pad) return;
+    __nv_bfloat16 *dst = dense + (size_t)r * d_pad;
+    for (int c = threadIdx.x; c < d_pad; c += blockDim.x) dst[c] = __float2bfloat16_rn(0.f);
+    __syncthreads();
+    if (r < nrows) {
+        const int64_t row = list ? list[r] : r;
+        for (int64_t p = indptr[row] + threadIdx.x; p < indptr[row + 1]; p += blockDim.x)
+            dst[indices[p]] = __float2bfloat16_rn(vmix[p]);
+        if (threadIdx.x == 0) {
+            cnorm[r] = nscale * normf[row];
+            if (coef_out) coef_out[r] = (float)coef_in[r];
+            if (outrow) outrow[r] = out_by_row ? (int32_t)row : (int32_t)r;
+        }
+    } else if (threadIdx.x == 0) {
+        cnorm[r] = 0.f;
+        if (coef_out) coef_out[r] = 0.f;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, int64_t rows, int d_pad)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)d_pad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)d_pad * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)kTile};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_rbf_supported(int d) { return d >= 1 && d <= kMaxKBlocks * kKB && encode_fn() != nullptr; }
+
+size_t tc_rbf_workspace_bytes(int64_t nq, int64_t nsv, int d)
+{
+    const int d_pad = ((d + kKB - 1) / kKB) * kKB;
+    const int64_t nq_pad = (nq + kTile - 1) / kTile * kTile;
+    const int64_t ns_pad = (nsv + kTile - 1) / kTile * kTile;
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
+    add((size_t)nq_pad * d_pad * 2);
+    add((size_t)ns_pad * d_pad * 2);
+    add((size_t)nq_pad * 4);   // zc
+    add((size_t)ns_pad * 4);   // xc
+    add((size_t)ns_pad * 4);   // coef
+    add((size_t)nq_pad * 4);   // qrow
+    add(256);                  // err
+    return b;
+}
+
+// Same contract as launch_rbf_contract (MODE_MIXED inputs: vmix values and
+// FP32 norms), on the tensor cores. `ws` must hold tc_rbf_workspace_bytes.
+cudaError_t launch_rbf_contract_tc(const RbfContract &c, void *ws, int *err_host, cudaStream_t st)
+{
+    *err_host = 0;
+    if (c.nq <= 0) return cudaSuccess;
+    const int d_pad = ((c.d + kKB - 1) / kKB) * kKB;
+    const int kblocks = d_pad / kKB;
+    if (kblocks > kMaxKBlocks) return cudaErrorInvalidValue;
+    const int64_t nq_pad = (c.nq + kTile - 1) / kTile * kTile;
+    const int64_t ns = c.nsv > 0 ? c.nsv : 1;
+    const int64_t ns_pad = (ns + kTile - 1) / kTile * kTile;
+    unsigned char *p = static_cast<unsigned char *>(ws);
+    auto take = [&](size_t x) {
+        unsigned char *r = p;
+        p += (x + 255) & ~(size_t)255;
+        return r;
+    };
+    auto *Zd = reinterpret_cast<__nv_bfloat16 *>(take((size_t)nq_pad * d_pad * 2));
+    auto *Xd = reinterpret_cast<__nv_bfloat16 *>(take((size_t)ns_pad * d_pad * 2));
+    auto *zc = reinterpret_cast<float *>(take((size_t)nq_pad * 4));
+    auto *xc = reinterpret_cast<float *>(take((size_t)ns_pad * 4));
+    auto *coef = reinterpret_cast<float *>(take((size_t)ns_pad * 4));
+    auto *qrow = reinterpret_cast<int32_t *>(take((size_t)nq_pad * 4));
+    auto *err = reinterpret_cast<int *>(take(256));
+    const float L2E = 1.4426950408889634f;
+    const float nscale = (float)(-c.gamma) * L2E;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_densify<<<(unsigned)nq_pad, 64, 0, st>>>(c.nq, nq_pad, d_pad, c.q, c.z_indptr, c.z_indices, c.z_values,
+                                               c.z_normf, nscale, Zd, zc, nullptr, nullptr, qrow, c.out_by_row);
+    k_densify<<<(unsigned)ns_pad, 64, 0, st>>>(c.nsv, ns_pad, d_pad, c.sv, c.x_indptr, c.x_indices, c.x_values,
+                                               c.x_normf, nscale, Xd, xc, c.coef, coef, nullptr, 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    CUtensorMap mz, mx;
+    if (!make_map(&mz, Zd, nq_pad, d_pad) || !make_map(&mx, Xd, ns_pad, d_pad)) return cudaErrorInvalidValue;
+    TcArgs a;
+    a.nq = c.nq;
+    a.nsv = c.nsv;
+    a.kblocks = kblocks;
+    a.zc = zc;
+    a.xc = xc;
+    a.coef = coef;
+    a.g2 = 2.0f * (float)c.gamma * L2E;
+    a.qrow = qrow;
+    a.yq = c.yq;
+    a.add_scalar = c.add_scalar;
+    a.out = c.out;
+    a.err = err;
+    // at least 52 KiB so that at most 4 CTAs share an SM: their 4 x 128
+    // tensor-memory columns then fit the SM's 512 without waiting
+    const size_t smem = std::max<size_t>(2 * (size_t)kblocks * kTileBytes + 1024, 52 * 1024);
+    e = cudaFuncSetAttribute(tc_rbf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (c.nsv > 0) {
+        tc_rbf_kernel<<<(unsigned)(nq_pad / kTile), kTcThreads, smem, st>>>(mz, mx, a);
+    } else {
+        // no support vectors: every sum is zero
+        return cudaErrorInvalidValue;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(err_host, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    return e;
+}
+
+}  // namespace svmgb

@@ -1,0 +1,166 @@
+"""Mixed-precision path (SVM_MIXED_BF16): BF16-rounded feature values, FP32
+inner products and exp, FP64 f / pair step / b; the reconstruction and
+decision contractions on the tcgen05 tensor cores.
+
+* The tensor-core contraction equals a float64 numpy evaluation of the same
+  formula on the BF16-rounded inputs to FP32 accuracy, on tile-ragged shapes.
+* The tensor-core and CUDA-core versions of the mixed path agree.
+* Against the FP64 oracle the mixed solve is a solve of a slightly perturbed
+  kernel matrix: its errors in alpha, b, the objective and the decision values
+  are measured and bounded here; the FP64 path stays at oracle parity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1406_5161_gb300 as pkg
+from paper_1406_5161_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+
+def bf16(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def dev(p):
+    return pkg.to_device(p.X), torch.as_tensor(p.y, device="cuda")
+
+
+@pytest.mark.parametrize("n,m,d", [(300, 200, 20), (128, 128, 64), (129, 1, 64),
+                                   (1000, 257, 100), (513, 300, 256), (64, 1000, 7)])
+def test_tensor_core_contraction_matches_reference(n, m, d):
+    rng = np.random.default_rng(n * 7 + d)
+    x = rng.standard_normal((n, d)).astype(np.float32)
+    z = rng.standard_normal((m, d)).astype(np.float32)
+    X = synth.csr_from_dense(x, keep_zeros=True)
+    Z = synth.csr_from_dense(z, keep_zeros=True)
+    y = np.where(rng.random(n) < 0.5, 1, -1).astype(np.int8)
+    a = np.where(rng.random(n) < 0.6, rng.random(n), 0.0)
+    g = 0.05 if d > 64 else 0.2
+    Xd, Zd = pkg.to_device(X), pkg.to_device(Z)
+    yd, ad = torch.as_tensor(y, device="cuda"), torch.as_tensor(a, device="cuda")
+    d_tc = pkg.svm_decision(Xd, yd, ad, 0.25, g, Zd, precision=pkg.SVM_MIXED_BF16).cpu().numpy()
+    d_simt = pkg.svm_decision(Xd, yd, ad, 0.25, g, Zd, precision=pkg.SVM_MIXED_BF16_SIMT).cpu().numpy()
+    xb, zb = bf16(x), bf16(z)
+    d2 = (zb ** 2).sum(1)[:, None] + (xb ** 2).sum(1)[None, :] - 2 * zb @ xb.T
+    ref = np.exp(-g * np.maximum(d2, 0)) @ (a * y) - 0.25
+    scale = max(1.0, np.abs(a).sum())
+    assert np.abs(d_tc - ref).max() <= 2e-6 * scale
+    assert np.abs(d_simt - ref).max() <= 2e-6 * scale
+
+
+def test_sparse_rows_on_tensor_cores():
+    # CSR rows with ragged lengths densify correctly into the BF16 tiles
+    p = synth.random_sparse(700, 90, 0.1, seed=3, C=1.0, gamma=0.1)
+    q = synth.random_sparse(333, 90, 0.1, seed=4)
+    rng = np.random.default_rng(5)
+    a = np.where(rng.random(700) < 0.5, rng.random(700), 0.0)
+    Xd, yd = dev(p)
+    dz = pkg.svm_decision(Xd, yd, torch.as_tensor(a, device="cuda"), -0.1, p.gamma,
+                          pkg.to_device(q.X), precision=pkg.SVM_MIXED_BF16).cpu().numpy()
+    xb, zb = bf16(p.X.to_dense()), bf16(q.X.to_dense())
+    d2 = (zb ** 2).sum(1)[:, None] + (xb ** 2).sum(1)[None, :] - 2 * zb @ xb.T
+    ref = np.exp(-p.gamma * np.maximum(d2, 0)) @ (a * p.y) + 0.1
+    assert np.abs(dz - ref).max() <= 2e-6 * max(1.0, a.sum())
+
+
+@pytest.fixture(scope="module")
+def covtype_small():
+    p = synth.covtype_like(n=6000, n_test=2000, seed=13)
+    ref = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau)
+    dref = oracle.decision(p.X, p.y, ref["alpha"], ref["b"], p.gamma, p.Z)
+    return p, ref, dref
+
+
+def test_fp64_path_is_at_oracle_parity_on_covtype(covtype_small):
+    p, ref, dref = covtype_small
+    Xd, yd = dev(p)
+    r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_FP64)
+    assert r["iters"] == ref["iters"]
+    assert np.abs(r["alpha"].cpu().numpy() - ref["alpha"]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("shrink", [None, "Multi5pc"])
+def test_mixed_errors_against_oracle(covtype_small, shrink):
+    p, ref, dref = covtype_small
+    Xd, yd = dev(p)
+    pol = pkg.POLICIES[shrink] if shrink else None
+    r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_MIXED_BF16, shrink=pol)
+    assert r["status"] == pkg.SVM_OK
+    a = r["alpha"].cpu().numpy()
+    kk = oracle.kkt(p.X, p.y, a, p.C, p.gamma)
+    dz = pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, pkg.to_device(p.Z),
+                          precision=pkg.SVM_MIXED_BF16).cpu().numpy()
+    err = {"objective_rel": abs(kk["objective"] - ref["objective"]) / abs(ref["objective"]),
+           "alpha_max": float(np.abs(a - ref["alpha"]).max()),
+           "b": abs(r["b"] - ref["b"]),
+           "decision_max": float(np.abs(dz - dref).max()),
+           "sign_agree": float((np.sign(dz) == np.sign(dref)).mean())}
+    print("mixed vs FP64 oracle", shrink, err)
+    assert err["objective_rel"] <= 2e-4
+    assert err["b"] <= 1e-2
+    assert err["decision_max"] <= 5e-2
+    assert err["sign_agree"] >= 0.99
+    assert (a >= 0).all() and (a <= p.C).all() and abs((a * p.y).sum()) <= 1e-9 * len(a)
+
+
+def test_mixed_tensor_and_cuda_cores_agree(covtype_small):
+    p, _, _ = covtype_small
+    Xd, yd = dev(p)
+    pol = pkg.POLICIES["Multi5pc"]
+    r1 = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_MIXED_BF16, shrink=pol)
+    r2 = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_MIXED_BF16_SIMT, shrink=pol)
+    assert r1["stats"]["reconstructions"] >= 1
+    assert abs(r1["stats"]["objective"] - r2["stats"]["objective"]) <= 1e-6 * abs(r2["stats"]["objective"])
+
+
+@pytest.mark.timeout(900)
+def test_covtype_581012_fp64_and_mixed():
+    """Full-size covtype-shaped workload: the FP64 GPU solve is checked by the
+    oracle on sampled outputs it can compute one by one; the mixed solve's
+    errors are measured against the FP64 solve."""
+    p = synth.covtype_like()
+    Xd, yd = dev(p)
+    pol = pkg.POLICIES["Multi5pc"]
+    r64 = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_FP64, shrink=pol)
+    rmx = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_MIXED_BF16, shrink=pol)
+    assert r64["status"] == pkg.SVM_OK and rmx["status"] == pkg.SVM_OK
+    a64 = r64["alpha"].cpu().numpy()
+    amx = rmx["alpha"].cpu().numpy()
+    rng = np.random.default_rng(0)
+    # oracle: f of 300 sampled training rows from the FP64 alpha (Algorithm 6
+    # definition) -> the KKT conditions hold on the sample
+    rows = np.sort(rng.choice(p.X.n, 300, replace=False))
+    f = oracle.reconstruct(p.X, p.y, a64, p.gamma, rows, np.zeros(p.X.n))[rows]
+    ys, as_ = p.y[rows].astype(float), a64[rows]
+    up = ((as_ > 0) & (as_ < p.C)) | ((ys > 0) & (as_ == 0)) | ((ys < 0) & (as_ == p.C))
+    low = ((as_ > 0) & (as_ < p.C)) | ((ys > 0) & (as_ == p.C)) | ((ys < 0) & (as_ == 0))
+    assert f[low].max() - f[up].min() <= 2 * p.tau + 1e-6
+    # oracle decision values of 200 held-out points from the FP64 model
+    Zs = p.Z.take(np.arange(0, p.Z.n, 50))
+    Zsd = pkg.to_device(Zs)
+    d64 = pkg.svm_decision(Xd, yd, r64["alpha"], r64["b"], p.gamma, Zsd).cpu().numpy()
+    dor = oracle.decision(p.X, p.y, a64, r64["b"], p.gamma, Zs)
+    assert np.abs(d64 - dor).max() <= 1e-9 * max(1.0, np.abs(dor).max())
+    # mixed against FP64 (errors reported in the design doc)
+    Zd = pkg.to_device(p.Z)
+    dz64 = pkg.svm_decision(Xd, yd, r64["alpha"], r64["b"], p.gamma, Zd).cpu().numpy()
+    dzmx = pkg.svm_decision(Xd, yd, rmx["alpha"], rmx["b"], p.gamma, Zd,
+                            precision=pkg.SVM_MIXED_BF16).cpu().numpy()
+    w64, wmx = r64["stats"]["objective"], rmx["stats"]["objective"]
+    err = {"objective_rel": abs(wmx - w64) / abs(w64), "alpha_max": float(np.abs(amx - a64).max()),
+           "alpha_mean": float(np.abs(amx - a64).mean()), "b": abs(rmx["b"] - r64["b"]),
+           "decision_max": float(np.abs(dzmx - dz64).max()),
+           "decision_mean": float(np.abs(dzmx - dz64).mean()),
+           "sign_agree": float((np.sign(dzmx) == np.sign(dz64)).mean()),
+           "iters": (r64["iters"], rmx["iters"]),
+           "ms": (r64["stats"]["ms_total"], rmx["stats"]["ms_total"]),
+           "recon_ms": (r64["stats"]["ms_recon"], rmx["stats"]["ms_recon"])}
+    print("covtype 581012 mixed vs FP64:", err)
+    assert err["objective_rel"] <= 1e-3
+    assert err["sign_agree"] >= 0.99
