@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--policy", default="Multi5pc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="onehot", choices=["onehot", "batch"],
+                    help="onehot: the benchmark line; batch: the one-vs-one x C x gamma grid "
+                         "(405 jobs) batched vs one job at a time")
+    ap.add_argument("--plain-sample", type=int, default=27,
+                    help="batch workload: jobs trained one at a time for the comparison")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap SMO steps per solve (profiling of small cases; not a bench value)")
     return ap.parse_args()
@@ -343,11 +348,79 @@ def run_gb300(args, rank, world, local):
     return 0
 
 
+def run_batch(args):
+    """405 trainings (45 one-vs-one pairs x 3 C x 3 gamma) over one 50,000 x 256
+    matrix: batched in one persistent launch vs one svm_train at a time."""
+    import numpy as np
+    import torch
+    import paper_1406_5161_gb300 as pkg
+    from paper_1406_5161_gb300 import synth
+
+    torch.cuda.set_device(0)
+    mc = synth.multiclass()
+    jobs = []
+    for a, b in mc.ovo_pairs():
+        rows, y = mc.subproblem(a, b)
+        for C in mc.Cs:
+            for g in mc.gammas:
+                jobs.append({"rows": rows.astype(np.int32), "y": y, "C": C, "gamma": g, "tau": mc.tau})
+    Xd = pkg.to_device(mc.X)
+    djobs = [dict(j, rows=torch.as_tensor(j["rows"], device="cuda"), y=torch.as_tensor(j["y"], device="cuda"))
+             for j in jobs]
+    prec = pkg.SVM_MIXED_BF16
+    t0 = time.perf_counter()
+    shape = pkg.svm_batch_autotune(Xd, djobs, precision=prec)
+    tune_s = time.perf_counter() - t0
+    # warm-up on a slice, then the timed full batch
+    pkg.svm_train_batch(Xd, djobs[:20], precision=prec, **shape)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = pkg.svm_train_batch(Xd, djobs, precision=prec, **shape)
+    torch.cuda.synchronize()
+    batch_s = time.perf_counter() - t0
+    # one job at a time on a sample: all 9 (C, gamma) cells of evenly spaced pairs
+    npairs = len(mc.ovo_pairs())
+    cells = len(mc.Cs) * len(mc.gammas)
+    take = max(1, args.plain_sample // cells)
+    pairs = [round(k * (npairs - 1) / max(1, take - 1)) for k in range(take)] if take > 1 else [0]
+    idx = [pp * cells + c for pp in pairs for c in range(cells)]
+    subs = [(pkg.to_device(mc.X.take(jobs[i]["rows"])), torch.as_tensor(jobs[i]["y"], device="cuda")) for i in idx]
+    pkg.svm_train(subs[0][0], subs[0][1], jobs[idx[0]]["C"], jobs[idx[0]]["gamma"], mc.tau, precision=prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for (Xs, ys), i in zip(subs, idx):
+        plain.append(pkg.svm_train(Xs, ys, jobs[i]["C"], jobs[i]["gamma"], mc.tau, precision=prec))
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    rel = [abs(out["results"][i]["objective"] - r["stats"]["objective"]) / abs(r["stats"]["objective"])
+           for i, r in zip(idx, plain)]
+    batch_tps = len(jobs) / batch_s
+    plain_tps = len(idx) / plain_s
+    line = {"metric": "batched trains/s", "value": batch_tps, "unit": "trains/s",
+            "workload": "multiclass 50000x256, 45 one-vs-one pairs x C{0.1,1,10} x gamma{0.002,0.01,0.05} = 405 jobs",
+            "precision": "mixed (BF16 values, FP32 dots/exp, FP64 f/step/b)",
+            "batched": {"trains_per_s": batch_tps, "seconds": batch_s, "iters_total": out["iters_total"],
+                        "job_iters_per_s": out["iters_total"] / batch_s, "cluster_size": out["cluster_size"],
+                        "lanes_per_row": out["lanes_per_row"], "clusters_in_flight": out["clusters"],
+                        "autotune_s": tune_s, "not_converged": sum(r["status"] != 0 for r in out["results"])},
+            "one_at_a_time": {"trains_per_s": plain_tps, "jobs": len(idx), "seconds": plain_s,
+                              "batched_trains_per_s_same_jobs": len(idx) / (batch_s * sum(out["results"][i]["iters"] for i in idx) / max(1, out["iters_total"])),
+                              "iters": int(sum(r["iters"] for r in plain)),
+                              "job_iters_per_s": sum(r["iters"] for r in plain) / plain_s},
+            "speedup_trains_per_s": batch_tps / plain_tps,
+            "objective_rel_diff_max": max(rel)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gb300(args, rank, world, local)
 
 

@@ -198,6 +198,64 @@ int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double 
                  double gamma, const svm_csr *Z, int32_t precision, void *stream,
                  double *out);
 
+/* ------------------------------------------------------------ batching */
+
+/* One training job of a batch: a two-class subproblem over rows of the shared
+ * matrix (e.g. one class pair of a one-vs-one split, with its own C and
+ * gamma). Pointers are in the memory space of the batch's matrix. */
+typedef struct svm_job {
+    int64_t n_rows;          /* rows in the subproblem (>= 2) */
+    const int32_t *rows;     /* n_rows row ids of the matrix; NULL = rows 0 .. n_rows-1 */
+    const int8_t *y;         /* n_rows labels, +1 / -1, both present */
+    double C, gamma, tau;    /* as in svm_params */
+    int64_t max_iter;        /* <= 0: 100 * n_rows + 1e6 */
+    double *alpha_out;       /* n_rows multipliers (caller-owned) */
+} svm_job;
+
+typedef struct svm_result {
+    double b;                /* threshold of Section III-A */
+    double b_up, b_low;      /* Eq. (bminmax) at exit */
+    double objective;        /* dual objective W */
+    int64_t iters;
+    int32_t status;          /* SVM_OK or SVM_NOT_CONVERGED */
+    int32_t n_sv;
+} svm_result;
+
+typedef struct svm_batch_config {
+    int32_t precision;       /* enum svm_precision (tensor cores are not used here) */
+    int32_t cluster_size;    /* in/out: CTAs that share one job (1..16, power of
+                                two); 0 = picked by svm_batch_autotune */
+    int32_t lanes_per_row;   /* in/out: lanes per row in the row pass; 0 = autotuned */
+    int32_t clusters;        /* jobs in flight at once; 0 = as many as fit */
+    void *stream;            /* cudaStream_t or NULL */
+    double ms_kernel;        /* out: device time of the batched launch */
+    double ms_total;         /* out: wall time of the call */
+    int64_t iters_total;     /* out: SMO steps summed over the jobs */
+    int32_t clusters_used;   /* out */
+    int32_t reserved;
+} svm_batch_config;
+
+/*
+ * svm_train_batch -- train every job (plain SMO, Algorithm 1, per job) in one
+ * persistent launch: thread-block clusters take jobs from a device work-list;
+ * each job's rows are split over the CTAs of one cluster, which exchange
+ * their candidates through distributed shared memory. X is ingested once for
+ * all jobs. Results and multipliers are those each job would get alone with
+ * svm_train at the same precision (no shrinking). Returns SVM_OK,
+ * SVM_NOT_CONVERGED (some job hit max_iter) or an error.
+ */
+int svm_train_batch(const svm_csr *X, const svm_job *jobs, int32_t n_jobs,
+                    svm_batch_config *config, svm_result *results);
+
+/*
+ * svm_batch_autotune -- choose cluster_size and lanes_per_row for this matrix
+ * and these jobs by timing each candidate shape on a sample of at most 64
+ * jobs capped at 300 steps, and write the fastest into *config. Fields the
+ * caller set to non-zero values are kept.
+ */
+int svm_batch_autotune(const svm_csr *X, const svm_job *jobs, int32_t n_jobs,
+                       svm_batch_config *config);
+
 /*
  * svm_train_fixed_workspace -- the plain solve of svm_train (no shrinking,
  * SVM_FP64) without any device allocation. The paper has no counterpart to

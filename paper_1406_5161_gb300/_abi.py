@@ -280,3 +280,95 @@ def svm_train_fixed_workspace(X, y, C: float, gamma: float, tau: float = 1e-3, *
     if check and rc < 0:
         raise SvmError(rc, svm_last_error())
     return {"status": rc, "alpha": alpha_out, "b": b.value, "iters": it.value}
+
+
+class svm_job(ct.Structure):
+    _fields_ = [("n_rows", ct.c_int64), ("rows", ct.c_void_p), ("y", ct.c_void_p),
+                ("C", ct.c_double), ("gamma", ct.c_double), ("tau", ct.c_double),
+                ("max_iter", ct.c_int64), ("alpha_out", ct.c_void_p)]
+
+
+class svm_result(ct.Structure):
+    _fields_ = [("b", ct.c_double), ("b_up", ct.c_double), ("b_low", ct.c_double),
+                ("objective", ct.c_double), ("iters", ct.c_int64), ("status", ct.c_int32),
+                ("n_sv", ct.c_int32)]
+
+
+class svm_batch_config(ct.Structure):
+    _fields_ = [("precision", ct.c_int32), ("cluster_size", ct.c_int32),
+                ("lanes_per_row", ct.c_int32), ("clusters", ct.c_int32), ("stream", ct.c_void_p),
+                ("ms_kernel", ct.c_double), ("ms_total", ct.c_double), ("iters_total", ct.c_int64),
+                ("clusters_used", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+def _batch_args(X, jobs, precision, cluster_size, lanes_per_row, clusters, stream, h, alloc_alpha):
+    cx, dev = _csr(h, X)
+    arr = (svm_job * len(jobs))()
+    alphas = []
+    for k, jb in enumerate(jobs):
+        y = jb["y"]
+        n = len(y)
+        rows = jb.get("rows")
+        if dev:
+            import torch
+            yp = h.tensor(y, "int8")
+            rp = None if rows is None else h.tensor(rows, "int32")
+            a = torch.empty(n, dtype=torch.float64, device=X.indptr.device) if alloc_alpha else None
+            ap = a.data_ptr() if a is not None else None
+        else:
+            yp = h.np(y, np.int8)
+            rp = None if rows is None else h.np(rows, np.int32)
+            a = np.zeros(n) if alloc_alpha else None
+            ap = a.ctypes.data if a is not None else None
+        alphas.append(a)
+        arr[k] = svm_job(n, rp, yp, float(jb["C"]), float(jb["gamma"]), float(jb.get("tau", 1e-3)),
+                         int(jb.get("max_iter", 0)), ap)
+    cfg = svm_batch_config(int(precision), int(cluster_size), int(lanes_per_row), int(clusters),
+                           _stream_ptr(stream), 0.0, 0.0, 0, 0, 0)
+    return cx, arr, cfg, alphas
+
+
+def svm_train_batch(X, jobs, *, precision: int = SVM_FP64, cluster_size: int = 0,
+                    lanes_per_row: int = 0, clusters: int = 0, stream=None, check: bool = True) -> dict:
+    """Train every job of ``jobs`` (dicts with rows, y, C, gamma[, tau, max_iter])
+    over the shared matrix X in one persistent launch."""
+    lib = load()
+    if not hasattr(lib, "_batch_bound"):
+        P = ct.c_void_p
+        lib.svm_train_batch.restype = ct.c_int
+        lib.svm_train_batch.argtypes = [P, P, ct.c_int32, P, P]
+        lib.svm_batch_autotune.restype = ct.c_int
+        lib.svm_batch_autotune.argtypes = [P, P, ct.c_int32, P]
+        lib._batch_bound = True
+    h = _Hold()
+    cx, arr, cfg, alphas = _batch_args(X, jobs, precision, cluster_size, lanes_per_row, clusters,
+                                       stream, h, True)
+    res = (svm_result * len(jobs))()
+    rc = lib.svm_train_batch(ct.byref(cx), arr, len(jobs), ct.byref(cfg), res)
+    if check and rc < 0:
+        raise SvmError(rc, svm_last_error())
+    out = [{"b": r.b, "b_up": r.b_up, "b_low": r.b_low, "objective": r.objective,
+            "iters": r.iters, "status": r.status, "n_sv": r.n_sv, "alpha": a}
+           for r, a in zip(res, alphas)]
+    return {"status": rc, "results": out, "cluster_size": cfg.cluster_size,
+            "lanes_per_row": cfg.lanes_per_row, "clusters": cfg.clusters_used,
+            "ms_kernel": cfg.ms_kernel, "ms_total": cfg.ms_total, "iters_total": cfg.iters_total}
+
+
+def svm_batch_autotune(X, jobs, *, precision: int = SVM_FP64, cluster_size: int = 0,
+                       lanes_per_row: int = 0, stream=None) -> dict:
+    """Pick cluster_size / lanes_per_row for a batch by timing candidates."""
+    lib = load()
+    if not hasattr(lib, "_batch_bound"):
+        P = ct.c_void_p
+        lib.svm_train_batch.restype = ct.c_int
+        lib.svm_train_batch.argtypes = [P, P, ct.c_int32, P, P]
+        lib.svm_batch_autotune.restype = ct.c_int
+        lib.svm_batch_autotune.argtypes = [P, P, ct.c_int32, P]
+        lib._batch_bound = True
+    h = _Hold()
+    cx, arr, cfg, _ = _batch_args(X, jobs, precision, cluster_size, lanes_per_row, 0, stream, h, False)
+    rc = lib.svm_batch_autotune(ct.byref(cx), arr, len(jobs), ct.byref(cfg))
+    if rc < 0:
+        raise SvmError(rc, svm_last_error())
+    return {"cluster_size": cfg.cluster_size, "lanes_per_row": cfg.lanes_per_row}

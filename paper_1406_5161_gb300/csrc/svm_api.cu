@@ -908,6 +908,331 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
 }
 
 
+
+// ---------------------------------------------------------------------------
+// Batched training (many subproblems over one matrix in one launch)
+// ---------------------------------------------------------------------------
+
+// BF16 dense copy of dense rows (row stride d_pad, zero padding).
+__global__ void k_dense_bf16(int64_t n, int d, int d_pad, const int64_t *indptr, const int32_t *indices,
+                             const float *vmix, __nv_bfloat16 *out)
+{
+    const int64_t r = blockIdx.x;
+    if (r >= n) return;
+    __nv_bfloat16 *dst = out + (size_t)r * d_pad;
+    for (int c = threadIdx.x; c < d_pad; c += blockDim.x) dst[c] = __float2bfloat16_rn(0.f);
+    __syncthreads();
+    for (int64_t p = indptr[r] + threadIdx.x; p < indptr[r + 1]; p += blockDim.x)
+        dst[indices[p]] = __float2bfloat16_rn(vmix[p]);
+}
+
+__global__ void k_iota(int64_t n, int32_t *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)i;
+}
+
+// per job: row ids in range, labels +-1, both classes present
+__global__ void k_job_check(int njobs, const BatchJobDev *jobs, const int32_t *rows, const int8_t *y, int64_t n,
+                            int *bad)
+{
+    const int j = blockIdx.x;
+    if (j >= njobs) return;
+    __shared__ int s_bad, s_pos, s_neg;
+    if (threadIdx.x == 0) s_bad = s_pos = s_neg = 0;
+    __syncthreads();
+    const BatchJobDev J = jobs[j];
+    int b = 0, pos = 0, neg = 0;
+    for (int r = threadIdx.x; r < J.nrows; r += blockDim.x) {
+        const int32_t g = rows[J.off + r];
+        const int8_t v = y[J.off + r];
+        if (g < 0 || g >= n) b = 1;
+        if (v == 1) pos = 1;
+        else if (v == -1) neg = 1;
+        else b = 1;
+    }
+    if (b) atomicOr(&s_bad, 1);
+    if (pos) atomicOr(&s_pos, 1);
+    if (neg) atomicOr(&s_neg, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) bad[j] = s_bad ? 1 : ((s_pos && s_neg) ? 0 : 2);
+}
+
+struct BatchPlan {
+    DevCSR D;
+    int mode = MODE_FP64;
+    int dense = 0;
+    int d_eff = 0;
+    __nv_bfloat16 *dense_rows = nullptr;
+    int ktab_len = 0;
+    size_t smem = 0;
+};
+
+void batch_prepare(Arena &ar, const svm_csr *X, int precision, cudaStream_t st, BatchPlan &B, int *launches)
+{
+    const bool mixed = precision != SVM_FP64;
+    ingest(ar, X, nullptr, !mixed, mixed, st, B.D, launches);
+    DevCSR &D = B.D;
+    B.mode = D.binary ? MODE_BINARY : (mixed ? MODE_MIXED : MODE_FP64);
+    if (B.mode == MODE_BINARY && smo_layout(MODE_BINARY, (int)D.d, 2 * D.maxnnz + 1, D.maxnnz, 0, 0, 0).total >
+                                     smem_limit() - 12288) {
+        B.mode = mixed ? MODE_MIXED : MODE_FP64;
+        if (B.mode == MODE_FP64 && !D.norm) D.norm = ar.alloc<double>(D.n);
+        if (B.mode == MODE_MIXED && !D.vmix) {
+            D.vmix = ar.alloc<float>(D.nnz);
+            D.normf = ar.alloc<float>(D.n);
+        }
+        k_norms<<<grid1(D.n), 256, 0, st>>>(D.n, D.indptr, D.values, D.norm, D.vmix, D.normf);
+        CK(cudaGetLastError());
+        ++*launches;
+    }
+    B.dense = B.mode == MODE_MIXED && D.nnz == D.n * D.d;
+    B.d_eff = (int)D.d;
+    if (B.dense) {
+        const int d_pad = (int)((D.d + 7) & ~7ll);
+        B.dense_rows = ar.alloc<__nv_bfloat16>((size_t)D.n * d_pad);
+        k_dense_bf16<<<(unsigned)D.n, 128, 0, st>>>(D.n, (int)D.d, d_pad, D.indptr, D.indices, D.vmix,
+                                                    B.dense_rows);
+        CK(cudaGetLastError());
+        ++*launches;
+        B.d_eff = d_pad;
+    }
+    B.ktab_len = B.mode == MODE_BINARY ? 2 * D.maxnnz + 1 : 0;
+    B.smem = smo_batch_smem(B.mode, B.d_eff, B.ktab_len, D.maxnnz);
+    if (B.smem > smem_limit() - 12288) {
+        set_err("d = %lld exceeds the shared-memory target rows of the batched solver", (long long)D.d);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+}
+
+// timed run of the batch kernel; returns device ms and fills results
+float batch_run(const BatchPlan &P, const BatchArgs &A0, int lpr, int cs, int nclusters, int *next_job,
+                cudaStream_t st, int *launches)
+{
+    BatchArgs A = A0;
+    A.next_job = next_job;
+    CK(cudaMemsetAsync(next_job, 0, sizeof(int), st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, st));
+    CK(launch_smo_batch(P.mode, lpr, P.dense, A, P.smem, cs, nclusters, st));
+    ++*launches;
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+int batch_clusters(const BatchPlan &P, int lpr, int cs)
+{
+    return smo_batch_max_clusters(P.mode, lpr, P.dense, P.smem, cs);
+}
+
+int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_batch_config *cfg,
+                     svm_result *results, bool tune_only)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    if (!X || !jobs || !cfg || (!results && !tune_only)) ARG_FAIL("NULL argument");
+    if (n_jobs < 1) ARG_FAIL("n_jobs must be >= 1");
+    if (cfg->precision < SVM_FP64 || cfg->precision > SVM_MIXED_BF16_SIMT)
+        ARG_FAIL("unknown precision %d", cfg->precision);
+    if (cfg->cluster_size < 0 || cfg->cluster_size > 16 || (cfg->cluster_size & (cfg->cluster_size - 1)))
+        ARG_FAIL("cluster_size must be 0 (autotune) or a power of two <= 16");
+    cudaStream_t st = as_stream(cfg->stream);
+    int launches = 0;
+    Arena ar(st);
+    BatchPlan P;
+    batch_prepare(ar, X, cfg->precision, st, P, &launches);
+    const DevCSR &D = P.D;
+
+    // ---- concatenated job arrays
+    std::vector<BatchJobDev> hj(n_jobs);
+    int64_t total = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const svm_job &J = jobs[j];
+        if (J.n_rows < 2) ARG_FAIL("job %d: need at least two rows", j);
+        if (!J.rows && J.n_rows > D.n) ARG_FAIL("job %d: n_rows exceeds the matrix", j);
+        if (!J.y || (!J.alpha_out && !tune_only)) ARG_FAIL("job %d: labels and alpha_out must not be NULL", j);
+        if (!(J.C > 0) || !(J.gamma > 0) || !(J.tau > 0)) ARG_FAIL("job %d: C, gamma and tau must be > 0", j);
+        if (J.n_rows >= INT32_MAX) ARG_FAIL("job %d: too many rows", j);
+        hj[j].off = total;
+        hj[j].nrows = (int32_t)J.n_rows;
+        hj[j].pad = 0;
+        hj[j].C = J.C;
+        hj[j].gamma = J.gamma;
+        hj[j].tau = J.tau;
+        hj[j].max_iter = J.max_iter > 0 ? J.max_iter : 100 * J.n_rows + 1000000;
+        total += J.n_rows;
+    }
+    int32_t *rows = ar.alloc<int32_t>(total);
+    int8_t *ycat = ar.alloc<int8_t>(total);
+    if (X->on_device) {
+        for (int j = 0; j < n_jobs; ++j) {
+            const svm_job &J = jobs[j];
+            if (J.rows)
+                CK(cudaMemcpyAsync(rows + hj[j].off, J.rows, 4 * J.n_rows, cudaMemcpyDeviceToDevice, st));
+            else {
+                k_iota<<<grid1(J.n_rows), 256, 0, st>>>(J.n_rows, rows + hj[j].off);
+                CK(cudaGetLastError());
+                ++launches;
+            }
+            CK(cudaMemcpyAsync(ycat + hj[j].off, J.y, J.n_rows, cudaMemcpyDeviceToDevice, st));
+        }
+    } else {
+        std::vector<int32_t> hr(total);
+        std::vector<int8_t> hy(total);
+        for (int j = 0; j < n_jobs; ++j) {
+            const svm_job &J = jobs[j];
+            for (int64_t r = 0; r < J.n_rows; ++r) hr[hj[j].off + r] = J.rows ? J.rows[r] : (int32_t)r;
+            std::memcpy(hy.data() + hj[j].off, J.y, J.n_rows);
+        }
+        CK(cudaMemcpyAsync(rows, hr.data(), 4 * total, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ycat, hy.data(), total, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    BatchJobDev *djobs = ar.alloc<BatchJobDev>(n_jobs);
+    CK(cudaMemcpyAsync(djobs, hj.data(), sizeof(BatchJobDev) * n_jobs, cudaMemcpyHostToDevice, st));
+    int *bad = ar.alloc<int>(n_jobs);
+    k_job_check<<<n_jobs, 256, 0, st>>>(n_jobs, djobs, rows, ycat, D.n, bad);
+    CK(cudaGetLastError());
+    ++launches;
+    std::vector<int> hbad(n_jobs);
+    CK(cudaMemcpyAsync(hbad.data(), bad, sizeof(int) * n_jobs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int j = 0; j < n_jobs; ++j) {
+        if (hbad[j] == 1) ARG_FAIL("job %d: row ids out of range or labels not +-1", j);
+        if (hbad[j] == 2) ARG_FAIL("job %d: both classes must be present", j);
+    }
+
+    double *alpha = ar.alloc<double>(total);
+    double *f = ar.alloc<double>(total);
+    uint8_t *status = ar.alloc<uint8_t>(total);
+    BatchResultDev *dres = ar.alloc<BatchResultDev>(n_jobs);
+    int *next_job = ar.alloc<int>(1);
+    BatchArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.n = D.n;
+    A.d = P.d_eff;
+    A.njobs = n_jobs;
+    A.indptr = D.indptr;
+    A.indices = D.indices;
+    A.values = D.values;
+    A.vmix = D.vmix;
+    A.dense = P.dense_rows;
+    A.norm = D.norm;
+    A.normf = D.normf;
+    A.rows = rows;
+    A.y = ycat;
+    A.alpha = alpha;
+    A.f = f;
+    A.status = status;
+    A.jobs = djobs;
+    A.results = dres;
+    A.ktab_len = P.ktab_len;
+    A.maxnnz = D.maxnnz;
+
+    // ---- launch shape: given, or picked by timing candidates on a sample
+    int cs = cfg->cluster_size, lpr = cfg->lanes_per_row;
+    if (lpr > 0) {
+        int l = 1;
+        while (l < 32 && l < lpr) l <<= 1;
+        lpr = l;
+    }
+    if (cs == 0 || lpr == 0) {
+        const double avg = (double)D.nnz / (double)D.n;
+        std::vector<int> lprs, css;
+        if (lpr > 0) lprs = {lpr};
+        else if (P.dense) lprs = {2, 4, 8, 16, 32};
+        else if (avg <= 48) lprs = {1, 2, 4};
+        else lprs = {2, 4, 8, 16};
+        if (cs > 0) css = {cs};
+        else css = {2, 4, 8, 16};
+        // sample: up to 64 jobs, at most 300 steps each
+        const int ns = std::min(n_jobs, 64);
+        std::vector<BatchJobDev> sj(hj.begin(), hj.begin() + ns);
+        for (auto &x : sj) x.max_iter = std::min<int64_t>(x.max_iter, 300);
+        BatchJobDev *dsj = ar.alloc<BatchJobDev>(ns);
+        CK(cudaMemcpyAsync(dsj, sj.data(), sizeof(BatchJobDev) * ns, cudaMemcpyHostToDevice, st));
+        std::vector<BatchResultDev> sres(ns);
+        BatchArgs S = A;
+        S.jobs = dsj;
+        S.njobs = ns;
+        double best = -1.0;
+        int best_cs = css[0], best_lpr = lprs[0];
+        for (int c : css) {
+            for (int l : lprs) {
+                const int maxc = batch_clusters(P, l, c);
+                if (maxc < 1) continue;
+                const float ms = batch_run(P, S, l, c, std::min(maxc, ns), next_job, st, &launches);
+                CK(cudaMemcpy(sres.data(), dres, sizeof(BatchResultDev) * ns, cudaMemcpyDeviceToHost));
+                int64_t it = 0;
+                for (auto &r : sres) it += r.iters;
+                const double rate = (double)it / (double)std::max(ms, 1e-3f);
+                if (rate > best) {
+                    best = rate;
+                    best_cs = c;
+                    best_lpr = l;
+                }
+            }
+        }
+        if (best < 0) {
+            set_err("no batched launch shape fits this device");
+            throw Fail{SVM_ERR_UNSUPPORTED};
+        }
+        cs = best_cs;
+        lpr = best_lpr;
+        cfg->cluster_size = cs;
+        cfg->lanes_per_row = lpr;
+    }
+    if (tune_only) return SVM_OK;
+    const int maxc = batch_clusters(P, lpr, cs);
+    if (maxc < 1) {
+        set_err("cluster size %d does not fit this device", cs);
+        throw Fail{SVM_ERR_UNSUPPORTED};
+    }
+    int ncl = std::min(maxc, n_jobs);
+    if (cfg->clusters > 0) ncl = std::min(ncl, cfg->clusters);
+    const float ms = batch_run(P, A, lpr, cs, ncl, next_job, st, &launches);
+    std::vector<BatchResultDev> hres(n_jobs);
+    CK(cudaMemcpyAsync(hres.data(), dres, sizeof(BatchResultDev) * n_jobs, cudaMemcpyDeviceToHost, st));
+    if (X->on_device) {
+        for (int j = 0; j < n_jobs; ++j)
+            CK(cudaMemcpyAsync(jobs[j].alpha_out, alpha + hj[j].off, 8 * jobs[j].n_rows, cudaMemcpyDeviceToDevice,
+                               st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::vector<double> ha(total);
+        CK(cudaMemcpyAsync(ha.data(), alpha, 8 * total, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int j = 0; j < n_jobs; ++j)
+            std::memcpy(jobs[j].alpha_out, ha.data() + hj[j].off, 8 * jobs[j].n_rows);
+    }
+    int64_t iters = 0;
+    int rc = SVM_OK;
+    for (int j = 0; j < n_jobs; ++j) {
+        svm_result &R = results[j];
+        R.b = hres[j].b;
+        R.b_up = hres[j].b_up;
+        R.b_low = hres[j].b_low;
+        R.objective = hres[j].objective;
+        R.iters = hres[j].iters;
+        R.status = hres[j].status == 1 ? SVM_NOT_CONVERGED : SVM_OK;
+        R.n_sv = hres[j].n_sv;
+        iters += hres[j].iters;
+        if (R.status != SVM_OK) rc = SVM_NOT_CONVERGED;
+    }
+    cfg->ms_kernel = ms;
+    cfg->iters_total = iters;
+    cfg->clusters_used = ncl;
+    cfg->ms_total = elapsed_ms(t_start);
+    g_launches += launches;
+    return rc;
+}
+
 // ---------------------------------------------------------------------------
 // Fixed-workspace training: a variant of the plain (no shrinking) FP64 solve
 // that allocates nothing. Some callers cannot allocate device memory during
@@ -1154,6 +1479,33 @@ int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double 
 const char *svm_last_error(void) { return g_err.c_str(); }
 
 int64_t svm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int svm_train_batch(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_batch_config *config,
+                    svm_result *results)
+{
+    g_err.clear();
+    try {
+        return train_batch_impl(X, jobs, n_jobs, config, results, false);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_batch_autotune(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_batch_config *config)
+{
+    g_err.clear();
+    try {
+        return train_batch_impl(X, jobs, n_jobs, config, nullptr, true);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
 
 int svm_train_fixed_workspace(const svm_csr *X, const int8_t *y, const svm_params *params,
                               double *alpha_out, double *b_out, int64_t *iters_out)

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 SVM library (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -80,6 +81,50 @@ struct SmoArgs {
     int64_t *cta_cycles;       // with phase_times: per-CTA cycles of work per launch (G)
     int64_t timeout_ns;
 };
+
+// ---- batched solves: one job = one subproblem over rows of a shared matrix
+struct BatchJobDev {
+    int64_t off;               // first entry of the job in the concatenated arrays
+    int32_t nrows;
+    int32_t pad;
+    double C, gamma, tau;
+    int64_t max_iter;
+};
+
+struct BatchResultDev {
+    double b, b_up, b_low, objective;
+    int64_t iters;
+    int32_t status;            // 0 converged, 1 iteration limit
+    int32_t n_sv;
+};
+
+struct BatchArgs {
+    int64_t n;
+    int32_t d;                 // columns (dense: padded to a multiple of 8)
+    int32_t njobs;
+    const int64_t *indptr;
+    const int32_t *indices;
+    const float *values;       // FP64 mode
+    const float *vmix;         // mixed mode (CSR)
+    const __nv_bfloat16 *dense;  // mixed mode, dense rows: BF16 [n][d]
+    const double *norm;
+    const float *normf;
+    const int32_t *rows;       // concatenated job row ids
+    const int8_t *y;           // concatenated job labels
+    double *alpha;
+    double *f;
+    uint8_t *status;
+    const BatchJobDev *jobs;
+    BatchResultDev *results;
+    int *next_job;             // work-list counter (zeroed before the launch)
+    int32_t ktab_len;          // binary mode: 2 * maxnnz + 1
+    int32_t maxnnz;
+};
+
+size_t smo_batch_smem(int mode, int d, int ktab_len, int maxnnz);
+int smo_batch_max_clusters(int mode, int lpr, int dense, size_t smem, int cs);
+cudaError_t launch_smo_batch(int mode, int lpr, int dense, const BatchArgs &a, size_t smem, int cs,
+                             int nclusters, cudaStream_t st);
 
 // Dynamic shared-memory layout of the step kernel (byte offsets).
 struct SmoLayout {
