@@ -50,7 +50,12 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--policy", default="Multi5pc")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="onehot", choices=["onehot", "batch"],
+    ap.add_argument("--serve-jobs", type=int, default=100)
+    ap.add_argument("--serve-nmax", type=int, default=10000)
+    ap.add_argument("--serve-cluster", type=int, default=0, help="CTAs per served job (0 = server default)")
+    ap.add_argument("--serve-burst", action="store_true",
+                    help="submit every job at time 0 (saturated server) instead of the Poisson times")
+    ap.add_argument("--workload", default="onehot", choices=["onehot", "batch", "serve"],
                     help="onehot: the benchmark line; batch: the one-vs-one x C x gamma grid "
                          "(405 jobs) batched vs one job at a time")
     ap.add_argument("--plain-sample", type=int, default=27,
@@ -414,6 +419,71 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """A Poisson stream (20 jobs/s) of training jobs of different n and d:
+    served with continuous batching vs one svm_train at a time (FIFO)."""
+    import numpy as np
+    import torch
+    import paper_1406_5161_gb300 as pkg
+    from paper_1406_5161_gb300 import synth
+
+    torch.cuda.set_device(0)
+    specs = synth.serving_stream(n_jobs=args.serve_jobs)
+    jobs = [synth.serving_job(sp, n=min(sp.n, args.serve_nmax)) for sp in specs]
+    arrivals = np.array([sp.arrival_s for sp in specs])
+    arrivals -= arrivals[0]
+    if args.serve_burst:
+        arrivals[:] = 0.0
+    prec = pkg.SVM_MIXED_BF16
+    # warm-up (library load, engine and kernels)
+    with pkg.Server(budget_bytes=150 << 30, max_slots=64, precision=prec,
+                    cluster_size=args.serve_cluster) as srv:
+        srv.wait(srv.submit(jobs[0].X, jobs[0].y, jobs[0].C, jobs[0].gamma))
+        t0 = time.perf_counter()
+        tickets = []
+        for p, at in zip(jobs, arrivals):
+            now = time.perf_counter() - t0
+            if at > now:
+                time.sleep(at - now)
+            tickets.append(srv.submit(p.X, p.y, p.C, p.gamma, p.tau))
+        outs = [srv.wait(t) for t in tickets]
+        served_span = time.perf_counter() - t0
+        info = srv.stats()
+    ttm = np.array([o["time_to_model_ms"] for o in outs])
+    ok = sum(o["status"] == pkg.SVM_OK for o in outs)
+    # one at a time: the same stream through one svm_train after another
+    pkg.svm_train(jobs[0].X, jobs[0].y, jobs[0].C, jobs[0].gamma, jobs[0].tau, precision=prec)
+    dur = []
+    objs = []
+    for p in jobs:
+        t = time.perf_counter()
+        r = pkg.svm_train(p.X, p.y, p.C, p.gamma, p.tau, precision=prec)
+        dur.append(time.perf_counter() - t)
+        objs.append(r["stats"]["objective"])
+    finish, ttm_plain = 0.0, []
+    for at, du in zip(arrivals, dur):
+        finish = max(finish, at) + du
+        ttm_plain.append(1e3 * (finish - at))
+    plain_span = finish
+    rel = max(abs(o["objective"] - w) / abs(w) for o, w in zip(outs, objs))
+    line = {"metric": "served trains/s", "value": len(jobs) / served_span, "unit": "trains/s",
+            "workload": ("all jobs at t=0, " if args.serve_burst else "Poisson 20 jobs/s, ") +
+                        f"{len(jobs)} jobs, n log-uniform [1e3, 2e5] capped at "
+                        f"{args.serve_nmax}, d log-uniform [20, 2000], half dense / half CSR 0.5%",
+            "precision": "mixed (BF16 values, FP32 dots/exp, FP64 f/step/b)",
+            "served": {"trains_per_s": len(jobs) / served_span, "p50_ms": float(np.percentile(ttm, 50)),
+                       "p99_ms": float(np.percentile(ttm, 99)), "span_s": served_span, "ok": ok,
+                       "clusters": info["clusters"], "cluster_size": info["cluster_size"],
+                       "engine_launches": info["engine_launches"]},
+            "one_at_a_time": {"trains_per_s": len(jobs) / plain_span,
+                              "p50_ms": float(np.percentile(ttm_plain, 50)),
+                              "p99_ms": float(np.percentile(ttm_plain, 99)), "span_s": plain_span,
+                              "busy_s": float(sum(dur))},
+            "objective_rel_diff_max": rel}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -421,6 +491,8 @@ def main():
         return run_reference(args, rank)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gb300(args, rank, world, local)
 
 

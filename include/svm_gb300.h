@@ -256,6 +256,61 @@ int svm_train_batch(const svm_csr *X, const svm_job *jobs, int32_t n_jobs,
 int svm_batch_autotune(const svm_csr *X, const svm_job *jobs, int32_t n_jobs,
                        svm_batch_config *config);
 
+/* ------------------------------------------------------------- serving */
+
+/* A training server: jobs of any n and d arrive over time, are admitted while
+ * a slot and the device-memory budget allow, and run concurrently on the
+ * device (continuous batching): a persistent engine kernel made of
+ * thread-block clusters takes admitted jobs from a ring the host extends
+ * while the engine runs; each job's matrix, alpha and f stay resident on the
+ * device until it finishes. Every job is the plain solve of Algorithm 1; its
+ * result is the one svm_train gives alone at the same precision. */
+typedef struct svm_server svm_server;
+
+typedef struct svm_server_config {
+    size_t budget_bytes;     /* device memory the server may hold for jobs */
+    int32_t max_slots;       /* jobs on the device at once (<= 1024; 0 = 64) */
+    int32_t precision;       /* SVM_FP64 or SVM_MIXED_BF16 */
+    int32_t cluster_size;    /* CTAs per job (power of two <= 16; 0 = 16) */
+    int32_t lanes_per_row;   /* 0 = 2 */
+    int32_t max_d;           /* widest job accepted (0 = 2048) */
+    int32_t reserved;
+} svm_server_config;
+
+typedef struct svm_server_times {
+    double submit_to_admit_ms;
+    double admit_to_done_ms;
+    double submit_to_done_ms;   /* time to model */
+} svm_server_times;
+
+typedef struct svm_server_info {
+    size_t bytes_in_use, budget_bytes;
+    int32_t queued, running;
+    int32_t clusters, cluster_size;   /* engine: jobs that can run at once, CTAs each */
+    int64_t engine_launches;
+} svm_server_info;
+
+/* Create a server on the current device (starts its host worker thread). */
+int svm_server_create(const svm_server_config *config, svm_server **out);
+/* Queue a job. X and y are host buffers and are copied before the call
+ * returns. SVM_ERR_BUDGET if the job alone exceeds the budget. */
+int svm_server_submit(svm_server *srv, const svm_csr *X, const int8_t *y,
+                      const svm_params *params, uint64_t *ticket);
+/* Non-blocking: SVM_PENDING while queued or running; otherwise the job's
+ * status, and res / alpha_out (n doubles) / times are filled (each may be
+ * NULL) and the ticket is released. */
+int svm_server_poll(svm_server *srv, uint64_t ticket, svm_result *res, double *alpha_out,
+                    svm_server_times *times);
+/* As svm_server_poll, waiting up to timeout_s seconds for the job. */
+int svm_server_wait(svm_server *srv, uint64_t ticket, double timeout_s, svm_result *res,
+                    double *alpha_out, svm_server_times *times);
+/* Cancel: a queued job ends with SVM_ERR_CANCELLED; a running job finishes
+ * on the device and then reports SVM_ERR_CANCELLED. */
+int svm_server_cancel(svm_server *srv, uint64_t ticket);
+int svm_server_stats(svm_server *srv, svm_server_info *info);
+/* Stop the server: running jobs finish, queued jobs are dropped. */
+int svm_server_destroy(svm_server *srv);
+
 /*
  * svm_train_fixed_workspace -- the plain solve of svm_train (no shrinking,
  * SVM_FP64) without any device allocation. The paper has no counterpart to

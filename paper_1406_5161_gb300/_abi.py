@@ -372,3 +372,115 @@ def svm_batch_autotune(X, jobs, *, precision: int = SVM_FP64, cluster_size: int 
     if rc < 0:
         raise SvmError(rc, svm_last_error())
     return {"cluster_size": cfg.cluster_size, "lanes_per_row": cfg.lanes_per_row}
+
+
+class svm_server_config(ct.Structure):
+    _fields_ = [("budget_bytes", ct.c_size_t), ("max_slots", ct.c_int32), ("precision", ct.c_int32),
+                ("cluster_size", ct.c_int32), ("lanes_per_row", ct.c_int32), ("max_d", ct.c_int32),
+                ("reserved", ct.c_int32)]
+
+
+class svm_server_times(ct.Structure):
+    _fields_ = [("submit_to_admit_ms", ct.c_double), ("admit_to_done_ms", ct.c_double),
+                ("submit_to_done_ms", ct.c_double)]
+
+
+class svm_server_info(ct.Structure):
+    _fields_ = [("bytes_in_use", ct.c_size_t), ("budget_bytes", ct.c_size_t), ("queued", ct.c_int32),
+                ("running", ct.c_int32), ("clusters", ct.c_int32), ("cluster_size", ct.c_int32),
+                ("engine_launches", ct.c_int64)]
+
+
+def _bind_server(lib):
+    if getattr(lib, "_server_bound", False):
+        return
+    P = ct.c_void_p
+    lib.svm_server_create.restype = ct.c_int
+    lib.svm_server_create.argtypes = [P, P]
+    lib.svm_server_submit.restype = ct.c_int
+    lib.svm_server_submit.argtypes = [P, P, P, P, P]
+    lib.svm_server_poll.restype = ct.c_int
+    lib.svm_server_poll.argtypes = [P, ct.c_uint64, P, P, P]
+    lib.svm_server_wait.restype = ct.c_int
+    lib.svm_server_wait.argtypes = [P, ct.c_uint64, ct.c_double, P, P, P]
+    lib.svm_server_cancel.restype = ct.c_int
+    lib.svm_server_cancel.argtypes = [P, ct.c_uint64]
+    lib.svm_server_stats.restype = ct.c_int
+    lib.svm_server_stats.argtypes = [P, P]
+    lib.svm_server_destroy.restype = ct.c_int
+    lib.svm_server_destroy.argtypes = [P]
+    lib._server_bound = True
+
+
+class Server:
+    """Continuous-batching training server (svm_server_* of the C ABI)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 0, precision: int = SVM_MIXED_BF16,
+                 cluster_size: int = 0, lanes_per_row: int = 0, max_d: int = 0):
+        self.lib = load()
+        _bind_server(self.lib)
+        cfg = svm_server_config(int(budget_bytes), int(max_slots), int(precision), int(cluster_size),
+                                int(lanes_per_row), int(max_d), 0)
+        self.h = ct.c_void_p()
+        rc = self.lib.svm_server_create(ct.byref(cfg), ct.byref(self.h))
+        if rc < 0:
+            raise SvmError(rc, svm_last_error())
+        self.n = {}
+
+    def submit(self, X, y, C: float, gamma: float, tau: float = 1e-3, max_iter: int = 0,
+               check: bool = True):
+        h = _Hold()
+        cx, dev = _csr(h, X)
+        if dev:
+            raise ValueError("submit takes host arrays")
+        p = svm_params(float(C), float(gamma), float(tau), int(max_iter), 0, 0, None, None, 0, 0, 0, 0, 0)
+        t = ct.c_uint64(0)
+        rc = self.lib.svm_server_submit(self.h, ct.byref(cx), h.np(y, np.int8), ct.byref(p), ct.byref(t))
+        if rc < 0:
+            if check:
+                raise SvmError(rc, svm_last_error())
+            return rc
+        self.n[t.value] = int(X.n)
+        return t.value
+
+    def _out(self, rc, ticket, r, a, tm):
+        if rc == SVM_PENDING:
+            return None
+        self.n.pop(ticket, None)
+        return {"status": rc, "b": r.b, "b_up": r.b_up, "b_low": r.b_low, "objective": r.objective,
+                "iters": r.iters, "n_sv": r.n_sv, "alpha": a,
+                "time_to_model_ms": tm.submit_to_done_ms, "queue_ms": tm.submit_to_admit_ms,
+                "run_ms": tm.admit_to_done_ms, "error": svm_last_error() if rc < 0 else ""}
+
+    def poll(self, ticket: int):
+        r, tm = svm_result(), svm_server_times()
+        a = np.zeros(self.n.get(ticket, 0))
+        rc = self.lib.svm_server_poll(self.h, ticket, ct.byref(r), a.ctypes.data if len(a) else None,
+                                      ct.byref(tm))
+        return self._out(rc, ticket, r, a, tm)
+
+    def wait(self, ticket: int, timeout: float = 600.0):
+        r, tm = svm_result(), svm_server_times()
+        a = np.zeros(self.n.get(ticket, 0))
+        rc = self.lib.svm_server_wait(self.h, ticket, float(timeout), ct.byref(r),
+                                      a.ctypes.data if len(a) else None, ct.byref(tm))
+        return self._out(rc, ticket, r, a, tm)
+
+    def cancel(self, ticket: int) -> int:
+        return self.lib.svm_server_cancel(self.h, ticket)
+
+    def stats(self) -> dict:
+        i = svm_server_info()
+        self.lib.svm_server_stats(self.h, ct.byref(i))
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.svm_server_destroy(self.h)
+            self.h = ct.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

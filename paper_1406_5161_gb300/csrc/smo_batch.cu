@@ -24,6 +24,21 @@ namespace svmgb {
 namespace smo {
 namespace {
 
+__device__ __forceinline__ unsigned ld_acquire_sys_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int *p)
+{
+    return *reinterpret_cast<const volatile int *>(p);
+}
+__device__ __forceinline__ void st_release_sys_i32(int *p, int v)
+{
+    asm volatile("st.release.sys.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 struct __align__(16) BatchFinish {
     double sum_a, sum_ayfy, sum_f0;
     long long n0, nsv;
@@ -43,7 +58,7 @@ struct BatchShared {
     int job;
 };
 
-template <int MODE, int LPR, bool DENSE>
+template <int MODE, int LPR>
 __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
 {
     using Tgt = typename RowMath<MODE>::Tgt;
@@ -55,9 +70,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
     const int csize = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int d = B.d;
+    const int dmax = B.d;   // target buffers hold this many columns
     const int maxnnz = B.maxnnz > 0 ? B.maxnnz : 1;
-    const SmoLayout L = smo_layout(MODE, d, B.ktab_len, maxnnz, 0, 0, 0);
+    const SmoLayout L = smo_layout(MODE, dmax, B.ktab_len, maxnnz, 0, 0, 0);
     Tgt *tbuf = reinterpret_cast<Tgt *>(dsm + L.tgt);
     int *tcol = reinterpret_cast<int *>(dsm + L.tcol);
     double *ktab = reinterpret_cast<double *>(dsm + L.ktab);
@@ -66,25 +81,59 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
     for (;;) {
         // ---- next job from the work-list, broadcast to the cluster
         if (crank == 0 && tid == 0) {
-            const int j = atomicAdd(B.next_job, 1);
+            int j = INT_MAX;
+            if (!B.ring) {
+                j = atomicAdd(B.next_job, 1);
+                if (j >= B.njobs) j = INT_MAX;
+            } else {
+                // server: wait (bounded by the idle limit) for a published slot
+                const uint64_t t0 = global_ns();
+                for (;;) {
+                    const unsigned tail = ld_acquire_sys_u32(B.ring_tail);
+                    const unsigned head = (unsigned)atomicAdd(B.next_job, 0);
+                    if (head < tail) {
+                        if ((unsigned)atomicCAS(B.next_job, (int)head, (int)(head + 1)) == head) {
+                            j = ld_volatile_i32(B.ring + (head % (unsigned)B.ring_cap));
+                            break;
+                        }
+                        continue;
+                    }
+                    if (ld_volatile_i32(B.shutdown)) break;
+                    if (global_ns() - t0 > (uint64_t)B.idle_ns) break;
+                    __nanosleep(2000);
+                }
+            }
             for (int r = 0; r < csize; ++r) *cluster.map_shared_rank(&sh.job, r) = j;
         }
         cluster.sync();
         const int job = sh.job;
-        if (job >= B.njobs) break;
+        if (job == INT_MAX) break;
         const BatchJobDev J = B.jobs[job];
-        const int64_t off = J.off;
+        // the job's matrix (shared by all jobs of a batch, own per served job)
+        const int d = J.d;
+        const bool dense = J.dense != 0;
+        const int64_t *indptr = J.indptr;
+        const int32_t *indices = J.indices;
+        const float *values = J.values;
+        const float *vmix = J.vmix;
+        const __nv_bfloat16 *dmat = J.dmat;
+        const double *norm = J.norm;
+        const float *normf = J.normf;
         const int m = J.nrows;
+        const int8_t *yj = J.y;
+        double *aj = J.alpha;
+        double *fj = J.f;
+        uint8_t *sj = J.status;
         const int lo = (int)((int64_t)m * crank / csize);
         const int hi = (int)((int64_t)m * (crank + 1) / csize);
         const double C = J.C, gamma = J.gamma;
         const float gammaf = (float)gamma;
         const double snap = 1e-12 * C, c_snap = C - snap;
         const double thr = 2.0 * J.tau;
-        const int32_t *rows = B.rows + off;
+        const int32_t *rows = J.rows;
 
         // ---- job set-up: tables, empty target buffers, alpha = 0, f = -y
-        for (int c = tid; c < 2 * d; c += kThreads) tgt_clear<MODE>(tbuf[c]);
+        for (int c = tid; c < 2 * dmax; c += kThreads) tgt_clear<MODE>(tbuf[c]);
         if constexpr (MODE == MODE_BINARY) {
             for (int k = tid; k < B.ktab_len; k += kThreads) {
                 const double kv = exp(-gamma * (double)k);
@@ -94,10 +143,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
             }
         }
         for (int r = lo + tid; r < hi; r += kThreads) {
-            const int8_t yr = B.y[off + r];
-            B.alpha[off + r] = 0.0;
-            B.f[off + r] = -(double)yr;
-            B.status[off + r] = (uint8_t)(st_of(yr, 0.0, 1.0) | (yr > 0 ? 0x80 : 0));
+            const int8_t yr = yj[r];
+            aj[r] = 0.0;
+            fj[r] = -(double)yr;
+            sj[r] = (uint8_t)(st_of(yr, 0.0, 1.0) | (yr > 0 ? 0x80 : 0));
         }
         __syncthreads();
 
@@ -111,34 +160,36 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
         int status_code = 0;
         for (;;) {
             const int buf = (int)(iter & 1);
-            Tgt *T = tbuf + (size_t)buf * d;
+            Tgt *T = tbuf + (size_t)buf * dmax;
             int *tcu = tcol + (size_t)(buf * 2 + 0) * maxnnz;
             int *tcl = tcol + (size_t)(buf * 2 + 1) * maxnnz;
             if (!first) {
                 if (!dless(thr, low.f - up.f)) { status_code = 0; break; }
                 if (iter >= J.max_iter) { status_code = 1; break; }
                 // ---- 1. targets into the shared-memory buffer
-                if constexpr (DENSE) {
-                    const __nv_bfloat16 *ru = B.dense + (size_t)up.p0 * d;
-                    const __nv_bfloat16 *rl = B.dense + (size_t)low.p0 * d;
-                    for (int c = tid; c < d; c += kThreads) {
-                        T[c].x = __bfloat162float(ru[c]);
-                        T[c].y = __bfloat162float(rl[c]);
+                if (dense) {
+                    if constexpr (MODE == MODE_MIXED) {
+                        const __nv_bfloat16 *ru = dmat + (size_t)up.p0 * d;
+                        const __nv_bfloat16 *rl = dmat + (size_t)low.p0 * d;
+                        for (int c = tid; c < d; c += kThreads) {
+                            T[c].x = __bfloat162float(ru[c]);
+                            T[c].y = __bfloat162float(rl[c]);
+                        }
                     }
                 } else {
                     for (int k = tid; k < up.len; k += kThreads) {
-                        const int c = B.indices[up.p0 + k];
+                        const int c = indices[up.p0 + k];
                         tcu[k] = c;
                         if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
-                        else if constexpr (MODE == MODE_FP64) T[c].x = (double)B.values[up.p0 + k];
-                        else T[c].x = B.vmix[up.p0 + k];
+                        else if constexpr (MODE == MODE_FP64) T[c].x = (double)values[up.p0 + k];
+                        else T[c].x = vmix[up.p0 + k];
                     }
                     for (int k = tid; k < low.len; k += kThreads) {
-                        const int c = B.indices[low.p0 + k];
+                        const int c = indices[low.p0 + k];
                         tcl[k] = c;
                         if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
-                        else if constexpr (MODE == MODE_FP64) T[c].y = (double)B.values[low.p0 + k];
-                        else T[c].y = B.vmix[low.p0 + k];
+                        else if constexpr (MODE == MODE_FP64) T[c].y = (double)values[low.p0 + k];
+                        else T[c].y = vmix[low.p0 + k];
                     }
                 }
                 __syncthreads();
@@ -149,8 +200,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                 // ---- 2. pair step (Eq. alphaup with rho = -eta, Platt clip)
                 if (!first) {
                     Acc s = 0;
-                    if constexpr (DENSE) {
-                        for (int c = lane; c < d; c += 32) s = fmaf(T[c].y, T[c].x, s);
+                    if (dense) {
+                        if constexpr (MODE == MODE_MIXED)
+                            for (int c = lane; c < d; c += 32) s = fmaf(T[c].y, T[c].x, s);
                     } else {
                         for (int k = lane; k < low.len; k += 32) {
                             const Tgt t = T[tcl[k]];
@@ -246,28 +298,28 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                             ku = ktab[du2 < 0 ? 0 : du2];
                             kl = ktab[dl2 < 0 ? 0 : dl2];
                         } else if constexpr (MODE == MODE_FP64) {
-                            const double nrm_i = B.norm[g];
+                            const double nrm_i = norm[g];
                             double d2u = up.nrm + nrm_i - 2.0 * su;
                             double d2l = low.nrm + nrm_i - 2.0 * sl;
                             ku = exp(-gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
                             kl = exp(-gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
                         } else {
-                            const float nf = B.normf[g];
+                            const float nf = normf[g];
                             float d2u = (float)up.nrm + nf - 2.0f * su;
                             float d2l = (float)low.nrm + nf - 2.0f * sl;
                             ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
                             kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
                         }
                         fi = fma(dl, kl, fma(du, ku, fi));
-                        B.f[off + r] = fi;
+                        fj[r] = fi;
                         if (r == up.i) {
                             sb = st_u;
-                            B.status[off + r] = sb;
-                            B.alpha[off + r] = au_new;
+                            sj[r] = sb;
+                            aj[r] = au_new;
                         } else if (r == low.i) {
                             sb = st_l;
-                            B.status[off + r] = sb;
-                            B.alpha[off + r] = al_new;
+                            sj[r] = sb;
+                            aj[r] = al_new;
                         }
                     }
                     const uint8_t set = set_bits(sb);
@@ -276,9 +328,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                     if (st_low(set) && ki_less(klo, r, bkl, bil)) { bkl = klo; bil = r; brl = r; }
                 };
                 bool blocked = false;
-                if constexpr (DENSE && LPR == 32) blocked = d <= 256;
+                if constexpr (LPR == 32) blocked = dense && d <= 256;
                 if (blocked) {
-                    if constexpr (DENSE && LPR == 32 && MODE == MODE_MIXED) {
+                    if constexpr (LPR == 32 && MODE == MODE_MIXED) {
                         // 8 rows per warp at a time; lane l covers columns
                         // [8l, 8l+8) of all 8 rows with its target columns in
                         // registers; a butterfly transpose-reduction leaves
@@ -312,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                                 const int r = base + j;
                                 if (!first && r < hi && has_cols) {
                                     const int g = rows[r];
-                                    const uint4 raw = *reinterpret_cast<const uint4 *>(B.dense + (size_t)g * d + c8);
+                                    const uint4 raw = *reinterpret_cast<const uint4 *>(dmat + (size_t)g * d + c8);
                                     const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&raw);
 #pragma unroll
                                     for (int e = 0; e < 4; ++e) {
@@ -349,8 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                             const bool lead = (lane & 3) == 0 && r < hi;
                             if (lead) {
                                 g = rows[r];
-                                fi = B.f[off + r];
-                                sb = B.status[off + r];
+                                fi = fj[r];
+                                sb = sj[r];
                             }
                             wait_step();
                             if (lead) finish_row(r, g, d, su, sl, fi, sb);
@@ -371,19 +423,20 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                         uint8_t sb = 0;
                         if (valid) {
                             g = rows[r];
-                            if constexpr (!DENSE) {
-                                p0 = B.indptr[g];
-                                p1 = B.indptr[g + 1];
+                            if (!dense) {
+                                p0 = indptr[g];
+                                p1 = indptr[g + 1];
                             }
                             if (gl == 0) {
-                                fi = B.f[off + r];
-                                sb = B.status[off + r];
+                                fi = fj[r];
+                                sb = sj[r];
                             }
                         }
                         Acc su = 0, sl = 0;
                         if (!first && valid) {
-                            if constexpr (DENSE) {
-                                const __nv_bfloat16 *xr = B.dense + (size_t)g * d;
+                            if (dense) {
+                                if constexpr (MODE == MODE_MIXED) {
+                                const __nv_bfloat16 *xr = dmat + (size_t)g * d;
                                 for (int c = gl * 8; c < d; c += LPR * 8) {
                                     const uint4 raw = *reinterpret_cast<const uint4 *>(xr + c);
                                     const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&raw);
@@ -397,20 +450,21 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                                         sl = fmaf(v.y, t1.y, sl);
                                     }
                                 }
+                                }
                             } else {
                                 for (int64_t p = p0 + gl; p < p1; p += LPR) {
-                                    const int c = B.indices[p];
+                                    const int c = indices[p];
                                     if constexpr (MODE == MODE_BINARY) {
                                         const unsigned short t = T[c];
                                         su += (int)(t & 0xff);
                                         sl += (int)(t >> 8);
                                     } else if constexpr (MODE == MODE_FP64) {
-                                        const double v = (double)B.values[p];
+                                        const double v = (double)values[p];
                                         const double2 t = T[c];
                                         su = fma(v, t.x, su);
                                         sl = fma(v, t.y, sl);
                                     } else {
-                                        const float v = B.vmix[p];
+                                        const float v = vmix[p];
                                         const float2 t = T[c];
                                         su = fmaf(v, t.x, su);
                                         sl = fmaf(v, t.y, sl);
@@ -434,18 +488,18 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
             auto make_side = [&](int r) {
                 Side sd;
                 const int g = rows[r];
-                const uint8_t sb = B.status[off + r];
-                sd.f = B.f[off + r];
-                sd.a = B.alpha[off + r];
-                if constexpr (MODE == MODE_FP64) sd.nrm = B.norm[g];
-                else if constexpr (MODE == MODE_MIXED) sd.nrm = (double)B.normf[g];
+                const uint8_t sb = sj[r];
+                sd.f = fj[r];
+                sd.a = aj[r];
+                if constexpr (MODE == MODE_FP64) sd.nrm = norm[g];
+                else if constexpr (MODE == MODE_MIXED) sd.nrm = (double)normf[g];
                 else sd.nrm = 0.0;
-                if constexpr (DENSE) {
+                if (dense) {
                     sd.p0 = g;
                     sd.len = d;
                 } else {
-                    sd.p0 = B.indptr[g];
-                    sd.len = (int)(B.indptr[g + 1] - sd.p0);
+                    sd.p0 = indptr[g];
+                    sd.len = (int)(indptr[g + 1] - sd.p0);
                 }
                 sd.i = r;
                 sd.y = y_of(sb);
@@ -487,8 +541,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                 }
             }
             if (prev_valid && warp >= 8) {
-                Tgt *P = tbuf + (size_t)(1 - buf) * d;
-                if constexpr (DENSE) {
+                Tgt *P = tbuf + (size_t)(1 - buf) * dmax;
+                if (dense) {
                     (void)prev_pu;
                     (void)prev_pl;
                 } else {
@@ -538,10 +592,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
         {
             BatchFinish pf = {0, 0, 0, 0, 0, {0, 0}};
             for (int r = lo + tid; r < hi; r += kThreads) {
-                const double a = B.alpha[off + r];
-                const uint8_t sb = B.status[off + r];
+                const double a = aj[r];
+                const uint8_t sb = sj[r];
                 const double yi = (sb & 0x80) ? 1.0 : -1.0;
-                const double fi = B.f[off + r];
+                const double fi = fj[r];
                 pf.sum_a += a;
                 pf.sum_ayfy += a * yi * (fi + yi);
                 if ((sb & 7) == ST_I0) { pf.sum_f0 += fi; pf.n0 += 1; }
@@ -587,6 +641,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                 R.status = status_code;
                 R.n_sv = (int32_t)t.nsv;
                 B.results[job] = R;
+                if (B.done) {
+                    __threadfence_system();
+                    st_release_sys_i32(B.done + job, 1);
+                }
             }
             cluster.sync();   // shared memory of the cluster is reused by the next job
         }
@@ -594,18 +652,26 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
     cluster.sync();
 }
 
-template <int MODE, bool DENSE>
+template <int MODE>
 void *batch_kernel_for(int lpr)
 {
     switch (lpr) {
-    case 1: return (void *)smo_batch_kernel<MODE, 1, DENSE>;
-    case 2: return (void *)smo_batch_kernel<MODE, 2, DENSE>;
-    case 4: return (void *)smo_batch_kernel<MODE, 4, DENSE>;
-    case 8: return (void *)smo_batch_kernel<MODE, 8, DENSE>;
-    case 16: return (void *)smo_batch_kernel<MODE, 16, DENSE>;
-    case 32: return (void *)smo_batch_kernel<MODE, 32, DENSE>;
+    case 1: return (void *)smo_batch_kernel<MODE, 1>;
+    case 2: return (void *)smo_batch_kernel<MODE, 2>;
+    case 4: return (void *)smo_batch_kernel<MODE, 4>;
+    case 8: return (void *)smo_batch_kernel<MODE, 8>;
+    case 16: return (void *)smo_batch_kernel<MODE, 16>;
+    case 32: return (void *)smo_batch_kernel<MODE, 32>;
     default: return nullptr;
     }
+}
+
+void *batch_fn(int mode, int lpr)
+{
+    if (mode == MODE_MIXED) return batch_kernel_for<MODE_MIXED>(lpr);
+    if (mode == MODE_FP64) return batch_kernel_for<MODE_FP64>(lpr);
+    if (mode == MODE_BINARY) return batch_kernel_for<MODE_BINARY>(lpr);
+    return nullptr;
 }
 
 }  // namespace
@@ -618,11 +684,8 @@ size_t smo_batch_smem(int mode, int d, int ktab_len, int maxnnz)
 
 int smo_batch_max_clusters(int mode, int lpr, int dense, size_t smem, int cs)
 {
-    void *fn = nullptr;
-    if (mode == MODE_MIXED && dense) fn = smo::batch_kernel_for<MODE_MIXED, true>(lpr);
-    else if (mode == MODE_MIXED) fn = smo::batch_kernel_for<MODE_MIXED, false>(lpr);
-    else if (mode == MODE_FP64) fn = smo::batch_kernel_for<MODE_FP64, false>(lpr);
-    else fn = smo::batch_kernel_for<MODE_BINARY, false>(lpr);
+    (void)dense;
+    void *fn = smo::batch_fn(mode, lpr);
     if (!fn) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     if (cs > 1 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
@@ -645,11 +708,8 @@ int smo_batch_max_clusters(int mode, int lpr, int dense, size_t smem, int cs)
 cudaError_t launch_smo_batch(int mode, int lpr, int dense, const BatchArgs &a, size_t smem, int cs,
                              int nclusters, cudaStream_t st)
 {
-    void *fn = nullptr;
-    if (mode == MODE_MIXED && dense) fn = smo::batch_kernel_for<MODE_MIXED, true>(lpr);
-    else if (mode == MODE_MIXED) fn = smo::batch_kernel_for<MODE_MIXED, false>(lpr);
-    else if (mode == MODE_FP64 && !dense) fn = smo::batch_kernel_for<MODE_FP64, false>(lpr);
-    else if (mode == MODE_BINARY && !dense) fn = smo::batch_kernel_for<MODE_BINARY, false>(lpr);
+    (void)dense;
+    void *fn = smo::batch_fn(mode, lpr);
     if (!fn || cs < 1 || cs > 16 || nclusters < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

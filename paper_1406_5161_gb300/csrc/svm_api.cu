@@ -10,7 +10,12 @@
 
 #include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -50,6 +55,8 @@ struct Fail {
             throw Fail{e_ == cudaErrorMemoryAllocation ? SVM_ERR_OOM : SVM_ERR_CUDA};   \
         }                                                                                \
     } while (0)
+
+#define CK_NOTHROW(call) (void)(call)
 
 #define ARG_FAIL(...)                 \
     do {                              \
@@ -933,8 +940,7 @@ __global__ void k_iota(int64_t n, int32_t *out)
 }
 
 // per job: row ids in range, labels +-1, both classes present
-__global__ void k_job_check(int njobs, const BatchJobDev *jobs, const int32_t *rows, const int8_t *y, int64_t n,
-                            int *bad)
+__global__ void k_job_check(int njobs, const BatchJobDev *jobs, int64_t n, int *bad)
 {
     const int j = blockIdx.x;
     if (j >= njobs) return;
@@ -944,8 +950,8 @@ __global__ void k_job_check(int njobs, const BatchJobDev *jobs, const int32_t *r
     const BatchJobDev J = jobs[j];
     int b = 0, pos = 0, neg = 0;
     for (int r = threadIdx.x; r < J.nrows; r += blockDim.x) {
-        const int32_t g = rows[J.off + r];
-        const int8_t v = y[J.off + r];
+        const int32_t g = J.rows[r];
+        const int8_t v = J.y[r];
         if (g < 0 || g >= n) b = 1;
         if (v == 1) pos = 1;
         else if (v == -1) neg = 1;
@@ -1051,6 +1057,7 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
 
     // ---- concatenated job arrays
     std::vector<BatchJobDev> hj(n_jobs);
+    std::vector<int64_t> offs(n_jobs);
     int64_t total = 0;
     for (int j = 0; j < n_jobs; ++j) {
         const svm_job &J = jobs[j];
@@ -1059,9 +1066,9 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
         if (!J.y || (!J.alpha_out && !tune_only)) ARG_FAIL("job %d: labels and alpha_out must not be NULL", j);
         if (!(J.C > 0) || !(J.gamma > 0) || !(J.tau > 0)) ARG_FAIL("job %d: C, gamma and tau must be > 0", j);
         if (J.n_rows >= INT32_MAX) ARG_FAIL("job %d: too many rows", j);
-        hj[j].off = total;
+        std::memset(&hj[j], 0, sizeof(BatchJobDev));
+        offs[j] = total;
         hj[j].nrows = (int32_t)J.n_rows;
-        hj[j].pad = 0;
         hj[j].C = J.C;
         hj[j].gamma = J.gamma;
         hj[j].tau = J.tau;
@@ -1074,30 +1081,50 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
         for (int j = 0; j < n_jobs; ++j) {
             const svm_job &J = jobs[j];
             if (J.rows)
-                CK(cudaMemcpyAsync(rows + hj[j].off, J.rows, 4 * J.n_rows, cudaMemcpyDeviceToDevice, st));
+                CK(cudaMemcpyAsync(rows + offs[j], J.rows, 4 * J.n_rows, cudaMemcpyDeviceToDevice, st));
             else {
-                k_iota<<<grid1(J.n_rows), 256, 0, st>>>(J.n_rows, rows + hj[j].off);
+                k_iota<<<grid1(J.n_rows), 256, 0, st>>>(J.n_rows, rows + offs[j]);
                 CK(cudaGetLastError());
                 ++launches;
             }
-            CK(cudaMemcpyAsync(ycat + hj[j].off, J.y, J.n_rows, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(ycat + offs[j], J.y, J.n_rows, cudaMemcpyDeviceToDevice, st));
         }
     } else {
         std::vector<int32_t> hr(total);
         std::vector<int8_t> hy(total);
         for (int j = 0; j < n_jobs; ++j) {
             const svm_job &J = jobs[j];
-            for (int64_t r = 0; r < J.n_rows; ++r) hr[hj[j].off + r] = J.rows ? J.rows[r] : (int32_t)r;
-            std::memcpy(hy.data() + hj[j].off, J.y, J.n_rows);
+            for (int64_t r = 0; r < J.n_rows; ++r) hr[offs[j] + r] = J.rows ? J.rows[r] : (int32_t)r;
+            std::memcpy(hy.data() + offs[j], J.y, J.n_rows);
         }
         CK(cudaMemcpyAsync(rows, hr.data(), 4 * total, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(ycat, hy.data(), total, cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
     }
+    double *alpha = ar.alloc<double>(total);
+    double *f = ar.alloc<double>(total);
+    uint8_t *status = ar.alloc<uint8_t>(total);
+    for (int j = 0; j < n_jobs; ++j) {
+        BatchJobDev &J = hj[j];
+        J.indptr = D.indptr;
+        J.indices = D.indices;
+        J.values = D.values;
+        J.vmix = D.vmix;
+        J.dmat = P.dense_rows;
+        J.norm = D.norm;
+        J.normf = D.normf;
+        J.d = P.d_eff;
+        J.dense = P.dense;
+        J.rows = rows + offs[j];
+        J.y = ycat + offs[j];
+        J.alpha = alpha + offs[j];
+        J.f = f + offs[j];
+        J.status = status + offs[j];
+    }
     BatchJobDev *djobs = ar.alloc<BatchJobDev>(n_jobs);
     CK(cudaMemcpyAsync(djobs, hj.data(), sizeof(BatchJobDev) * n_jobs, cudaMemcpyHostToDevice, st));
     int *bad = ar.alloc<int>(n_jobs);
-    k_job_check<<<n_jobs, 256, 0, st>>>(n_jobs, djobs, rows, ycat, D.n, bad);
+    k_job_check<<<n_jobs, 256, 0, st>>>(n_jobs, djobs, D.n, bad);
     CK(cudaGetLastError());
     ++launches;
     std::vector<int> hbad(n_jobs);
@@ -1108,28 +1135,12 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
         if (hbad[j] == 2) ARG_FAIL("job %d: both classes must be present", j);
     }
 
-    double *alpha = ar.alloc<double>(total);
-    double *f = ar.alloc<double>(total);
-    uint8_t *status = ar.alloc<uint8_t>(total);
     BatchResultDev *dres = ar.alloc<BatchResultDev>(n_jobs);
     int *next_job = ar.alloc<int>(1);
     BatchArgs A;
     std::memset(&A, 0, sizeof A);
-    A.n = D.n;
     A.d = P.d_eff;
     A.njobs = n_jobs;
-    A.indptr = D.indptr;
-    A.indices = D.indices;
-    A.values = D.values;
-    A.vmix = D.vmix;
-    A.dense = P.dense_rows;
-    A.norm = D.norm;
-    A.normf = D.normf;
-    A.rows = rows;
-    A.y = ycat;
-    A.alpha = alpha;
-    A.f = f;
-    A.status = status;
     A.jobs = djobs;
     A.results = dres;
     A.ktab_len = P.ktab_len;
@@ -1201,7 +1212,7 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
     CK(cudaMemcpyAsync(hres.data(), dres, sizeof(BatchResultDev) * n_jobs, cudaMemcpyDeviceToHost, st));
     if (X->on_device) {
         for (int j = 0; j < n_jobs; ++j)
-            CK(cudaMemcpyAsync(jobs[j].alpha_out, alpha + hj[j].off, 8 * jobs[j].n_rows, cudaMemcpyDeviceToDevice,
+            CK(cudaMemcpyAsync(jobs[j].alpha_out, alpha + offs[j], 8 * jobs[j].n_rows, cudaMemcpyDeviceToDevice,
                                st));
         CK(cudaStreamSynchronize(st));
     } else {
@@ -1209,7 +1220,7 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
         CK(cudaMemcpyAsync(ha.data(), alpha, 8 * total, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int j = 0; j < n_jobs; ++j)
-            std::memcpy(jobs[j].alpha_out, ha.data() + hj[j].off, 8 * jobs[j].n_rows);
+            std::memcpy(jobs[j].alpha_out, ha.data() + offs[j], 8 * jobs[j].n_rows);
     }
     int64_t iters = 0;
     int rc = SVM_OK;
@@ -1231,6 +1242,275 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
     cfg->ms_total = elapsed_ms(t_start);
     g_launches += launches;
     return rc;
+}
+
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of training jobs that arrive over time
+// ---------------------------------------------------------------------------
+
+struct SrvJob {
+    uint64_t ticket = 0;
+    int state = 0;           // 0 queued, 1 on the device, 2 finished
+    int slot = -1;
+    bool cancelled = false;
+    int64_t n = 0, d = 0, nnz = 0;
+    std::vector<int64_t> indptr;
+    std::vector<int32_t> indices;
+    std::vector<float> values;
+    std::vector<int8_t> y;
+    double C = 1, gamma = 1, tau = 1e-3;
+    int64_t max_iter = 0;
+    size_t bytes = 0;
+    void *mem = nullptr;
+    double *alpha_d = nullptr;
+    int rc = SVM_PENDING;
+    std::string err;
+    svm_result res{};
+    std::vector<double> alpha;
+    std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+};
+
+struct EngineCtl {
+    unsigned tail;
+    int shutdown;
+    int pad[30];
+};
+
+struct Server {
+    svm_server_config cfg{};
+    int mode = MODE_MIXED;
+    size_t used = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<uint64_t, std::shared_ptr<SrvJob>> jobs;
+    std::deque<uint64_t> queue;
+    std::vector<int> free_slots;
+    std::vector<std::shared_ptr<SrvJob>> running;
+    uint64_t next_ticket = 1;
+    std::thread worker;
+    bool stop = false;
+    int device = 0;
+    cudaStream_t s_engine = nullptr, s_side = nullptr;
+    EngineCtl *ctl_h = nullptr, *ctl_d = nullptr;
+    int32_t *ring_h = nullptr, *ring_d = nullptr;
+    BatchJobDev *slots_h = nullptr, *slots_d = nullptr;
+    BatchResultDev *res_h = nullptr, *res_d = nullptr;
+    int *done_h = nullptr, *done_d = nullptr;
+    int *next_d = nullptr;
+    IngestInfo *info_h = nullptr, *info_d = nullptr;
+    size_t smem = 0;
+    int nclusters = 0;
+    int64_t engine_launches = 0;
+    std::string fatal;
+};
+
+size_t srv_job_bytes(const SrvJob &J, int mode)
+{
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const bool dense = mode == MODE_MIXED && J.nnz == J.n * J.d;
+    const size_t dpad = (size_t)((J.d + 7) & ~7ll);
+    size_t b = a(8 * (J.n + 1)) + a(4 * J.nnz) + a(4 * J.nnz) + a(4 * J.n) + a(J.n) + a(8 * J.n) * 2 + a(J.n);
+    if (mode == MODE_MIXED) b += a(4 * J.nnz) + a(4 * J.n);
+    else b += a(8 * J.n);
+    if (dense) b += a(2 * J.n * dpad);
+    return b;
+}
+
+// one engine launch; the engine runs until shutdown or until idle
+void srv_launch_engine(Server &S)
+{
+    BatchArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.d = S.cfg.max_d;
+    A.njobs = 0;
+    A.jobs = S.slots_d;
+    A.results = S.res_d;
+    A.next_job = S.next_d;
+    A.ktab_len = 0;
+    A.maxnnz = S.cfg.max_d;
+    A.ring = S.ring_d;
+    A.ring_tail = &S.ctl_d->tail;
+    A.ring_cap = S.cfg.max_slots;
+    A.shutdown = &S.ctl_d->shutdown;
+    A.done = S.done_d;
+    A.idle_ns = 500ll * 1000 * 1000;
+    CK(launch_smo_batch(S.mode, S.cfg.lanes_per_row, 0, A, S.smem, S.cfg.cluster_size, S.nclusters, S.s_engine));
+    ++S.engine_launches;
+    g_launches += 1;
+}
+
+// stage a queued job on the device and publish it to the engine (lock held)
+void srv_admit(Server &S, const std::shared_ptr<SrvJob> &J)
+{
+    cudaStream_t st = S.s_side;
+    const bool mixed = S.mode == MODE_MIXED;
+    const bool dense = mixed && J->nnz == J->n * J->d;
+    const int dpad = (int)((J->d + 7) & ~7ll);
+    CK(cudaMallocAsync(&J->mem, J->bytes, st));
+    unsigned char *p = static_cast<unsigned char *>(J->mem);
+    auto take = [&](size_t x) {
+        unsigned char *r = p;
+        p += (x + 255) & ~(size_t)255;
+        return r;
+    };
+    int64_t *indptr = reinterpret_cast<int64_t *>(take(8 * (J->n + 1)));
+    int32_t *indices = reinterpret_cast<int32_t *>(take(4 * J->nnz));
+    float *values = reinterpret_cast<float *>(take(4 * J->nnz));
+    int32_t *rows = reinterpret_cast<int32_t *>(take(4 * J->n));
+    int8_t *y = reinterpret_cast<int8_t *>(take(J->n));
+    double *alpha = reinterpret_cast<double *>(take(8 * J->n));
+    double *f = reinterpret_cast<double *>(take(8 * J->n));
+    uint8_t *status = reinterpret_cast<uint8_t *>(take(J->n));
+    float *vmix = nullptr, *normf = nullptr;
+    double *norm = nullptr;
+    __nv_bfloat16 *dmat = nullptr;
+    if (mixed) {
+        vmix = reinterpret_cast<float *>(take(4 * J->nnz));
+        normf = reinterpret_cast<float *>(take(4 * J->n));
+    } else {
+        norm = reinterpret_cast<double *>(take(8 * J->n));
+    }
+    if (dense) dmat = reinterpret_cast<__nv_bfloat16 *>(take(2 * (size_t)J->n * dpad));
+    CK(cudaMemcpyAsync(indptr, J->indptr.data(), 8 * (J->n + 1), cudaMemcpyHostToDevice, st));
+    if (J->nnz) {
+        CK(cudaMemcpyAsync(indices, J->indices.data(), 4 * J->nnz, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(values, J->values.data(), 4 * J->nnz, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(y, J->y.data(), J->n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(S.info_d, 0, sizeof(IngestInfo), st));
+    k_validate<<<grid1(J->n), 256, 0, st>>>(J->n, J->d, indptr, indices, values, y, S.info_d);
+    k_norms<<<grid1(J->n), 256, 0, st>>>(J->n, indptr, values, norm, vmix, normf);
+    k_iota<<<grid1(J->n), 256, 0, st>>>(J->n, rows);
+    if (dense) k_dense_bf16<<<(unsigned)J->n, 128, 0, st>>>(J->n, (int)J->d, dpad, indptr, indices, vmix, dmat);
+    CK(cudaGetLastError());
+    g_launches += dense ? 4 : 3;
+    CK(cudaMemcpyAsync(S.info_h, S.info_d, sizeof(IngestInfo), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const IngestInfo &h = *S.info_h;
+    std::string bad;
+    if (h.bad_indptr) bad = "indptr is not non-decreasing from 0";
+    else if (h.bad_index) bad = "column indices must be strictly increasing within a row and < d";
+    else if (h.nonfinite) bad = "values must be finite";
+    else if (h.bad_y) bad = "labels must be +1 or -1";
+    else if (h.npos == 0 || (int64_t)h.npos == J->n) bad = "both classes must be present";
+    if (!bad.empty()) {
+        CK(cudaFreeAsync(J->mem, st));
+        J->mem = nullptr;
+        J->rc = SVM_ERR_ARG;
+        J->err = bad;
+        J->state = 2;
+        J->t_done = std::chrono::steady_clock::now();
+        S.used -= J->bytes;
+        return;
+    }
+    const int slot = S.free_slots.back();
+    S.free_slots.pop_back();
+    J->slot = slot;
+    J->alpha_d = alpha;
+    BatchJobDev &D = S.slots_h[slot];
+    std::memset(&D, 0, sizeof D);
+    D.indptr = indptr;
+    D.indices = indices;
+    D.values = values;
+    D.vmix = vmix;
+    D.dmat = dmat;
+    D.norm = norm;
+    D.normf = normf;
+    D.rows = rows;
+    D.y = y;
+    D.alpha = alpha;
+    D.f = f;
+    D.status = status;
+    D.nrows = (int32_t)J->n;
+    D.d = dense ? dpad : (int32_t)J->d;
+    D.dense = dense ? 1 : 0;
+    D.C = J->C;
+    D.gamma = J->gamma;
+    D.tau = J->tau;
+    D.max_iter = J->max_iter > 0 ? J->max_iter : 100 * J->n + 1000000;
+    __atomic_store_n(&S.done_h[slot], 0, __ATOMIC_RELAXED);
+    const unsigned tail = __atomic_load_n(&S.ctl_h->tail, __ATOMIC_RELAXED);
+    S.ring_h[tail % (unsigned)S.cfg.max_slots] = slot;
+    __atomic_store_n(&S.ctl_h->tail, tail + 1, __ATOMIC_RELEASE);   // publishes descriptor and ring entry
+    J->state = 1;
+    J->t_admit = std::chrono::steady_clock::now();
+    S.running.push_back(J);
+}
+
+// collect a finished job (lock held)
+void srv_finish(Server &S, const std::shared_ptr<SrvJob> &J)
+{
+    const BatchResultDev &R = S.res_h[J->slot];
+    J->res.b = R.b;
+    J->res.b_up = R.b_up;
+    J->res.b_low = R.b_low;
+    J->res.objective = R.objective;
+    J->res.iters = R.iters;
+    J->res.status = R.status == 1 ? SVM_NOT_CONVERGED : SVM_OK;
+    J->res.n_sv = R.n_sv;
+    J->alpha.resize(J->n);
+    CK(cudaMemcpyAsync(J->alpha.data(), J->alpha_d, 8 * J->n, cudaMemcpyDeviceToHost, S.s_side));
+    CK(cudaFreeAsync(J->mem, S.s_side));
+    CK(cudaStreamSynchronize(S.s_side));
+    J->mem = nullptr;
+    J->rc = J->cancelled ? SVM_ERR_CANCELLED : J->res.status;
+    J->state = 2;
+    J->t_done = std::chrono::steady_clock::now();
+    S.used -= J->bytes;
+    S.free_slots.push_back(J->slot);
+}
+
+void srv_loop(Server *S)
+{
+    CK_NOTHROW(cudaSetDevice(S->device));
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        try {
+            // finished jobs
+            for (size_t k = 0; k < S->running.size();) {
+                auto &J = S->running[k];
+                if (__atomic_load_n(&S->done_h[J->slot], __ATOMIC_ACQUIRE)) {
+                    srv_finish(*S, J);
+                    S->running.erase(S->running.begin() + k);
+                    S->cv.notify_all();
+                } else {
+                    ++k;
+                }
+            }
+            // admission: first come, first served while a slot and budget are free
+            while (!S->queue.empty() && !S->free_slots.empty()) {
+                auto it = S->jobs.find(S->queue.front());
+                if (it == S->jobs.end() || it->second->state != 0) {
+                    S->queue.pop_front();
+                    continue;
+                }
+                auto J = it->second;
+                if (S->used + J->bytes > S->cfg.budget_bytes) break;
+                S->queue.pop_front();
+                S->used += J->bytes;
+                srv_admit(*S, J);
+                if (J->state == 2) S->cv.notify_all();
+            }
+            // the engine leaves when idle: start it again while work is out
+            if (!S->running.empty() && cudaStreamQuery(S->s_engine) == cudaSuccess) srv_launch_engine(*S);
+        } catch (const Fail &) {
+            S->fatal = g_err;
+            for (auto &J : S->running) {
+                J->rc = SVM_ERR_CUDA;
+                J->err = S->fatal;
+                J->state = 2;
+            }
+            S->running.clear();
+            S->cv.notify_all();
+        }
+        S->cv.wait_for(lk, std::chrono::microseconds(S->running.empty() && S->queue.empty() ? 2000 : 50));
+    }
+}
+
+double ms_between(std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
 // ---------------------------------------------------------------------------
@@ -1505,6 +1785,274 @@ int svm_batch_autotune(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, sv
         set_err("unexpected host exception");
         return SVM_ERR_CUDA;
     }
+}
+
+
+struct svm_server {
+    Server impl;
+};
+
+int svm_server_create(const svm_server_config *config, svm_server **out)
+{
+    g_err.clear();
+    try {
+        if (!config || !out) ARG_FAIL("NULL argument");
+        svm_server_config c = *config;
+        if (c.budget_bytes == 0) ARG_FAIL("budget_bytes must be > 0");
+        if (c.max_slots <= 0) c.max_slots = 64;
+        if (c.max_slots > 1024) ARG_FAIL("max_slots must be <= 1024");
+        if (c.precision != SVM_FP64 && c.precision != SVM_MIXED_BF16 && c.precision != SVM_MIXED_BF16_SIMT)
+            ARG_FAIL("unknown precision %d", c.precision);
+        if (c.cluster_size <= 0) c.cluster_size = 16;
+        if (c.cluster_size > 16 || (c.cluster_size & (c.cluster_size - 1))) ARG_FAIL("cluster_size must be a power of two <= 16");
+        if (c.lanes_per_row <= 0) c.lanes_per_row = 2;
+        {
+            int l = 1;
+            while (l < 32 && l < c.lanes_per_row) l <<= 1;
+            c.lanes_per_row = l;
+        }
+        if (c.max_d <= 0) c.max_d = 2048;
+        c.max_d = (c.max_d + 7) & ~7;
+        auto S = std::make_unique<svm_server>();
+        Server &V = S->impl;
+        V.cfg = c;
+        V.mode = c.precision == SVM_FP64 ? MODE_FP64 : MODE_MIXED;
+        V.smem = smo_batch_smem(V.mode, c.max_d, 0, c.max_d);
+        if (V.smem > smem_limit() - 12288) ARG_FAIL("max_d = %d does not fit the engine's shared memory", c.max_d);
+        V.nclusters = smo_batch_max_clusters(V.mode, c.lanes_per_row, 0, V.smem, c.cluster_size);
+        if (V.nclusters < 1) ARG_FAIL("cluster_size %d does not fit this device", c.cluster_size);
+        CK(cudaGetDevice(&V.device));
+        CK(cudaStreamCreateWithFlags(&V.s_engine, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&V.s_side, cudaStreamNonBlocking));
+        auto mapped = [&](auto **h, auto **d, size_t bytes) {
+            void *p = nullptr;
+            CK(cudaHostAlloc(&p, bytes, cudaHostAllocMapped));
+            std::memset(p, 0, bytes);
+            void *q = nullptr;
+            CK(cudaHostGetDevicePointer(&q, p, 0));
+            *h = static_cast<std::remove_reference_t<decltype(**h)> *>(p);
+            *d = static_cast<std::remove_reference_t<decltype(**d)> *>(q);
+        };
+        mapped(&V.ctl_h, &V.ctl_d, sizeof(EngineCtl));
+        mapped(&V.ring_h, &V.ring_d, sizeof(int32_t) * c.max_slots);
+        mapped(&V.slots_h, &V.slots_d, sizeof(BatchJobDev) * c.max_slots);
+        mapped(&V.res_h, &V.res_d, sizeof(BatchResultDev) * c.max_slots);
+        mapped(&V.done_h, &V.done_d, sizeof(int) * c.max_slots);
+        mapped(&V.info_h, &V.info_d, sizeof(IngestInfo));
+        // the ingest check writes into device memory, then copies to the mapped record
+        void *infod = nullptr;
+        CK(cudaMalloc(&infod, sizeof(IngestInfo)));
+        V.info_d = static_cast<IngestInfo *>(infod);
+        void *nd = nullptr;
+        CK(cudaMalloc(&nd, sizeof(int)));
+        CK(cudaMemset(nd, 0, sizeof(int)));
+        V.next_d = static_cast<int *>(nd);
+        for (int k = c.max_slots - 1; k >= 0; --k) V.free_slots.push_back(k);
+        V.worker = std::thread(srv_loop, &V);
+        *out = S.release();
+        return SVM_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_server_submit(svm_server *srv, const svm_csr *X, const int8_t *y, const svm_params *params,
+                      uint64_t *ticket)
+{
+    g_err.clear();
+    try {
+        if (!srv || !X || !y || !params || !ticket) ARG_FAIL("NULL argument");
+        if (X->on_device) ARG_FAIL("svm_server_submit takes host buffers (they are copied)");
+        if (X->n < 2 || X->d < 1) ARG_FAIL("need n >= 2 and d >= 1");
+        if (X->n >= INT32_MAX) ARG_FAIL("n must be < 2^31");
+        if (!(params->C > 0) || !(params->gamma > 0) || !(params->tau > 0)) ARG_FAIL("C, gamma and tau must be > 0");
+        Server &V = srv->impl;
+        if (X->d > V.cfg.max_d) {
+            set_err("d = %lld exceeds the server's max_d = %d", (long long)X->d, V.cfg.max_d);
+            throw Fail{SVM_ERR_UNSUPPORTED};
+        }
+        auto J = std::make_shared<SrvJob>();
+        J->n = X->n;
+        J->d = X->d;
+        J->nnz = X->indptr[X->n];
+        if (J->nnz < 0) ARG_FAIL("indptr[n] < 0");
+        J->indptr.assign(X->indptr, X->indptr + X->n + 1);
+        J->indices.assign(X->indices, X->indices + J->nnz);
+        if (X->values) J->values.assign(X->values, X->values + J->nnz);
+        else J->values.assign(J->nnz, 1.0f);
+        J->y.assign(y, y + X->n);
+        J->C = params->C;
+        J->gamma = params->gamma;
+        J->tau = params->tau;
+        J->max_iter = params->max_iter;
+        J->bytes = srv_job_bytes(*J, V.mode);
+        if (J->bytes > V.cfg.budget_bytes) {
+            set_err("job needs %zu bytes of device memory; the budget is %zu", J->bytes, V.cfg.budget_bytes);
+            throw Fail{SVM_ERR_BUDGET};
+        }
+        J->t_submit = std::chrono::steady_clock::now();
+        {
+            std::lock_guard<std::mutex> lk(V.mu);
+            if (!V.fatal.empty()) {
+                set_err("server stopped: %s", V.fatal.c_str());
+                throw Fail{SVM_ERR_CUDA};
+            }
+            J->ticket = V.next_ticket++;
+            V.jobs[J->ticket] = J;
+            V.queue.push_back(J->ticket);
+        }
+        V.cv.notify_all();
+        *ticket = J->ticket;
+        return SVM_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+static int srv_take(Server &V, uint64_t ticket, svm_result *res, double *alpha_out, svm_server_times *times)
+{
+    auto it = V.jobs.find(ticket);
+    if (it == V.jobs.end()) ARG_FAIL("unknown ticket %llu", (unsigned long long)ticket);
+    auto J = it->second;
+    if (J->state != 2) return SVM_PENDING;
+    if (res) *res = J->res;
+    if (alpha_out && !J->alpha.empty()) std::memcpy(alpha_out, J->alpha.data(), 8 * J->n);
+    if (times) {
+        times->submit_to_admit_ms = J->t_admit.time_since_epoch().count() ? ms_between(J->t_submit, J->t_admit) : 0.0;
+        times->admit_to_done_ms = J->t_admit.time_since_epoch().count() ? ms_between(J->t_admit, J->t_done) : 0.0;
+        times->submit_to_done_ms = ms_between(J->t_submit, J->t_done);
+    }
+    const int rc = J->rc;
+    if (rc < 0) set_err("%s", J->err.empty() ? "job failed" : J->err.c_str());
+    V.jobs.erase(it);
+    return rc;
+}
+
+int svm_server_poll(svm_server *srv, uint64_t ticket, svm_result *res, double *alpha_out,
+                    svm_server_times *times)
+{
+    g_err.clear();
+    try {
+        if (!srv) ARG_FAIL("NULL server");
+        Server &V = srv->impl;
+        std::lock_guard<std::mutex> lk(V.mu);
+        return srv_take(V, ticket, res, alpha_out, times);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_server_wait(svm_server *srv, uint64_t ticket, double timeout_s, svm_result *res, double *alpha_out,
+                    svm_server_times *times)
+{
+    g_err.clear();
+    try {
+        if (!srv) ARG_FAIL("NULL server");
+        Server &V = srv->impl;
+        std::unique_lock<std::mutex> lk(V.mu);
+        auto it = V.jobs.find(ticket);
+        if (it == V.jobs.end()) ARG_FAIL("unknown ticket %llu", (unsigned long long)ticket);
+        auto J = it->second;
+        const auto until = std::chrono::steady_clock::now() +
+                           std::chrono::microseconds((int64_t)(std::max(0.0, timeout_s) * 1e6));
+        while (J->state != 2) {
+            if (V.cv.wait_until(lk, until) == std::cv_status::timeout && J->state != 2) return SVM_PENDING;
+        }
+        return srv_take(V, ticket, res, alpha_out, times);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_server_cancel(svm_server *srv, uint64_t ticket)
+{
+    g_err.clear();
+    try {
+        if (!srv) ARG_FAIL("NULL server");
+        Server &V = srv->impl;
+        std::lock_guard<std::mutex> lk(V.mu);
+        auto it = V.jobs.find(ticket);
+        if (it == V.jobs.end()) ARG_FAIL("unknown ticket %llu", (unsigned long long)ticket);
+        auto J = it->second;
+        if (J->state == 0) {
+            J->state = 2;
+            J->rc = SVM_ERR_CANCELLED;
+            J->err = "cancelled";
+            J->t_done = std::chrono::steady_clock::now();
+            V.cv.notify_all();
+        } else if (J->state == 1) {
+            J->cancelled = true;
+        }
+        return SVM_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_server_stats(svm_server *srv, svm_server_info *info)
+{
+    g_err.clear();
+    if (!srv || !info) {
+        set_err("NULL argument");
+        return SVM_ERR_ARG;
+    }
+    Server &V = srv->impl;
+    std::lock_guard<std::mutex> lk(V.mu);
+    info->bytes_in_use = V.used;
+    info->budget_bytes = V.cfg.budget_bytes;
+    info->queued = 0;
+    for (auto t : V.queue) {
+        auto it = V.jobs.find(t);
+        if (it != V.jobs.end() && it->second->state == 0) ++info->queued;
+    }
+    info->running = (int32_t)V.running.size();
+    info->clusters = V.nclusters;
+    info->cluster_size = V.cfg.cluster_size;
+    info->engine_launches = V.engine_launches;
+    return SVM_OK;
+}
+
+int svm_server_destroy(svm_server *srv)
+{
+    g_err.clear();
+    if (!srv) return SVM_OK;
+    Server &V = srv->impl;
+    {
+        std::lock_guard<std::mutex> lk(V.mu);
+        V.stop = true;
+    }
+    V.cv.notify_all();
+    if (V.worker.joinable()) V.worker.join();
+    if (V.ctl_h) __atomic_store_n(&V.ctl_h->shutdown, 1, __ATOMIC_RELEASE);
+    int rc = SVM_OK;
+    if (V.s_engine && cudaStreamSynchronize(V.s_engine) != cudaSuccess) rc = SVM_ERR_CUDA;
+    for (auto &kv : V.jobs)
+        if (kv.second->mem) cudaFreeAsync(kv.second->mem, V.s_side);
+    if (V.s_side) cudaStreamSynchronize(V.s_side);
+    for (void *p : {(void *)V.ctl_h, (void *)V.ring_h, (void *)V.slots_h, (void *)V.res_h, (void *)V.done_h,
+                    (void *)V.info_h})
+        if (p) cudaFreeHost(p);
+    if (V.info_d) cudaFree(V.info_d);
+    if (V.next_d) cudaFree(V.next_d);
+    if (V.s_engine) cudaStreamDestroy(V.s_engine);
+    if (V.s_side) cudaStreamDestroy(V.s_side);
+    delete srv;
+    return rc;
 }
 
 int svm_train_fixed_workspace(const svm_csr *X, const int8_t *y, const svm_params *params,

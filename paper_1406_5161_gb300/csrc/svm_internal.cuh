@@ -82,10 +82,25 @@ struct SmoArgs {
     int64_t timeout_ns;
 };
 
-// ---- batched solves: one job = one subproblem over rows of a shared matrix
+// ---- batched and served solves: one job = one two-class problem
 struct BatchJobDev {
-    int64_t off;               // first entry of the job in the concatenated arrays
+    // the job's matrix (a batch shares one; a served job brings its own)
+    const int64_t *indptr;
+    const int32_t *indices;
+    const float *values;       // FP64 mode
+    const float *vmix;         // mixed mode (CSR)
+    const __nv_bfloat16 *dmat; // mixed mode, dense rows: BF16 [rows][d]
+    const double *norm;
+    const float *normf;
+    // the job's rows of that matrix, labels and state
+    const int32_t *rows;
+    const int8_t *y;
+    double *alpha;
+    double *f;
+    uint8_t *status;
     int32_t nrows;
+    int32_t d;                 // columns (dense: padded to a multiple of 8)
+    int32_t dense;
     int32_t pad;
     double C, gamma, tau;
     int64_t max_iter;
@@ -99,26 +114,22 @@ struct BatchResultDev {
 };
 
 struct BatchArgs {
-    int64_t n;
-    int32_t d;                 // columns (dense: padded to a multiple of 8)
-    int32_t njobs;
-    const int64_t *indptr;
-    const int32_t *indices;
-    const float *values;       // FP64 mode
-    const float *vmix;         // mixed mode (CSR)
-    const __nv_bfloat16 *dense;  // mixed mode, dense rows: BF16 [n][d]
-    const double *norm;
-    const float *normf;
-    const int32_t *rows;       // concatenated job row ids
-    const int8_t *y;           // concatenated job labels
-    double *alpha;
-    double *f;
-    uint8_t *status;
-    const BatchJobDev *jobs;
-    BatchResultDev *results;
-    int *next_job;             // work-list counter (zeroed before the launch)
+    int32_t d;                 // widest job (target buffers)
+    int32_t njobs;             // static work-list: jobs[0 .. njobs)
+    const BatchJobDev *jobs;   // job table (static list or server slots)
+    BatchResultDev *results;   // per job / slot
+    int *next_job;             // claim counter (zeroed before a static launch)
     int32_t ktab_len;          // binary mode: 2 * maxnnz + 1
     int32_t maxnnz;
+    // dynamic work-list of a server (NULL for a batch): slots published by
+    // the host in ring[head % ring_cap] for head < *ring_tail
+    const int32_t *ring;
+    const unsigned *ring_tail;
+    int32_t ring_cap;
+    int32_t pad;
+    const int *shutdown;       // host sets to stop the engine
+    int *done;                 // per slot: set to 1 when the result is written
+    int64_t idle_ns;           // an engine cluster leaves after this long without work
 };
 
 size_t smo_batch_smem(int mode, int d, int ktab_len, int maxnnz);
