@@ -112,10 +112,14 @@ typedef struct svm_params {
                                 trace_len steps, 2 ints per step; -1 if not reached */
     int64_t trace_len;
     int32_t flags;           /* bitwise OR of SVM_FLAG_* */
-    int32_t ctas;            /* CTAs (= row segments) of the fused step; 0 = one per
-                                SM (capped by n / 16); larger values are clamped */
+    int32_t ctas;            /* CTAs (= row segments) of the fused step; 0 = automatic:
+                                one thread-block cluster of 16 CTAs when n <= 200,000
+                                and its segments fit in shared memory, else one CTA
+                                per SM (capped by n / 16); 16 asks for the single
+                                cluster at any n; larger values are clamped */
     int32_t lanes_per_row;   /* lanes sharing one row in the row pass (rounded up to
-                                a power of two <= 32); 0 = from the mean row length */
+                                a power of two <= 32); 0 = from the mean row length;
+                                bit-mask rows always use one lane */
     int32_t reserved;
 } svm_params;
 
@@ -127,9 +131,15 @@ typedef struct svm_params {
  * (svm_stats.phase_ms, converted at the device's maximum clock). */
 #define SVM_FLAG_PHASE_TIMES 2
 /* Exchange the per-step candidates of all CTAs through global memory only
- * (by default CTAs form thread-block clusters of 8 that reduce through
- * distributed shared memory, and only cluster leaders use global memory). */
+ * (by default the CTAs form one cluster of 16 that reduces through
+ * distributed shared memory alone, or clusters of 8 whose leaders exchange
+ * through global memory). */
 #define SVM_FLAG_NO_CLUSTERS 4
+/* Binary input (every stored value 1.0) with d <= 256 is read in the row
+ * pass as one bit mask per row (16 or 32 bytes), the squared distance to
+ * x_up / x_low being the popcount of an XOR; this flag keeps the CSR column
+ * gather instead. The results are identical either way. */
+#define SVM_FLAG_CSR_ROWS 8
 
 typedef struct svm_shrink_policy {
     int32_t kind;            /* enum svm_shrink_kind */
@@ -165,6 +175,8 @@ typedef struct svm_stats {
                                 unused */
     double cta_busy_ms_min;  /* with SVM_FLAG_PHASE_TIMES: least and most time a */
     double cta_busy_ms_max;  /* CTA spent from step start to publishing its candidate */
+    int32_t bit_rows;        /* 1 when the row pass read binary rows as bit masks */
+    int32_t reserved;
 } svm_stats;
 
 /*

@@ -25,6 +25,7 @@ SVM_RECON_SINGLE, SVM_RECON_MULTI = 0, 1
 SVM_FLAG_STREAM_ROWS = 1
 SVM_FLAG_PHASE_TIMES = 2
 SVM_FLAG_NO_CLUSTERS = 4
+SVM_FLAG_CSR_ROWS = 8
 
 STATUS_NAMES = {0: "SVM_OK", 1: "SVM_NOT_CONVERGED", 2: "SVM_PENDING", -1: "SVM_ERR_ARG",
                 -2: "SVM_ERR_OOM", -3: "SVM_ERR_BUDGET", -4: "SVM_ERR_TIMEOUT",
@@ -59,7 +60,8 @@ class svm_stats(ct.Structure):
                 ("binary_input", ct.c_int32), ("launches", ct.c_int32),
                 ("resident", ct.c_int32), ("ctas", ct.c_int32), ("lanes_per_row", ct.c_int32),
                 ("cluster_size", ct.c_int32), ("phase_ms", ct.c_double * 8),
-                ("cta_busy_ms_min", ct.c_double), ("cta_busy_ms_max", ct.c_double)]
+                ("cta_busy_ms_min", ct.c_double), ("cta_busy_ms_max", ct.c_double),
+                ("bit_rows", ct.c_int32), ("reserved", ct.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}

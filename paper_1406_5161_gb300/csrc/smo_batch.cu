@@ -49,9 +49,9 @@ struct BatchShared {
     Side wup[kWarps], wlow[kWarps];
     unsigned long long wkup[kWarps], wklow[kWarps];
     int wiup[kWarps], wilow[kWarps];
-    CandFull ccand[8];
+    CandFull ccand[kMaxCluster];   // cluster leader: its CTAs' candidates
     ResultArea res;
-    BatchFinish fin[8];
+    BatchFinish fin[kMaxCluster];  // cluster leader: its CTAs' partial sums
     BatchFinish wfin[kWarps];
     double du, dl, au_new, al_new;
     unsigned char st_u, st_l;
@@ -710,7 +710,7 @@ cudaError_t launch_smo_batch(int mode, int lpr, int dense, const BatchArgs &a, s
 {
     (void)dense;
     void *fn = smo::batch_fn(mode, lpr);
-    if (!fn || cs < 1 || cs > 16 || nclusters < 1) return cudaErrorInvalidValue;
+    if (!fn || cs < 1 || cs > smo::kMaxCluster || nclusters < 1) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (cs > 8) {

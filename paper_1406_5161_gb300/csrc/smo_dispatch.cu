@@ -9,9 +9,11 @@ cudaError_t launch_smo_mixed(int lpr, const SmoArgs &a, size_t smem, cudaStream_
 int max_clusters_binary(int lpr, int resident, size_t smem, int cs);
 int max_clusters_fp64(int lpr, int resident, size_t smem, int cs);
 int max_clusters_mixed(int lpr, int resident, size_t smem, int cs);
+cudaError_t launch_smo_bits(int mode, int lpr, const SmoArgs &a, size_t smem, cudaStream_t st, int cs);
+int max_clusters_bits(int mode, int lpr, int resident, size_t smem, int cs);
 
 int smo_threads() { return smo::kThreads; }
-size_t smo_cand_bytes() { return sizeof(smo::CandFull); }
+size_t smo_cand_bytes() { return smo::kCandStride; }
 size_t smo_static_smem() { return sizeof(smo::Shared); }
 
 cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem, cudaStream_t st,
@@ -21,6 +23,8 @@ cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t sm
     case MODE_BINARY: return launch_smo_binary(lpr, a, smem, st, cs);
     case MODE_FP64: return launch_smo_fp64(lpr, a, smem, st, cs);
     case MODE_MIXED: return launch_smo_mixed(lpr, a, smem, st, cs);
+    case MODE_BITS4:
+    case MODE_BITS8: return launch_smo_bits(mode, lpr, a, smem, st, cs);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -31,6 +35,8 @@ int smo_max_clusters(int mode, int lpr, int resident, size_t smem, int cs)
     case MODE_BINARY: return max_clusters_binary(lpr, resident, smem, cs);
     case MODE_FP64: return max_clusters_fp64(lpr, resident, smem, cs);
     case MODE_MIXED: return max_clusters_mixed(lpr, resident, smem, cs);
+    case MODE_BITS4:
+    case MODE_BITS8: return max_clusters_bits(mode, lpr, resident, smem, cs);
     default: return 0;
     }
 }

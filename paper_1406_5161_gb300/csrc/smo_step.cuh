@@ -40,6 +40,7 @@ namespace smo {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxCluster = 16;   // largest thread-block cluster launched (non-portable size)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
 {
@@ -66,6 +67,52 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// distributed shared memory and mbarriers (32-bit shared-window addresses)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t a, uint4 v)
+{
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+// asynchronous store into a CTA of the cluster that counts its bytes on that
+// CTA's mbarrier (no fence on the sending side)
+__device__ __forceinline__ void st_async_v4(uint32_t a, uint4 v, uint32_t remote_bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(a),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(remote_bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t remote_bar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
@@ -87,6 +134,7 @@ struct Side {
     int32_t len;    // CSR length of the row
     int32_t y;
     int32_t pad;
+    uint32_t m[8];  // bit-mask modes: the row's bits (unused words zero)
 };
 
 struct __align__(16) CandFull {
@@ -95,9 +143,12 @@ struct __align__(16) CandFull {
     int32_t pad[3];
 };
 static_assert(sizeof(CandFull) % 16 == 0, "candidate slots are read with vector loads");
+// global exchange slots: each candidate and each flag on lines of its own
+constexpr size_t kCandStride = 256;
+static_assert(sizeof(CandFull) <= kCandStride, "candidate slot too small");
 
 // Result of a step's exchange, written into every CTA of a cluster.
-struct __align__(16) ResultArea {
+struct __align__(16) ResultArea {   // (sizeof a multiple of 16)
     Side up, low;
     long long total;   // active-set size over all segments
     int flag;          // a wait timed out
@@ -164,6 +215,42 @@ __device__ __forceinline__ void side_empty(Side &s, bool up)
     s.len = 0;
     s.y = 0;
     s.pad = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s.m[w] = 0;
+}
+
+// Word-wise copies of a candidate side (few live registers; generic
+// destinations may be another CTA's shared memory).
+__device__ __forceinline__ void copy_side(Side *dst, const Side *src)
+{
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(Side) / 8); ++w) d[w] = s[w];
+}
+__device__ __forceinline__ void copy_side_ldcg(Side *dst, const Side *src)   // src in global memory
+{
+    const unsigned long long *s = reinterpret_cast<const unsigned long long *>(src);
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(dst);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(Side) / 8); ++w) d[w] = __ldcg(s + w);
+}
+__device__ __forceinline__ void copy_result(ResultArea *dst, const ResultArea *src)
+{
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(ResultArea) / 16); ++w) d[w] = s[w];
+}
+// (key, index) of the I_up and I_low sides of a candidate
+__device__ __forceinline__ void cand_keys(const CandFull &c, unsigned long long &k1, int &i1,
+                                          unsigned long long &k2, int &i2, long long &cnt)
+{
+    i1 = c.up.i;
+    i2 = c.low.i;
+    k1 = i1 == INT_MAX ? kNoKey : key_up(c.up.f);
+    k2 = i2 == INT_MAX ? kNoKey : key_low(c.low.f);
+    cnt = c.count;
 }
 
 // Block-wide exclusive scan of 0/1 flags; returns the prefix, total in *tot.
@@ -209,6 +296,14 @@ struct RowMath<MODE_MIXED> {
     using Tgt = float2;
     using Nrm = float;
 };
+template <>
+struct RowMath<MODE_BITS4> {
+    using Acc = int;
+    using Tgt = unsigned char;   // unused: the targets are the masks in registers
+    using Nrm = float;           // unused
+};
+template <>
+struct RowMath<MODE_BITS8> : RowMath<MODE_BITS4> {};
 
 struct Shared {
     Side wup[kWarps], wlow[kWarps];           // per-warp winners of the row pass
@@ -217,7 +312,10 @@ struct Shared {
     Side rup[8], rlow[8];                     // per-warp winners of the exchange
     unsigned long long rkup[8], rklow[8];
     int riup[8], rilow[8], rto[8];
-    CandFull ccand[8];                        // cluster leader: its CTAs' candidates
+    CandFull ccand[kMaxCluster];              // cluster leader: its CTAs' candidates
+    CandFull xc[2][kMaxCluster];              // one cluster: every CTA's candidate, by epoch parity
+    CandFull mycand;                          // this CTA's candidate of the step
+    unsigned long long xbar[2];               // one cluster: mbarriers of the two parities
     ResultArea res;                           // exchange result pushed by the leader
     long long rcount[8];
     int scan[kWarps];
@@ -231,17 +329,22 @@ struct Shared {
 template <int MODE>
 __device__ __forceinline__ void tgt_clear(typename RowMath<MODE>::Tgt &t)
 {
-    if constexpr (MODE == MODE_BINARY) t = 0;
+    if constexpr (MODE == MODE_BINARY || mode_bits(MODE)) t = 0;
     else if constexpr (MODE == MODE_FP64) t = make_double2(0.0, 0.0);
     else t = make_float2(0.f, 0.f);
 }
 
-template <int MODE, int LPR, bool RES>
+// SOLO: the grid is one thread-block cluster (exchange through distributed
+// shared memory only); a separate instantiation, so that the kernels for
+// several clusters carry none of its code.
+template <int MODE, int LPR, bool RES, bool SOLO>
 __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
 {
     using Tgt = typename RowMath<MODE>::Tgt;
     using Acc = typename RowMath<MODE>::Acc;
     using Nrm = typename RowMath<MODE>::Nrm;
+    constexpr bool BITS = mode_bits(MODE);
+    constexpr int W4 = mode_words(MODE) / 4;   // uint4 words of a bit-mask row
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ Shared sh;
 
@@ -267,6 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     uint8_t *st_s = reinterpret_cast<uint8_t *>(dsm + L.st);
     unsigned short *col_s = reinterpret_cast<unsigned short *>(dsm + L.col);
     float *val_s = reinterpret_cast<float *>(dsm + L.val);
+    uint4 *bits_s = reinterpret_cast<uint4 *>(dsm + L.bits);
+    uint32_t *dist_s = reinterpret_cast<uint32_t *>(dsm + L.dist);   // bit-mask rows on chip
+    const uint4 *bits_g = reinterpret_cast<const uint4 *>(A.bits);
     const int maxnnz = A.maxnnz > 0 ? A.maxnnz : 1;
 
     const int64_t lo = seg_lo(A.n, G, cta);
@@ -274,8 +380,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     const int64_t base = A.indptr[lo];   // global CSR offset of the segment
 
     // ---- set-up
-    for (int c = tid; c < 2 * d; c += kThreads) tgt_clear<MODE>(tbuf[c]);
-    if constexpr (MODE == MODE_BINARY) {
+    if constexpr (!BITS) {
+        for (int c = tid; c < 2 * d; c += kThreads) tgt_clear<MODE>(tbuf[c]);
+    }
+    if constexpr (MODE == MODE_BINARY || BITS) {
         for (int c = tid; c < 2 * A.ktab_len; c += kThreads) ktab[c] = A.ktab[c];
     }
     const double *rtab = ktab + A.ktab_len;
@@ -285,16 +393,20 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             f_s[r] = A.f[lo + r];
             a_s[r] = A.alpha[lo + r];
             st_s[r] = A.status[lo + r];
-            rp_s[r] = (int)(A.indptr[lo + r] - base);
+            if constexpr (!BITS) rp_s[r] = (int)(A.indptr[lo + r] - base);
             if constexpr (MODE == MODE_FP64) nrm_s[r] = A.norm[lo + r];
             if constexpr (MODE == MODE_MIXED) nrm_s[r] = A.normf[lo + r];
         }
-        if (tid == 0) rp_s[nseg] = (int)(A.indptr[lo + nseg] - base);
-        const int64_t segnnz = A.indptr[lo + nseg] - base;
-        for (int64_t p = tid; p < segnnz; p += kThreads) {
-            col_s[p] = (unsigned short)A.indices[base + p];
-            if constexpr (MODE == MODE_FP64) val_s[p] = A.values[base + p];
-            if constexpr (MODE == MODE_MIXED) val_s[p] = A.vmix[base + p];
+        if constexpr (BITS) {
+            for (int q = tid; q < nseg * W4; q += kThreads) bits_s[q] = bits_g[(size_t)lo * W4 + q];
+        } else {
+            if (tid == 0) rp_s[nseg] = (int)(A.indptr[lo + nseg] - base);
+            const int64_t segnnz = A.indptr[lo + nseg] - base;
+            for (int64_t p = tid; p < segnnz; p += kThreads) {
+                col_s[p] = (unsigned short)A.indices[base + p];
+                if constexpr (MODE == MODE_FP64) val_s[p] = A.values[base + p];
+                if constexpr (MODE == MODE_MIXED) val_s[p] = A.vmix[base + p];
+            }
         }
         for (int k = tid; k < cnt; k += kThreads) act_s[k] = A.act[lo + k];
     }
@@ -307,6 +419,15 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     Side up, low;
     side_empty(up, true);
     side_empty(low, false);
+    auto load_mask = [&](Side &sd) {
+        if constexpr (BITS) {
+#pragma unroll
+            for (int q = 0; q < W4; ++q) {
+                const uint4 v = bits_g[(size_t)sd.i * W4 + q];
+                sd.m[4 * q] = v.x; sd.m[4 * q + 1] = v.y; sd.m[4 * q + 2] = v.z; sd.m[4 * q + 3] = v.w;
+            }
+        }
+    };
     bool first = A.select_only != 0;
     if (!first) {
         up.f = C0.b_up; up.a = C0.a_up; up.i = C0.i_up;
@@ -316,15 +437,35 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             up.len = (int)(A.indptr[up.i + 1] - up.p0);
             up.y = A.y[up.i];
             up.nrm = MODE == MODE_MIXED ? (double)A.normf[up.i] : (MODE == MODE_FP64 ? A.norm[up.i] : 0.0);
+            load_mask(up);
         }
         if (low.i >= 0 && low.i < A.n) {
             low.p0 = A.indptr[low.i];
             low.len = (int)(A.indptr[low.i + 1] - low.p0);
             low.y = A.y[low.i];
             low.nrm = MODE == MODE_MIXED ? (double)A.normf[low.i] : (MODE == MODE_FP64 ? A.norm[low.i] : 0.0);
+            load_mask(low);
         }
     }
-    __syncthreads();
+    // one cluster over the whole grid: candidates go to every CTA as
+    // asynchronous stores whose bytes each CTA counts on its own mbarrier
+    // (one per epoch parity; the CTA's own arrival sets the expected bytes)
+    constexpr bool solo = SOLO;
+    if constexpr (SOLO) {
+        if (nlead != 1) {   // launched over several clusters: refuse
+            if (tid == 0) atomicExch(&A.ctrl->err, 1);
+            return;
+        }
+        if (tid == 0) {
+            mbar_init(smem_u32(&sh.xbar[0]), 1);
+            mbar_init(smem_u32(&sh.xbar[1]), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        cluster.sync();
+    } else {
+        __syncthreads();
+    }
 
     // ---- accessors (segment-local row r, global sample lo + r)
     auto ACT = [&](int k) -> int {
@@ -373,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         else A.alpha[lo + r] = v;
     };
     auto NRM = [&](int r) -> double {
-        if constexpr (MODE == MODE_BINARY) return 0.0;
+        if constexpr (MODE == MODE_BINARY || BITS) return 0.0;
         else if constexpr (RES) return (double)nrm_s[r];
         else if constexpr (MODE == MODE_FP64) return A.norm[lo + r];
         else return (double)A.normf[lo + r];
@@ -405,14 +546,15 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             if (!dless(A.thr, low.f - up.f)) { exit_reason = 0; break; }
             if (iter >= A.iter_limit) { exit_reason = 1; break; }
             // ---- 1. targets: x_up into .x / byte 0, x_low into .y / byte 1
-            for (int k = tid; k < up.len; k += kThreads) {
+            //         (bit-mask modes: the masks came with the exchange)
+            if constexpr (!BITS) for (int k = tid; k < up.len; k += kThreads) {
                 int c = A.indices[up.p0 + k];
                 tcu[k] = c;
                 if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
                 else if constexpr (MODE == MODE_FP64) T[c].x = (double)A.values[up.p0 + k];
                 else T[c].x = A.vmix[up.p0 + k];
             }
-            for (int k = tid; k < low.len; k += kThreads) {
+            if constexpr (!BITS) for (int k = tid; k < low.len; k += kThreads) {
                 int c = A.indices[low.p0 + k];
                 tcl[k] = c;
                 if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
@@ -424,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 shrink_now = counter <= 0;
             }
             row_visits += total;
-            __syncthreads();
+            if constexpr (!BITS) __syncthreads();
             if (timed && tid == 0) { uint64_t t = clock64(); ph[0] += t - tp; tp = t; }
         }
 
@@ -437,19 +579,25 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         if (warp == 0) {
             if (!first) {
                 Acc s = 0;
-                for (int k = lane; k < low.len; k += 32) {
-                    const Tgt t = T[tcl[k]];
-                    if constexpr (MODE == MODE_BINARY) s += (int)(t & 1);
-                    else if constexpr (MODE == MODE_FP64) s = fma(t.y, t.x, s);
-                    else s = fmaf(t.y, t.x, s);
-                }
+                if constexpr (BITS) {
+                    // ||x_up - x_low||^2 of binary rows
 #pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                    for (int w = 0; w < 4 * W4; ++w) s += __popc(up.m[w] ^ low.m[w]);
+                } else {
+                    for (int k = lane; k < low.len; k += 32) {
+                        const Tgt t = T[tcl[k]];
+                        if constexpr (MODE == MODE_BINARY) s += (int)(t & 1);
+                        else if constexpr (MODE == MODE_FP64) s = fma(t.y, t.x, s);
+                        else s = fmaf(t.y, t.x, s);
+                    }
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                }
                 if (timed && tid == 0) { uint64_t t = clock64(); ph[6] += t - tp; tp = t; }
                 if (lane == 0) {
                     double kul, rinv = 0.0;
-                    if constexpr (MODE == MODE_BINARY) {
-                        int dist = up.len + low.len - 2 * s;
+                    if constexpr (MODE == MODE_BINARY || BITS) {
+                        int dist = BITS ? s : up.len + low.len - 2 * s;
                         dist = dist < 0 ? 0 : dist;
                         kul = ktab[dist];
                         rinv = rtab[dist];
@@ -486,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     double aln;
                     if (dless(1e-12, eta)) {
                         double q;
-                        if constexpr (MODE == MODE_BINARY) {
+                        if constexpr (MODE == MODE_BINARY || BITS) {
                             // slope / eta from the correctly rounded 1/eta of
                             // the table: one Markstein correction gives the
                             // correctly rounded quotient
@@ -517,6 +665,62 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 step_bar_arrive(kThreads);
                 if (timed && tid == 0) { uint64_t t = clock64(); ph[1] += t - tp; tp = t; }
             }
+        } else if constexpr (BITS && RES) {
+            // ---- 3. row pass, bit-mask rows held on chip, in two sweeps
+            //         over the active list: the squared distances of every
+            //         row to x_up and x_low while warp 0 runs the pair step,
+            //         then the FP64 f updates (Eq. fup), the shrink rule and
+            //         the candidates. A thread handles the same rows in both.
+            if (!first) {
+                for (int k = tid - 32; k < cnt; k += kThreads - 32) {
+                    const uint4 *rb = bits_s + (size_t)act_s[k] * W4;
+                    int du2 = 0, dl2 = 0;
+#pragma unroll
+                    for (int q = 0; q < W4; ++q) {
+                        const uint4 v = rb[q];
+                        du2 += __popc(v.x ^ up.m[4 * q]) + __popc(v.y ^ up.m[4 * q + 1]) +
+                               __popc(v.z ^ up.m[4 * q + 2]) + __popc(v.w ^ up.m[4 * q + 3]);
+                        dl2 += __popc(v.x ^ low.m[4 * q]) + __popc(v.y ^ low.m[4 * q + 1]) +
+                               __popc(v.z ^ low.m[4 * q + 2]) + __popc(v.w ^ low.m[4 * q + 3]);
+                    }
+                    dist_s[k] = (uint32_t)du2 | ((uint32_t)dl2 << 16);
+                }
+                step_bar_sync(kThreads);
+            }
+            const double du = sh.du, dl = sh.dl, au_new = sh.au_new, al_new = sh.al_new;
+            const unsigned char st_u = sh.st_u, st_l = sh.st_l;
+            for (int k = tid - 32; k < cnt; k += kThreads - 32) {
+                const int r = act_s[k];
+                const int i = (int)(lo + r);
+                double fi = f_s[r];
+                uint8_t sb = st_s[r];
+                if (!first) {
+                    const uint32_t dd = dist_s[k];
+                    fi = fma(dl, ktab[dd >> 16], fma(du, ktab[dd & 0xffffu], fi));
+                    f_s[r] = fi;
+                    if (i == up.i) {
+                        sb = st_u;
+                        st_s[r] = sb;
+                        a_s[r] = au_new;
+                    } else if (i == low.i) {
+                        sb = st_l;
+                        st_s[r] = sb;
+                        a_s[r] = al_new;
+                    }
+                }
+                const uint8_t set = set_bits(sb);
+                bool keep = true;
+                if (shrink_now) {
+                    keep = !(((set == ST_I3 || set == ST_I4) && dless(fi, bup_sel)) ||
+                             ((set == ST_I1 || set == ST_I2) && dless(blow_sel, fi)));
+                    if (!keep) act_s[k] = ~r;
+                }
+                if (keep) {
+                    const unsigned long long kup = key_up(fi), klo = key_low(fi);
+                    if (st_up(set) && ki_less(kup, i, bku, biu)) { bku = kup; biu = i; bru = r; }
+                    if (st_low(set) && ki_less(klo, i, bkl, bil)) { bkl = klo; bil = i; brl = r; }
+                }
+            }
         } else {
             // ---- 3. row pass over the segment's active list (warps 1..)
             constexpr int RPW = 32 / LPR;
@@ -537,14 +741,27 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 uint8_t sb = 0;
                 if (valid) {
                     r = ACT(k);
-                    ROWP(r, p0, p1);
+                    if constexpr (!BITS) ROWP(r, p0, p1);
                     if (gl == 0) {
                         fi = GETF(r);
                         sb = GETST(r);
                     }
                 }
                 Acc su = 0, sl = 0;
-                if (!first) {
+                if constexpr (BITS) {
+                    // squared distances to x_up and x_low (one lane per row)
+                    if (!first && valid) {
+                        const uint4 *rb = RES ? bits_s + (size_t)r * W4 : bits_g + (size_t)(lo + r) * W4;
+#pragma unroll
+                        for (int q = 0; q < W4; ++q) {
+                            const uint4 v = RES ? rb[q] : __ldg(rb + q);
+                            su += __popc(v.x ^ up.m[4 * q]) + __popc(v.y ^ up.m[4 * q + 1]) +
+                                  __popc(v.z ^ up.m[4 * q + 2]) + __popc(v.w ^ up.m[4 * q + 3]);
+                            sl += __popc(v.x ^ low.m[4 * q]) + __popc(v.y ^ low.m[4 * q + 1]) +
+                                  __popc(v.z ^ low.m[4 * q + 2]) + __popc(v.w ^ low.m[4 * q + 3]);
+                        }
+                    }
+                } else if (!first) {
                     for (int64_t p = p0 + gl; p < p1; p += LPR) {
                         const int c = COL(p);
                         if constexpr (MODE == MODE_BINARY) {
@@ -572,7 +789,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 double ku = 0.0, kl = 0.0;
                 if (!first && valid && gl == 0) {
                     const int len = (int)(p1 - p0);
-                    if constexpr (MODE == MODE_BINARY) {
+                    if constexpr (BITS) {
+                        ku = ktab[su];
+                        kl = ktab[sl];
+                    } else if constexpr (MODE == MODE_BINARY) {
                         int du2 = up.len + len - 2 * su, dl2 = low.len + len - 2 * sl;
                         ku = ktab[du2 < 0 ? 0 : du2];
                         kl = ktab[dl2 < 0 ? 0 : dl2];
@@ -633,8 +853,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         // thread's own updates of f, alpha and the index set)
         auto make_side = [&](int r) {
             Side sd;
-            int64_t p0, p1;
-            ROWP(r, p0, p1);
+            int64_t p0 = 0, p1 = 0;
+            if constexpr (!BITS) ROWP(r, p0, p1);
             const uint8_t sb = GETST(r);
             sd.f = GETF(r);
             sd.a = GETA(r);
@@ -644,6 +864,16 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             sd.len = (int)(p1 - p0);
             sd.y = y_of(sb);
             sd.pad = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) sd.m[w] = 0;
+            if constexpr (BITS) {
+                const uint4 *rb = RES ? bits_s + (size_t)r * W4 : bits_g + (size_t)(lo + r) * W4;
+#pragma unroll
+                for (int q = 0; q < W4; ++q) {
+                    const uint4 v = rb[q];
+                    sd.m[4 * q] = v.x; sd.m[4 * q + 1] = v.y; sd.m[4 * q + 2] = v.z; sd.m[4 * q + 3] = v.w;
+                }
+            }
             return sd;
         };
         // ---- CTA reduction: warp minima of (key, index); winners' payloads
@@ -676,11 +906,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             cnt = kept;
         }
         if (timed && tid == 0) { uint64_t t = clock64(); ph[2] += t - tp; tp = t; }
-        // ---- 4. grid-wide exchange, hierarchical: the CTAs of a thread-block
-        //         cluster hand their candidates to the cluster's first CTA
-        //         through distributed shared memory; only those leaders
-        //         exchange through global memory (release/acquire flags,
-        //         bounded waits) and push the result back to their cluster.
+        // ---- 4. grid-wide exchange. One cluster over the whole grid: each
+        //         CTA writes its candidate into every CTA's shared memory and
+        //         arrives on that CTA's mbarrier; every CTA reduces the same
+        //         candidates in the same order. Several clusters: the CTAs of a
+        //         cluster hand their candidates to its first CTA through
+        //         distributed shared memory; only those leaders exchange
+        //         through global memory (release/acquire flags, bounded
+        //         waits) and push the result back to their cluster.
         ++epoch;
         const int par = (int)(epoch & 1);
         if (warp == 0) {
@@ -700,34 +933,63 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 if (ml) cf.low = sh.wlow[__ffs(ml) - 1]; else side_empty(cf.low, false);
                 cf.count = cnt;
                 cf.pad[0] = cf.pad[1] = cf.pad[2] = 0;
-                CandFull *dst = cluster.map_shared_rank(sh.ccand, 0);
-                dst[crank] = cf;
+                if constexpr (solo) {
+                    sh.mycand = cf;
+                } else {
+                    CandFull *dst = cluster.map_shared_rank(sh.ccand, 0);
+                    dst[crank] = cf;
+                }
+            }
+            if constexpr (solo) {
+                __syncwarp();
+                if (lane < csize) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(&sh.mycand);
+                    const uint32_t dst = cluster_addr(smem_u32(&sh.xc[par][crank]), lane);
+                    const uint32_t rbar = cluster_addr(smem_u32(&sh.xbar[par]), lane);
+#pragma unroll
+                    for (int j = 0; j < (int)(sizeof(CandFull) / 16); ++j) st_async_v4(dst + 16 * j, src[j], rbar);
+                }
+                if (lane == 0)
+                    mbar_arrive_expect_tx(smem_u32(&sh.xbar[par]), (uint32_t)(csize * sizeof(CandFull)));
+            }
+            if (lane == 0) {
                 if (busy_on) busy += clock64() - cta_t0;
                 if (timed) { uint64_t t = clock64(); ph[3] += t - tp; tp = t; }
             }
         }
         // the previous step's target rows are cleared while others wait
-        if (prev_valid && warp >= 8) {
+        if (!BITS && prev_valid && warp >= 8) {
             Tgt *P = tbuf + (size_t)(1 - buf) * d;
             const int *pcu = tcol + (size_t)((1 - buf) * 2 + 0) * maxnnz;
             const int *pcl = tcol + (size_t)((1 - buf) * 2 + 1) * maxnnz;
             for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) tgt_clear<MODE>(P[pcu[k]]);
             for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) tgt_clear<MODE>(P[pcl[k]]);
         }
-        cluster.sync();
-        const int rwarps = (nlead + 31) / 32;
-        if (crank == 0) {
+        if constexpr (solo) {
             if (warp == 0) {
-                // cluster winner -> this leader's global slot
-                CandFull c;
-                if (lane < csize) c = sh.ccand[lane];
-                else { side_empty(c.up, true); side_empty(c.low, false); c.count = 0; }
-                unsigned long long k1 = c.up.i == INT_MAX ? kNoKey : key_up(c.up.f);
-                unsigned long long k2 = c.low.i == INT_MAX ? kNoKey : key_low(c.low.f);
-                int i1 = c.up.i, i2 = c.low.i;
+                // this epoch's csize candidates; the k-th use of a barrier
+                // completes its phase of parity k & 1
+                const uint32_t bar = smem_u32(&sh.xbar[par]);
+                const uint32_t parity = (uint32_t)((epoch - 1) >> 1) & 1u;
+                int timed_out = 0, spins = 0;
+                uint64_t t0 = 0;
+                while (!mbar_try_wait_cluster(bar, parity)) {
+                    if (++spins >= 64) {
+                        spins = 0;
+                        const uint64_t now = global_ns();
+                        if (t0 == 0) t0 = now;
+                        else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
+                        if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+                    }
+                }
+                timed_out = __any_sync(0xffffffffu, timed_out);
+                if (timed_out && lane == 0) atomicExch(&A.ctrl->err, 1);
+                unsigned long long k1 = kNoKey, k2 = kNoKey;
+                int i1 = INT_MAX, i2 = INT_MAX;
+                long long cc = 0;
+                if (lane < csize && !timed_out) cand_keys(sh.xc[par][lane], k1, i1, k2, i2, cc);
                 const unsigned long long k1s = k1, k2s = k2;
                 const int i1s = i1, i2s = i2;
-                long long cc = c.count;
                 warp_min_ki(k1, i1);
                 warp_min_ki(k2, i2);
 #pragma unroll
@@ -735,93 +997,119 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                 const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
                 if (lane == 0) {
-                    CandFull out;
-                    if (mu) out.up = sh.ccand[__ffs(mu) - 1].up; else side_empty(out.up, true);
-                    if (ml) out.low = sh.ccand[__ffs(ml) - 1].low; else side_empty(out.low, false);
-                    out.count = (int32_t)cc;
-                    out.pad[0] = out.pad[1] = out.pad[2] = 0;
-                    *(reinterpret_cast<CandFull *>(A.cand) + (size_t)par * nlead + cid) = out;
-                    st_release_u32(A.seq + (size_t)par * nlead + cid, epoch);
+                    if (mu) copy_side(&sh.res.up, &sh.xc[par][__ffs(mu) - 1].up); else side_empty(sh.res.up, true);
+                    if (ml) copy_side(&sh.res.low, &sh.xc[par][__ffs(ml) - 1].low); else side_empty(sh.res.low, false);
+                    sh.res.total = cc;
+                    sh.res.flag = timed_out;
+                    sh.res.pad = 0;
                 }
-            }
-            if (warp < rwarps) {
-                const int c = warp * 32 + lane;
-                Side a, b;
-                side_empty(a, true);
-                side_empty(b, false);
-                long long cc = 0;
-                int timed_out = 0;
-                if (c < nlead) {
-                    const unsigned *sp = A.seq + (size_t)par * nlead + c;
-                    uint64_t t0 = 0;
-                    int spins = 0;
-                    while (ld_relaxed_u32(sp) < epoch) {
-                        if (++spins >= 256) {
-                            spins = 0;
-                            uint64_t now = global_ns();
-                            if (t0 == 0) t0 = now;
-                            else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
-                            if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
-                        }
-                    }
-                    if (!timed_out) {
-                        fence_acq_rel_gpu();   // acquire: the slot written before the flag
-                        // L2 reads (bypass L1, which is not coherent across SMs)
-                        union {
-                            CandFull c;
-                            int4 v[sizeof(CandFull) / 16];
-                        } u;
-                        const int4 *q = reinterpret_cast<const int4 *>(
-                            reinterpret_cast<const CandFull *>(A.cand) + (size_t)par * nlead + c);
-#pragma unroll
-                        for (int j = 0; j < (int)(sizeof(CandFull) / 16); ++j) u.v[j] = __ldcg(q + j);
-                        a = u.c.up;
-                        b = u.c.low;
-                        cc = u.c.count;
-                    }
-                }
-                const int any_to = __any_sync(0xffffffffu, timed_out);
-                if (any_to && lane == 0) atomicExch(&A.ctrl->err, 1);
-                unsigned long long k1 = a.i == INT_MAX ? kNoKey : key_up(a.f);
-                unsigned long long k2 = b.i == INT_MAX ? kNoKey : key_low(b.f);
-                int i1 = a.i, i2 = b.i;
-                warp_min_ki(k1, i1);
-                warp_min_ki(k2, i2);
-#pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
-                if (lane == 0) {
-                    sh.rkup[warp] = k1; sh.riup[warp] = i1;
-                    sh.rklow[warp] = k2; sh.rilow[warp] = i2;
-                    sh.rcount[warp] = cc;
-                    sh.rto[warp] = any_to;
-                }
-                if (i1 != INT_MAX && a.i == i1) sh.rup[warp] = a;
-                if (i2 != INT_MAX && b.i == i2) sh.rlow[warp] = b;
             }
             __syncthreads();
-            if (warp == 0) {
-                // final winner, pushed to every CTA of the cluster
-                unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
-                int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0, to = sh.rto[0];
-                long long cc = sh.rcount[0];
-                for (int w = 1; w < rwarps; ++w) {
-                    if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
-                    if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
-                    cc += sh.rcount[w];
-                    to |= sh.rto[w];
+        } else {
+            cluster.sync();
+            const int rwarps = (nlead + 31) / 32;
+            if (crank == 0) {
+                if (warp == 0) {
+                    // cluster winner -> this leader's global slot
+                    unsigned long long k1 = kNoKey, k2 = kNoKey;
+                    int i1 = INT_MAX, i2 = INT_MAX;
+                    long long cc = 0;
+                    if (lane < csize) cand_keys(sh.ccand[lane], k1, i1, k2, i2, cc);
+                    const unsigned long long k1s = k1, k2s = k2;
+                    const int i1s = i1, i2s = i2;
+                    warp_min_ki(k1, i1);
+                    warp_min_ki(k2, i2);
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
+                    const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
+                    const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
+                    if (lane == 0) {
+                        CandFull *out = reinterpret_cast<CandFull *>(static_cast<unsigned char *>(A.cand) +
+                                                                     ((size_t)par * nlead + cid) * kCandStride);
+                        if (mu) copy_side(&out->up, &sh.ccand[__ffs(mu) - 1].up);
+                        else { Side e; side_empty(e, true); copy_side(&out->up, &e); }
+                        if (ml) copy_side(&out->low, &sh.ccand[__ffs(ml) - 1].low);
+                        else { Side e; side_empty(e, false); copy_side(&out->low, &e); }
+                        out->count = (int32_t)cc;
+                        st_release_u32(A.seq + ((size_t)par * nlead + cid) * kSeqStride, epoch);
+                    }
                 }
-                if (lane < csize) {
-                    ResultArea res;
-                    if (iu != INT_MAX) res.up = sh.rup[wu]; else side_empty(res.up, true);
-                    if (il != INT_MAX) res.low = sh.rlow[wl]; else side_empty(res.low, false);
-                    res.total = cc;
-                    res.flag = to;
-                    res.pad = 0;
-                    *cluster.map_shared_rank(&sh.res, lane) = res;
+                if (warp < rwarps) {
+                    const int c = warp * 32 + lane;
+                    int ai = INT_MAX, bi = INT_MAX;
+                    double af = 0.0, bf = 0.0;
+                    const CandFull *gp = nullptr;
+                    long long cc = 0;
+                    int timed_out = 0;
+                    if (c < nlead) {
+                        const unsigned *sp = A.seq + ((size_t)par * nlead + c) * kSeqStride;
+                        uint64_t t0 = 0;
+                        int spins = 0;
+                        while (ld_relaxed_u32(sp) < epoch) {
+                            if (++spins >= 256) {
+                                spins = 0;
+                                uint64_t now = global_ns();
+                                if (t0 == 0) t0 = now;
+                                else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
+                                if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+                            }
+                        }
+                        if (!timed_out) {
+                            fence_acq_rel_gpu();   // acquire: the slot written before the flag
+                            // L2 reads (bypass L1, which is not coherent across SMs);
+                            // the winners' full sides are copied below
+                            gp = reinterpret_cast<const CandFull *>(static_cast<const unsigned char *>(A.cand) +
+                                                                    ((size_t)par * nlead + c) * kCandStride);
+                            ai = __ldcg(&gp->up.i);
+                            bi = __ldcg(&gp->low.i);
+                            af = __ldcg(&gp->up.f);
+                            bf = __ldcg(&gp->low.f);
+                            cc = __ldcg(&gp->count);
+                        }
+                    }
+                    const int any_to = __any_sync(0xffffffffu, timed_out);
+                    if (any_to && lane == 0) atomicExch(&A.ctrl->err, 1);
+                    unsigned long long k1 = ai == INT_MAX ? kNoKey : key_up(af);
+                    unsigned long long k2 = bi == INT_MAX ? kNoKey : key_low(bf);
+                    int i1 = ai, i2 = bi;
+                    warp_min_ki(k1, i1);
+                    warp_min_ki(k2, i2);
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
+                    if (lane == 0) {
+                        sh.rkup[warp] = k1; sh.riup[warp] = i1;
+                        sh.rklow[warp] = k2; sh.rilow[warp] = i2;
+                        sh.rcount[warp] = cc;
+                        sh.rto[warp] = any_to;
+                    }
+                    if (i1 != INT_MAX && ai == i1) copy_side_ldcg(&sh.rup[warp], &gp->up);
+                    if (i2 != INT_MAX && bi == i2) copy_side_ldcg(&sh.rlow[warp], &gp->low);
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    // final winner, pushed to every CTA of the cluster
+                    unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
+                    int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0, to = sh.rto[0];
+                    long long cc = sh.rcount[0];
+                    for (int w = 1; w < rwarps; ++w) {
+                        if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
+                        if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
+                        cc += sh.rcount[w];
+                        to |= sh.rto[w];
+                    }
+                    if (lane == 0) {
+                        if (iu != INT_MAX) copy_side(&sh.res.up, &sh.rup[wu]); else side_empty(sh.res.up, true);
+                        if (il != INT_MAX) copy_side(&sh.res.low, &sh.rlow[wl]); else side_empty(sh.res.low, false);
+                        sh.res.total = cc;
+                        sh.res.flag = to;
+                        sh.res.pad = 0;
+                    }
+                    __syncwarp();
+                    if (lane > 0 && lane < csize) copy_result(cluster.map_shared_rank(&sh.res, lane), &sh.res);
                 }
             }
+            cluster.sync();
         }
-        cluster.sync();
         if (timed && tid == 0) { uint64_t t = clock64(); ph[4] += t - tp; tp = t; }
         if (sh.res.flag) break;
         prev_valid = first ? 0 : 1;
@@ -876,28 +1164,45 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     }
 }
 
-template <int MODE, bool RES>
+template <int MODE, bool RES, bool SOLO>
 void *kernel_for(int lpr)
 {
-    switch (lpr) {
-    case 1: return (void *)smo_persistent_kernel<MODE, 1, RES>;
-    case 2: return (void *)smo_persistent_kernel<MODE, 2, RES>;
-    case 4: return (void *)smo_persistent_kernel<MODE, 4, RES>;
-    case 8: return (void *)smo_persistent_kernel<MODE, 8, RES>;
-    case 16: return (void *)smo_persistent_kernel<MODE, 16, RES>;
-    case 32: return (void *)smo_persistent_kernel<MODE, 32, RES>;
-    default: return nullptr;
+    if constexpr (mode_bits(MODE)) {
+        return lpr == 1 ? (void *)smo_persistent_kernel<MODE, 1, RES, SOLO> : nullptr;
+    } else {
+        switch (lpr) {
+        case 1: return (void *)smo_persistent_kernel<MODE, 1, RES, SOLO>;
+        case 2: return (void *)smo_persistent_kernel<MODE, 2, RES, SOLO>;
+        case 4: return (void *)smo_persistent_kernel<MODE, 4, RES, SOLO>;
+        case 8: return (void *)smo_persistent_kernel<MODE, 8, RES, SOLO>;
+        case 16: return (void *)smo_persistent_kernel<MODE, 16, RES, SOLO>;
+        case 32: return (void *)smo_persistent_kernel<MODE, 32, RES, SOLO>;
+        default: return nullptr;
+        }
     }
+}
+
+// resident: 0 streamed segments, 1 on-chip segments, 2 on-chip segments in
+// one cluster over the whole grid
+template <int MODE>
+void *kernel_pick(int lpr, int resident)
+{
+    if (resident == 0) return kernel_for<MODE, false, false>(lpr);
+    return resident == 2 ? kernel_for<MODE, true, true>(lpr) : kernel_for<MODE, true, false>(lpr);
 }
 
 template <int MODE>
 cudaError_t launch_mode(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st, int cs)
 {
-    void *fn = a.resident ? kernel_for<MODE, true>(lpr) : kernel_for<MODE, false>(lpr);
+    void *fn = kernel_pick<MODE>(lpr, a.resident ? (a.G == cs ? 2 : 1) : 0);
     if (!fn) return cudaErrorInvalidValue;
-    if (cs < 1 || a.G % cs != 0 || a.G / cs > 256 || cs > 8) return cudaErrorInvalidValue;
+    if (cs < 1 || a.G % cs != 0 || a.G / cs > 256 || cs > kMaxCluster) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    if (cs > 8) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     SmoArgs args = a;
     void *params[] = {&args};
     cudaLaunchAttribute attrs[2];
@@ -928,9 +1233,11 @@ cudaError_t launch_mode(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st,
 template <int MODE>
 int max_clusters(int lpr, int resident, size_t smem, int cs)
 {
-    void *fn = resident ? kernel_for<MODE, true>(lpr) : kernel_for<MODE, false>(lpr);
+    void *fn = kernel_pick<MODE>(lpr, resident);
     if (!fn) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return 0;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
     attr.val.clusterDim.x = (unsigned)cs;

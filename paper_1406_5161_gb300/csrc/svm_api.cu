@@ -343,6 +343,20 @@ int device_sms()
 }
 
 // Device-resident copy of one CSR matrix (+ labels) with its derived data.
+// Binary rows as bit masks of W words: bit c of row i is set when column c
+// is stored (d <= 32 W).
+__global__ void k_bits(int64_t n, int W, const int64_t *indptr, const int32_t *indices, uint32_t *bits)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
+        const int c = indices[p];
+        m[(c >> 5) & 7] |= 1u << (c & 31);
+    }
+    for (int w = 0; w < W; ++w) bits[i * W + w] = m[w];
+}
+
 struct DevCSR {
     int64_t n = 0, d = 0, nnz = 0;
     const int64_t *indptr = nullptr;
@@ -514,18 +528,46 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         lpr = 1;
         while (lpr < 32 && lpr < P->lanes_per_row) lpr <<= 1;
     }
+    // binary rows with d <= 256: bit masks, one lane per row
+    int kmode = mode;
+    uint32_t *bits = nullptr;
+    if (mode == MODE_BINARY && D.d <= 256 && (P->flags & SVM_FLAG_CSR_ROWS) == 0) {
+        kmode = D.d <= 128 ? MODE_BITS4 : MODE_BITS8;
+        lpr = 1;
+        const int W = mode_words(kmode);
+        bits = ar.alloc<uint32_t>((size_t)n * W);
+        k_bits<<<grid1(n), 256, 0, st>>>(n, W, D.indptr, D.indices, bits);
+        CK(cudaGetLastError());
+        ++launches;
+    }
     const int sms = device_sms();
     int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 15) / 16));
     if (P->ctas > 0) G = (int)std::min<int64_t>(std::min<int64_t>(P->ctas, sms), n);
     if (G > 256) G = 256;
     const int kt = mode == MODE_BINARY ? ktab_len : 0;
     const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
-    // thread-block clusters of 8 CTAs for the hierarchical exchange
+    // thread-block clusters for the hierarchical exchange: one cluster of 16
+    // when its segments stay in shared memory (no global exchange at all),
+    // else clusters of 8 with a leader exchange through global memory
     int cs = 1;
     {
-        const SmoLayout L0 = smo_layout(mode, (int)D.d, kt, D.maxnnz, 0, 0, 0);
-        if ((P->flags & SVM_FLAG_NO_CLUSTERS) == 0 && G >= 16 && L0.total <= lim_dyn) {
-            const int maxc = smo_max_clusters(mode, lpr, 0, L0.total, 8);
+        const SmoLayout L0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0);
+        const bool clusters_ok = (P->flags & SVM_FLAG_NO_CLUSTERS) == 0 && L0.total <= lim_dyn;
+        bool single = false;
+        if (clusters_ok && (P->ctas == 0 || P->ctas == 16) && n >= 16 * 32 &&
+            (P->flags & SVM_FLAG_STREAM_ROWS) == 0) {
+            const int rows16 = (int)((n + 15) / 16);
+            const int64_t nnz16 = (int64_t)(1.25 * (double)D.nnz / 16.0) + D.maxnnz;   // segment estimate
+            const SmoLayout L16 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, rows16, nnz16);
+            if (L16.total <= lim_dyn && smo_max_clusters(kmode, lpr, 2, L16.total, 16) >= 1 &&
+                (P->ctas == 16 || n <= 200000)) {
+                single = true;
+                cs = 16;
+                G = 16;
+            }
+        }
+        if (!single && clusters_ok && G >= 16) {
+            const int maxc = smo_max_clusters(kmode, lpr, 0, L0.total, 8);
             if (maxc >= 2) {
                 cs = 8;
                 G = 8 * std::min(maxc, G / 8);
@@ -533,21 +575,33 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         }
     }
     // segment sizes decide whether the rows stay in shared memory
-    int64_t *segnnz_d = ar.alloc<int64_t>(G);
-    k_seg_nnz<<<grid1(G), 256, 0, st>>>(n, G, D.indptr, segnnz_d);
-    CK(cudaGetLastError());
-    ++launches;
-    std::vector<int64_t> segnnz(G);
-    CK(cudaMemcpyAsync(segnnz.data(), segnnz_d, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    int64_t *segnnz_d = ar.alloc<int64_t>(std::max(G, 256));
     int64_t seg_nnz_max = 0;
-    for (int64_t v : segnnz) seg_nnz_max = std::max(seg_nnz_max, v);
-    const int seg_rows_max = (int)((n + G - 1) / G);
-    const SmoLayout Ls = smo_layout(mode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max, seg_nnz_max);
-    const SmoLayout Lr = smo_layout(mode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max, seg_nnz_max);
-    int resident = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 && seg_nnz_max < ((int64_t)1 << 31) &&
+    int seg_rows_max = 0;
+    SmoLayout Ls{}, Lr{};
+    int resident = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        k_seg_nnz<<<grid1(G), 256, 0, st>>>(n, G, D.indptr, segnnz_d);
+        CK(cudaGetLastError());
+        ++launches;
+        std::vector<int64_t> segnnz(G);
+        CK(cudaMemcpyAsync(segnnz.data(), segnnz_d, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        seg_nnz_max = 0;
+        for (int64_t v : segnnz) seg_nnz_max = std::max(seg_nnz_max, v);
+        seg_rows_max = (int)((n + G - 1) / G);
+        Ls = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max, seg_nnz_max);
+        Lr = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max, seg_nnz_max);
+        resident = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 && seg_nnz_max < ((int64_t)1 << 31) &&
                    Lr.total <= lim_dyn;
-    if (resident && cs > 1 && smo_max_clusters(mode, lpr, 1, Lr.total, cs) * cs < G) resident = 0;
+        if (resident && cs > 1 && smo_max_clusters(kmode, lpr, G == cs ? 2 : 1, Lr.total, cs) * cs < G) resident = 0;
+        if (resident || cs != 16) break;
+        // the single cluster was chosen for on-chip segments that do not
+        // fit after all: clusters of 8 over the whole GPU instead
+        cs = 8;
+        const size_t s0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0).total;
+        G = 8 * std::max(1, std::min(smo_max_clusters(kmode, lpr, 0, s0, 8), std::min(sms, 256) / 8));
+    }
     const size_t smem = resident ? Lr.total : Ls.total;
     if (smem > lim_dyn) {
         set_err("d = %lld exceeds the shared-memory target rows of this mode", (long long)D.d);
@@ -569,7 +623,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     int32_t *act = ar.alloc<int32_t>(n);
     int32_t *seg_cnt = ar.alloc<int32_t>(G);
     void *cand = ar.alloc<unsigned char>(2 * (size_t)G * smo_cand_bytes());
-    unsigned *seq = ar.alloc<unsigned>(2 * (size_t)G);
+    unsigned *seq = ar.alloc<unsigned>(smo_seq_words(G));
     SmoCtrl *ctrl = ar.alloc<SmoCtrl>(1);
     const int64_t trace_len = (P->trace && P->trace_len > 0) ? P->trace_len : 0;
     int32_t *trace = ar.alloc<int32_t>(2 * std::max<int64_t>(trace_len, 1));
@@ -605,6 +659,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.y = D.y;
     A.norm = D.norm;
     A.normf = D.normf;
+    A.bits = bits;
     A.alpha = alpha;
     A.f = f;
     A.status = status;
@@ -638,13 +693,13 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     double ms_smo = 0.0, ms_recon = 0.0;
     auto run = [&](int select_only, double thr, int64_t hh, int64_t limit) {
         CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
-        CK(cudaMemsetAsync(seq, 0, 2 * sizeof(unsigned) * G, st));
+        CK(cudaMemsetAsync(seq, 0, sizeof(unsigned) * smo_seq_words(G), st));
         A.thr = thr;
         A.h = hh;
         A.iter_limit = limit;
         A.select_only = select_only;
         CK(cudaEventRecord(e0, st));
-        CK(launch_smo_persistent(mode, lpr, A, smem, st, cs));
+        CK(launch_smo_persistent(kmode, lpr, A, smem, st, cs));
         CK(cudaEventRecord(e1, st));
         ++launches;
         CK(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));
@@ -794,6 +849,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         stats->ctas = G;
         stats->cluster_size = cs;
         stats->lanes_per_row = lpr;
+        stats->bit_rows = mode_bits(kmode) ? 1 : 0;
+        stats->reserved = 0;
         int dev = 0, khz = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
@@ -1656,7 +1713,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     int32_t *act = W.take<int32_t>(n);
     int32_t *seg_cnt = W.take<int32_t>(G);
     void *cand = W.take<unsigned char>(2 * (size_t)G * smo_cand_bytes());
-    unsigned *seq = W.take<unsigned>(2 * (size_t)G);
+    unsigned *seq = W.take<unsigned>(smo_seq_words(G));
     SmoCtrl *ctrl = W.take<SmoCtrl>(1);
     const int nbf = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 4095) / 4096));
     FinishPart *parts = W.take<FinishPart>(nbf);
@@ -1701,7 +1758,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     A.timeout_ns = 10ll * 1000 * 1000 * 1000;
     // every call starts from a zeroed exchange area and a fresh control block
     CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(seq, 0, 2 * sizeof(unsigned) * G, st));
+    CK(cudaMemsetAsync(seq, 0, sizeof(unsigned) * smo_seq_words(G), st));
     CK(launch_smo_persistent(mode, lpr, A, L0.total, st, cs));
     ++launches;
     CK(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));

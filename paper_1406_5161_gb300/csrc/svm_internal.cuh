@@ -22,7 +22,11 @@ __host__ __device__ __forceinline__ uint8_t st_of(int8_t y, double a, double C)
 }
 
 // Row-pass arithmetic of the fused step.
-enum { MODE_BINARY = 0, MODE_FP64 = 1, MODE_MIXED = 2 };
+enum { MODE_BINARY = 0, MODE_FP64 = 1, MODE_MIXED = 2, MODE_BITS4 = 3, MODE_BITS8 = 4 };
+// Binary rows held as bit masks of 4 or 8 words (d <= 128 or d <= 256): the
+// squared distance of two binary rows is the popcount of their XOR.
+__host__ __device__ constexpr bool mode_bits(int m) { return m == MODE_BITS4 || m == MODE_BITS8; }
+__host__ __device__ constexpr int mode_words(int m) { return m == MODE_BITS8 ? 8 : 4; }
 
 // Solver state carried between launches of the persistent step kernel.
 struct SmoCtrl {
@@ -55,6 +59,7 @@ struct SmoArgs {
     const float *vmix;         // mixed mode: values rounded to BF16, held as FP32
     const int8_t *y;
     const double *norm;        // ||x_i||^2 (FP64 / binary: exact)
+    const uint32_t *bits;      // bit-mask modes: row i = words [i * W, (i + 1) * W)
     const float *normf;        // mixed: ||x_i||^2 of the rounded values
     double *alpha;
     double *f;
@@ -139,7 +144,7 @@ cudaError_t launch_smo_batch(int mode, int lpr, int dense, const BatchArgs &a, s
 
 // Dynamic shared-memory layout of the step kernel (byte offsets).
 struct SmoLayout {
-    size_t tgt, tcol, ktab, f, alpha, nrm, rowptr, act, st, col, val, total;
+    size_t tgt, tcol, ktab, f, alpha, nrm, rowptr, act, st, col, val, bits, dist, total;
 };
 
 __host__ __device__ inline size_t smo_align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -148,20 +153,24 @@ __host__ __device__ inline SmoLayout smo_layout(int mode, int d, int ktab_len, i
                                                 int resident, int rows, int64_t nnz)
 {
     SmoLayout L;
-    size_t tgt_sz = mode == 0 ? 2 : (mode == 1 ? 16 : 8);
+    const bool bits = mode_bits(mode);
+    size_t tgt_sz = bits ? 0 : (mode == 0 ? 2 : (mode == 1 ? 16 : 8));
     size_t o = 0;
     L.tgt = o;    o = smo_align16(o + 2 * (size_t)d * tgt_sz);
-    L.tcol = o;   o = smo_align16(o + 4 * (size_t)(maxnnz > 0 ? maxnnz : 1) * 4);
-    L.ktab = o;   o = smo_align16(o + (mode == 0 ? (size_t)ktab_len * 16 : 0));  // exp and 1/eta tables
+    L.tcol = o;   o = smo_align16(o + (bits ? 0 : 4 * (size_t)(maxnnz > 0 ? maxnnz : 1) * 4));
+    L.ktab = o;   o = smo_align16(o + (mode == 0 || bits ? (size_t)ktab_len * 16 : 0));  // exp and 1/eta tables
     if (!resident) rows = 0, nnz = 0;
+    if (bits) nnz = 0;
     L.f = o;      o = smo_align16(o + (size_t)rows * 8);
     L.alpha = o;  o = smo_align16(o + (size_t)rows * 8);
     L.nrm = o;    o = smo_align16(o + (size_t)rows * (mode == 1 ? 8 : (mode == 2 ? 4 : 0)));
-    L.rowptr = o; o = smo_align16(o + (size_t)(resident ? rows + 1 : 0) * 4);
+    L.rowptr = o; o = smo_align16(o + (size_t)(resident && !bits ? rows + 1 : 0) * 4);
     L.act = o;    o = smo_align16(o + (size_t)rows * 4);
     L.st = o;     o = smo_align16(o + (size_t)rows);
     L.col = o;    o = smo_align16(o + (size_t)nnz * 2);
     L.val = o;    o = smo_align16(o + (size_t)nnz * (mode == 0 ? 0 : 4));
+    L.bits = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 * mode_words(mode) : 0));
+    L.dist = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 : 0));   // two 16-bit distances per row
     L.total = o;
     return L;
 }
@@ -173,12 +182,18 @@ __host__ __device__ __forceinline__ int64_t seg_lo(int64_t n, int G, int s)
 
 // ---------------------------------------------------------------- launchers
 // (each returns a cudaError_t; kernels live in their own translation units)
-// cs = CTAs per thread-block cluster (1 or 8); G must be a multiple of cs
+// cs = CTAs per thread-block cluster (1, 8 or 16); G must be a multiple of cs
 cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem,
                                   cudaStream_t st, int cs);
-// clusters of cs CTAs that can be resident at once (0 on error)
+// clusters of cs CTAs that can be resident at once (0 on error); resident:
+// 0 streamed segments, 1 on-chip segments, 2 on-chip segments with the grid
+// one cluster (the kernel that launch_smo_persistent picks when G == cs)
 int smo_max_clusters(int mode, int lpr, int resident, size_t smem, int cs);
-size_t smo_cand_bytes();
+size_t smo_cand_bytes();   // bytes of one global candidate slot
+// global exchange flags: one per leader and epoch parity, kSeqStride words
+// apart (a 128-byte line each); the array holds smo_seq_words(G) words
+constexpr int kSeqStride = 32;
+__host__ __device__ inline size_t smo_seq_words(int G) { return 2 * (size_t)G * kSeqStride; }
 size_t smo_static_smem();
 int smo_threads();
 

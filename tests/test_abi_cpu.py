@@ -62,3 +62,28 @@ def test_bad_shrink_policy_is_reported():
     p = synth.small_dense(10, 3, seed=1)
     r = pkg.svm_train(p.X, p.y, 1.0, 0.1, 1e-3, shrink=(9, 1, 0), check=False)
     assert r["status"] == pkg.SVM_ERR_ARG
+
+
+def test_flag_constants_match_header():
+    src = "".join(open(h).read() for h in glob.glob(os.path.join(ROOT, "include", "*.h")))
+    defines = dict(re.findall(r"^#define (SVM_FLAG_\w+) (\d+)", src, flags=re.M))
+    assert defines, "no SVM_FLAG_* in the header"
+    for name, value in defines.items():
+        assert getattr(pkg, name) == int(value), name
+
+
+def test_ctypes_struct_sizes_match_header(tmp_path):
+    """The Python binding's ctypes structures have the C header's sizes."""
+    from paper_1406_5161_gb300 import _abi
+    names = ["svm_csr", "svm_params", "svm_shrink_policy", "svm_stats"]
+    prog = "#include <stdio.h>\n#include \"svm_gb300.h\"\nint main(void){\n" + "".join(
+        f'printf("%zu\\n", sizeof({n}));\n' for n in names) + "return 0;}\n"
+    (tmp_path / "sz.c").write_text(prog)
+    exe = str(tmp_path / "sz")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(tmp_path / "sz.c"),
+                    "-o", exe], check=True)
+    sizes = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
+                                            check=True).stdout.split()]
+    import ctypes
+    for n, s in zip(names, sizes):
+        assert ctypes.sizeof(getattr(_abi, n)) == s, n

@@ -103,12 +103,15 @@ def c2():
     return p, ref
 
 
-@pytest.mark.parametrize("flags", [0, pkg.SVM_FLAG_STREAM_ROWS], ids=["resident", "streamed"])
+@pytest.mark.parametrize("flags", [0, pkg.SVM_FLAG_STREAM_ROWS, pkg.SVM_FLAG_CSR_ROWS,
+                                   pkg.SVM_FLAG_CSR_ROWS | pkg.SVM_FLAG_STREAM_ROWS],
+                         ids=["bits-resident", "bits-streamed", "csr-resident", "csr-streamed"])
 def test_onehot_32561_binary_fp64(c2, flags):
     p, ref = c2
     r, Xd, yd = gpu_train(p, trace_len=400, flags=flags)
     assert r["status"] == pkg.SVM_OK
     assert r["stats"]["binary_input"] == 1
+    assert r["stats"]["bit_rows"] == int(not flags & pkg.SVM_FLAG_CSR_ROWS)
     t = first_mismatch(r["trace"], ref["trace"], ref["margin"], 400)
     assert t >= 200
     check_end_state(p, r, ref)
@@ -135,6 +138,52 @@ def test_ragged_sparse_rows(binary, flags):
     alpha, _ = check_end_state(p, r, ref)
     if t == ref["iters"] and r["iters"] == ref["iters"]:
         assert np.abs(alpha - ref["alpha"]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("d", [1, 37, 128, 129, 256, 257])
+def test_bit_mask_rows_equal_csr_rows(d):
+    """Binary rows read as bit masks (4 words up to d = 128, 8 up to 256) give
+    the same steps and the same alpha as the CSR gather and the oracle; d = 257
+    falls back to CSR rows. Empty rows, a ragged tail and, at d = 1, many
+    duplicate rows (flat curvature) are included."""
+    n = 2501
+    p = synth.random_sparse(n, d, min(0.5, 6.0 / d), seed=d, binary=True, C=1.5, gamma=0.15)
+    ref = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, trace_len=300)
+    a, _, _ = gpu_train(p, trace_len=300)
+    b, _, _ = gpu_train(p, trace_len=300, flags=pkg.SVM_FLAG_CSR_ROWS)
+    assert a["stats"]["bit_rows"] == int(d <= 256) and b["stats"]["bit_rows"] == 0
+    assert np.array_equal(a["trace"], b["trace"])
+    assert a["iters"] == b["iters"]
+    assert np.array_equal(a["alpha"].cpu().numpy(), b["alpha"].cpu().numpy())
+    t = first_mismatch(a["trace"], ref["trace"], ref["margin"], 300)
+    assert t >= min(200, ref["iters"])
+    check_end_state(p, a, ref)
+
+
+@pytest.mark.parametrize("flags", [0, pkg.SVM_FLAG_CSR_ROWS], ids=["bits", "csr"])
+def test_launch_shapes_give_identical_solves(flags):
+    """One 16-CTA cluster (no global exchange), clusters of 8 over the whole
+    GPU, and no clusters: the selection is exact and each f update is per
+    row, so all shapes take the same steps to the same alpha."""
+    p = synth.onehot_sparse(n=6000, n_test=0, seed=12)
+    kind, value, recon = pkg.POLICIES["Multi5pc"]
+    runs = {}
+    for name, kw in {"single16": dict(ctas=16), "clusters8": dict(ctas=152),
+                     "flat": dict(ctas=152, flags=flags | pkg.SVM_FLAG_NO_CLUSTERS),
+                     "auto": dict()}.items():
+        kw.setdefault("flags", flags)
+        r, _, _ = gpu_train(p, shrink=(kind, value, recon), trace_len=2000, **kw)
+        assert r["status"] == pkg.SVM_OK
+        runs[name] = r
+    assert runs["single16"]["stats"]["cluster_size"] == 16 and runs["single16"]["stats"]["ctas"] == 16
+    assert runs["clusters8"]["stats"]["cluster_size"] == 8
+    assert runs["flat"]["stats"]["cluster_size"] == 1
+    base = runs["single16"]
+    for name, r in runs.items():
+        assert r["iters"] == base["iters"], name
+        assert np.array_equal(r["trace"], base["trace"]), name
+        assert np.array_equal(r["alpha"].cpu().numpy(), base["alpha"].cpu().numpy()), name
+        assert r["b"] == base["b"], name
 
 
 @pytest.mark.parametrize("dist,C,gamma", [(1.0, 100.0, 0.5), (3.0, 0.4, 0.1)])
