@@ -24,10 +24,12 @@ workload on the host cores; only rank 0 runs it.
 from __future__ import annotations
 
 import argparse
+import atexit
 import hashlib
 import json
 import os
 import statistics
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -88,12 +90,20 @@ class ClockSampler:
     def start(self):
         fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
         os.close(fd)
+        cmd = ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200", "-f", self.path]
+        if shutil.which("timeout"):
+            cmd = ["timeout", "900"] + cmd   # never outlives a crashed run by much
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+        if self.proc is not None:
+            atexit.register(self._kill)
+
+    def _kill(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.kill()
 
     def stop(self) -> dict:
         if self.proc is None:

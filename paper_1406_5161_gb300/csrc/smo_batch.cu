@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                     if (ml) res.low = sh.ccand[__ffs(ml) - 1].low; else side_empty(res.low, false);
                     res.total = m;
                     res.flag = 0;
-                    res.pad = 0;
+                    res.gap_open = 1;   // the batch kernel tests the gap itself
                     *cluster.map_shared_rank(&sh.res, lane) = res;
                 }
             }

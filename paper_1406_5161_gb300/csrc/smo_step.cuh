@@ -152,7 +152,7 @@ struct __align__(16) ResultArea {   // (sizeof a multiple of 16)
     Side up, low;
     long long total;   // active-set size over all segments
     int flag;          // a wait timed out
-    int pad;
+    int gap_open;      // b_low - b_up > the launch's threshold (Eq. kktterm): step on
 };
 
 // FP64 compares and selects are long-latency on sm_103a; comparisons here
@@ -525,6 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     const float gammaf = (float)A.gamma;
     unsigned epoch = 0;
     int exit_reason = 0;
+    bool gap_open = first || dless(A.thr, low.f - up.f);   // stopping test of the pair in up / low
     int prev_valid = 0;              // buffer (1 - buf) holds the previous targets
     int prev_len_u = 0, prev_len_l = 0;
     // optional per-phase cycle counts of CTA 0 (one clock read per phase)
@@ -543,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         const double bup_sel = up.f, blow_sel = low.f;   // values that chose this pair
         if (busy_on && tid == 0) cta_t0 = clock64();
         if (!first) {
-            if (!dless(A.thr, low.f - up.f)) { exit_reason = 0; break; }
+            if (!gap_open) { exit_reason = 0; break; }
             if (iter >= A.iter_limit) { exit_reason = 1; break; }
             // ---- 1. targets: x_up into .x / byte 0, x_low into .y / byte 1
             //         (bit-mask modes: the masks came with the exchange)
@@ -1001,7 +1002,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     if (ml) copy_side(&sh.res.low, &sh.xc[par][__ffs(ml) - 1].low); else side_empty(sh.res.low, false);
                     sh.res.total = cc;
                     sh.res.flag = timed_out;
-                    sh.res.pad = 0;
+                    sh.res.gap_open = dless(A.thr, sh.res.low.f - sh.res.up.f);
                 }
             }
             __syncthreads();
@@ -1102,7 +1103,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         if (il != INT_MAX) copy_side(&sh.res.low, &sh.rlow[wl]); else side_empty(sh.res.low, false);
                         sh.res.total = cc;
                         sh.res.flag = to;
-                        sh.res.pad = 0;
+                        sh.res.gap_open = dless(A.thr, sh.res.low.f - sh.res.up.f);
                     }
                     __syncwarp();
                     if (lane > 0 && lane < csize) copy_result(cluster.map_shared_rank(&sh.res, lane), &sh.res);
@@ -1118,6 +1119,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         up = sh.res.up;
         low = sh.res.low;
         total = sh.res.total;
+        gap_open = sh.res.gap_open != 0;
         if (!first) {
             ++iter;
             if (shrink_now) {
@@ -1205,24 +1207,27 @@ cudaError_t launch_mode(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st,
     }
     SmoArgs args = a;
     void *params[] = {&args};
+    // A grid of one cluster is co-scheduled by the hardware; several
+    // clusters wait on one another, so that launch is cooperative.
+    const bool one_cluster = a.G == cs;
     cudaLaunchAttribute attrs[2];
-    attrs[0].id = cudaLaunchAttributeCooperative;
-    attrs[0].val.cooperative = 1;
-    attrs[1].id = cudaLaunchAttributeClusterDimension;
-    attrs[1].val.clusterDim.x = (unsigned)cs;
-    attrs[1].val.clusterDim.y = 1;
-    attrs[1].val.clusterDim.z = 1;
+    attrs[0].id = cudaLaunchAttributeClusterDimension;
+    attrs[0].val.clusterDim.x = (unsigned)cs;
+    attrs[0].val.clusterDim.y = 1;
+    attrs[0].val.clusterDim.z = 1;
+    attrs[1].id = cudaLaunchAttributeCooperative;
+    attrs[1].val.cooperative = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.G);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = attrs;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = one_cluster ? 1 : 2;
     // all CTAs must be resident at once (they wait on one another)
     int nclusters = 0;
     cudaLaunchConfig_t q = cfg;
-    q.attrs = attrs + 1;
+    q.attrs = attrs;
     q.numAttrs = 1;
     e = cudaOccupancyMaxActiveClusters(&nclusters, fn, &q);
     if (e != cudaSuccess) return e;
