@@ -133,6 +133,19 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
+def job_totals(dist, seconds: float, units: float, device) -> tuple[float, float]:
+    """Whole-job figures over replicas (one per rank, no data-path collective):
+    the slowest rank's time and the sum of the units all ranks processed."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for name in ("smo_step.cuh", "svm_internal.cuh"):
@@ -277,16 +290,7 @@ def run_gb300(args, rank, world, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(c) for a, c in zip(e0, e2)]
     kkt_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-    t_total = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-        it = torch.tensor([iters], dtype=torch.float64, device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        iters_all = float(it.item())
-    else:
-        iters_all = float(iters)
+    t_total, iters_all = job_totals(dist, sum(step_ms) / 1e3, float(iters), "cuda")
     value = iters_all / t_total
 
     # ---- end to end through the public API with host buffers
@@ -306,6 +310,8 @@ def run_gb300(args, rank, world, local):
         alpha_h = pinned(np.zeros(p.X.n))
         out_h = pinned(np.zeros(p.Z.n))
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         e2e_iters = 0
         n_e2e = max(1, min(3, args.steps))
@@ -314,11 +320,11 @@ def run_gb300(args, rank, world, local):
                               max_iter=args.max_iter)
             pkg.svm_decision(Xh, yh, alpha_h, r["b"], p.gamma, Zh, out=out_h)
             e2e_iters += r["iters"]
-        dt = time.perf_counter() - t0
+        dt, e2e_all = job_totals(dist, time.perf_counter() - t0, float(e2e_iters), "cuda")
         nbytes = lambda X: X.indptr.nbytes + X.indices.nbytes + X.values.nbytes  # noqa: E731
         h2d = (nbytes(p.X) + p.y.nbytes) * 2 + 8 * p.X.n + nbytes(p.Z)
         d2h = 8 * p.X.n + 8 * p.Z.n
-        e2e = {"value": e2e_iters / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": e2e_all / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * dt / n_e2e}
 
     if rank != 0:

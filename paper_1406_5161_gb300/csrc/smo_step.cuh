@@ -191,18 +191,18 @@ __device__ __forceinline__ bool ki_less(unsigned long long k, int i, unsigned lo
     return k < bk || (k == bk && i < bi);
 }
 
-// Warp minimum of (key, index); every lane ends with the winner.
+// Warp minimum of (key, index) in lexicographic order; every lane ends with
+// the winner. Three 32-bit warp reductions (high key word, low key word
+// among the lanes that hold the least high word, index among the lanes that
+// hold the least key); indices are non-negative, INT_MAX marks no candidate.
 __device__ __forceinline__ void warp_min_ki(unsigned long long &k, int &i)
 {
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        unsigned long long ko = __shfl_xor_sync(0xffffffffu, k, off);
-        int io = __shfl_xor_sync(0xffffffffu, i, off);
-        if (ki_less(ko, io, k, i)) {
-            k = ko;
-            i = io;
-        }
-    }
+    const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? lo : 0xffffffffu);
+    const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mhi && lo == mlo) ? (unsigned)i : 0xffffffffu);
+    k = ((unsigned long long)mhi << 32) | mlo;
+    i = (int)mi;
 }
 
 __device__ __forceinline__ void side_empty(Side &s, bool up)
@@ -384,9 +384,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         for (int c = tid; c < 2 * d; c += kThreads) tgt_clear<MODE>(tbuf[c]);
     }
     if constexpr (MODE == MODE_BINARY || BITS) {
-        for (int c = tid; c < 2 * A.ktab_len; c += kThreads) ktab[c] = A.ktab[c];
+        for (int c = tid; c < 3 * A.ktab_len; c += kThreads) ktab[c] = A.ktab[c];
     }
-    const double *rtab = ktab + A.ktab_len;
+    const double *rtab = ktab + A.ktab_len;      // 1 / eta (0 when eta <= 1e-12)
+    const double *etab = ktab + 2 * A.ktab_len;  // eta = 2 - 2 exp(-gamma k)
     int cnt = A.seg_cnt[cta];
     if constexpr (RES) {
         for (int r = tid; r < nseg; r += kThreads) {
@@ -596,44 +597,51 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 }
                 if (timed && tid == 0) { uint64_t t = clock64(); ph[6] += t - tp; tp = t; }
                 if (lane == 0) {
-                    double kul, rinv = 0.0;
+                    // kernel value K(up, low) and, from the tables on binary
+                    // input, eta = 2 - 2K with the correctly rounded 1 / eta
+                    double kul, rinv = 0.0, eta;
+                    bool curved;
                     if constexpr (MODE == MODE_BINARY || BITS) {
                         int dist = BITS ? s : up.len + low.len - 2 * s;
                         dist = dist < 0 ? 0 : dist;
                         kul = ktab[dist];
                         rinv = rtab[dist];
-                    } else if constexpr (MODE == MODE_FP64) {
-                        double d2 = up.nrm + low.nrm - 2.0 * s;
-                        kul = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                        eta = etab[dist];
+                        curved = __double_as_longlong(rinv) != 0;   // eta > 1e-12
                     } else {
-                        float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
-                        kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
+                        if constexpr (MODE == MODE_FP64) {
+                            double d2 = up.nrm + low.nrm - 2.0 * s;
+                            kul = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                        } else {
+                            float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
+                            kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
+                        }
+                        eta = 2.0 - 2.0 * kul;
+                        curved = dless(1e-12, eta);
                     }
                     // Eq. (alphaup) with rho = -eta (Eq. rho), K(x,x) = 1,
                     // clipped to the feasible segment [L, H]; end-point rule
-                    // for a flat curvature. The FP64 arithmetic is the
-                    // oracle's operation for operation; comparisons, clamps
-                    // and multiplications by y = +-1 are done on the bit
-                    // patterns (exact, and short-latency on this part).
+                    // for a flat curvature. Each FP64 operation is the
+                    // oracle's (same operands, same order). On this part a
+                    // warp's FP64 instructions issue about one per 64 cycles,
+                    // so signs y = +-1 are applied by choosing operands, and
+                    // comparisons, clamps and snaps work on integer keys.
                     const bool yu_neg = up.y < 0, yl_neg = low.y < 0;
                     const double au = up.a, al = low.a;
-                    const double eta = 2.0 - 2.0 * kul;
                     const bool opposite = yu_neg != yl_neg;
-                    double Lo, Hi;
-                    if (opposite) {
-                        const double x = al - au;
-                        Lo = dless(x, 0.0) ? 0.0 : x;
-                        const double h = C + al - au;
-                        Hi = dless(h, C) ? h : C;
-                    } else {
-                        const double x = al + au - C;
-                        Lo = dless(x, 0.0) ? 0.0 : x;
-                        const double h = al + au;
-                        Hi = dless(h, C) ? h : C;
-                    }
-                    const double slope = neg_if(up.f - low.f, yl_neg);
-                    double aln;
-                    if (dless(1e-12, eta)) {
+                    // slope = y_low (f_up - f_low)
+                    const double slope = (yl_neg ? low.f : up.f) - (yl_neg ? up.f : low.f);
+                    // [L, H]: opposite labels L = max(0, al - au),
+                    // H = min(C, (C + al) - au); equal labels L = max(0,
+                    // (al + au) - C), H = min(C, al + au)
+                    const double v1 = al + (opposite ? neg_if(au, true) : au);
+                    const double w = (opposite ? C : v1) + (opposite ? al : neg_if(C, true));
+                    const double h3 = w - au;
+                    const double xL = opposite ? v1 : w, xH = opposite ? h3 : v1;
+                    const double Lo = dless(xL, 0.0) ? 0.0 : xL;
+                    const double Hi = dless(xH, C) ? xH : C;
+                    double alc;
+                    if (curved) {
                         double q;
                         if constexpr (MODE == MODE_BINARY || BITS) {
                             // slope / eta from the correctly rounded 1/eta of
@@ -646,32 +654,38 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             q = slope / eta;
                         }
                         const double t = al + q;
-                        aln = dless(t, Lo) ? Lo : (dless(Hi, t) ? Hi : t);
+                        const unsigned long long kt = dkey(t);
+                        alc = kt < dkey(Lo) ? Lo : (dkey(Hi) < kt ? Hi : t);
                     } else {
-                        aln = dless(0.0, slope) ? Hi : Lo;
+                        alc = dless(0.0, slope) ? Hi : Lo;
                     }
-                    double aun = au + neg_if(al - aln, opposite);
-                    if (dless(aln, snap)) aln = 0.0;
-                    if (dless(c_snap, aln)) aln = C;
-                    if (dless(aun, snap)) aun = 0.0;
-                    if (dless(c_snap, aun)) aun = C;
-                    sh.du = neg_if(aun - au, yu_neg);
-                    sh.dl = neg_if(aln - al, yl_neg);
+                    // alpha_up' = au + s (al - alpha_low'), s = y_up y_low,
+                    // from the clipped (not yet snapped) alpha_low'
+                    const double aunc = fma(opposite ? -1.0 : 1.0, al - alc, au);
+                    const unsigned long long ka = dkey(alc), ku = dkey(aunc);
+                    const unsigned long long ks = dkey(snap), kc = dkey(c_snap);
+                    const double aln = ka < ks ? 0.0 : (kc < ka ? C : alc);
+                    const double aun = ku < ks ? 0.0 : (kc < ku ? C : aunc);
+                    // y_up (alpha_up' - au) and y_low (alpha_low' - al)
+                    sh.du = (yu_neg ? au : aun) - (yu_neg ? aun : au);
+                    sh.dl = (yl_neg ? al : aln) - (yl_neg ? aln : al);
                     sh.au_new = aun;
                     sh.al_new = aln;
                     sh.st_u = status_of(!yu_neg, aun, C);
                     sh.st_l = status_of(!yl_neg, aln, C);
                 }
                 __syncwarp();
-                step_bar_arrive(kThreads);
+                if constexpr (BITS && RES) step_bar_sync(kThreads);   // warp 0 joins the f updates
+                else step_bar_arrive(kThreads);
                 if (timed && tid == 0) { uint64_t t = clock64(); ph[1] += t - tp; tp = t; }
             }
         } else if constexpr (BITS && RES) {
             // ---- 3. row pass, bit-mask rows held on chip, in two sweeps
             //         over the active list: the squared distances of every
-            //         row to x_up and x_low while warp 0 runs the pair step,
-            //         then the FP64 f updates (Eq. fup), the shrink rule and
-            //         the candidates. A thread handles the same rows in both.
+            //         row to x_up and x_low (warps 1..) while warp 0 runs the
+            //         pair step, then, after a barrier of all warps, the FP64
+            //         f updates (Eq. fup), the shrink rule and the candidates
+            //         (all warps, below).
             if (!first) {
                 for (int k = tid - 32; k < cnt; k += kThreads - 32) {
                     const uint4 *rb = bits_s + (size_t)act_s[k] * W4;
@@ -687,40 +701,6 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     dist_s[k] = (uint32_t)du2 | ((uint32_t)dl2 << 16);
                 }
                 step_bar_sync(kThreads);
-            }
-            const double du = sh.du, dl = sh.dl, au_new = sh.au_new, al_new = sh.al_new;
-            const unsigned char st_u = sh.st_u, st_l = sh.st_l;
-            for (int k = tid - 32; k < cnt; k += kThreads - 32) {
-                const int r = act_s[k];
-                const int i = (int)(lo + r);
-                double fi = f_s[r];
-                uint8_t sb = st_s[r];
-                if (!first) {
-                    const uint32_t dd = dist_s[k];
-                    fi = fma(dl, ktab[dd >> 16], fma(du, ktab[dd & 0xffffu], fi));
-                    f_s[r] = fi;
-                    if (i == up.i) {
-                        sb = st_u;
-                        st_s[r] = sb;
-                        a_s[r] = au_new;
-                    } else if (i == low.i) {
-                        sb = st_l;
-                        st_s[r] = sb;
-                        a_s[r] = al_new;
-                    }
-                }
-                const uint8_t set = set_bits(sb);
-                bool keep = true;
-                if (shrink_now) {
-                    keep = !(((set == ST_I3 || set == ST_I4) && dless(fi, bup_sel)) ||
-                             ((set == ST_I1 || set == ST_I2) && dless(blow_sel, fi)));
-                    if (!keep) act_s[k] = ~r;
-                }
-                if (keep) {
-                    const unsigned long long kup = key_up(fi), klo = key_low(fi);
-                    if (st_up(set) && ki_less(kup, i, bku, biu)) { bku = kup; biu = i; bru = r; }
-                    if (st_low(set) && ki_less(klo, i, bkl, bil)) { bkl = klo; bil = i; brl = r; }
-                }
             }
         } else {
             // ---- 3. row pass over the segment's active list (warps 1..)
@@ -847,6 +827,43 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         if (st_up(set) && ki_less(kup, i, bku, biu)) { bku = kup; biu = i; bru = r; }
                         if (st_low(set) && ki_less(klo, i, bkl, bil)) { bkl = klo; bil = i; brl = r; }
                     }
+                }
+            }
+        }
+        if constexpr (BITS && RES) {
+            // second sweep, all warps: f updates, shrink rule, candidates
+            const double du = sh.du, dl = sh.dl, au_new = sh.au_new, al_new = sh.al_new;
+            const unsigned char st_u = sh.st_u, st_l = sh.st_l;
+            for (int k = tid; k < cnt; k += kThreads) {
+                const int r = act_s[k];
+                const int i = (int)(lo + r);
+                double fi = f_s[r];
+                uint8_t sb = st_s[r];
+                if (!first) {
+                    const uint32_t dd = dist_s[k];
+                    fi = fma(dl, ktab[dd >> 16], fma(du, ktab[dd & 0xffffu], fi));
+                    f_s[r] = fi;
+                    if (i == up.i) {
+                        sb = st_u;
+                        st_s[r] = sb;
+                        a_s[r] = au_new;
+                    } else if (i == low.i) {
+                        sb = st_l;
+                        st_s[r] = sb;
+                        a_s[r] = al_new;
+                    }
+                }
+                const uint8_t set = set_bits(sb);
+                bool keep = true;
+                if (shrink_now) {
+                    keep = !(((set == ST_I3 || set == ST_I4) && dless(fi, bup_sel)) ||
+                             ((set == ST_I1 || set == ST_I2) && dless(blow_sel, fi)));
+                    if (!keep) act_s[k] = ~r;
+                }
+                if (keep) {
+                    const unsigned long long kup = key_up(fi), klo = key_low(fi);
+                    if (st_up(set) && ki_less(kup, i, bku, biu)) { bku = kup; biu = i; bru = r; }
+                    if (st_low(set) && ki_less(klo, i, bkl, bil)) { bkl = klo; bil = i; brl = r; }
                 }
             }
         }

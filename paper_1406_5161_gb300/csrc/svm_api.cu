@@ -155,9 +155,10 @@ __global__ void k_norms(int64_t n, const int64_t *indptr, const float *values, d
     if (normf) normf[i] = sf;
 }
 
-// exp(-gamma * k) for the integer squared distances of binary rows, and
-// (second half) the correctly rounded reciprocal of eta = 2 - 2 exp(-gamma k)
-// used by the pair step (0 where eta <= 1e-12).
+// Tables over the integer squared distances k of binary rows (3 len
+// doubles): exp(-gamma * k); the correctly rounded reciprocal of
+// eta = 2 - 2 exp(-gamma k) used by the pair step (0 where eta <= 1e-12);
+// eta itself.
 __global__ void k_ktab(double gamma, int len, double *ktab)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,6 +167,7 @@ __global__ void k_ktab(double gamma, int len, double *ktab)
         const double eta = 2.0 - 2.0 * kv;
         ktab[k] = kv;
         ktab[len + k] = eta > 1e-12 ? 1.0 / eta : 0.0;
+        ktab[2 * len + k] = eta;
     }
 }
 
@@ -609,7 +611,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     }
     double *ktab = nullptr;
     if (mode == MODE_BINARY) {
-        ktab = ar.alloc<double>(2 * (size_t)ktab_len);
+        ktab = ar.alloc<double>(3 * (size_t)ktab_len);
         k_ktab<<<grid1(ktab_len), 256, 0, st>>>(P->gamma, ktab_len, ktab);
         CK(cudaGetLastError());
         ++launches;
@@ -910,7 +912,7 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     int ktab_len = DX.maxnnz + DZ.maxnnz + 1;
     double *ktab = nullptr;
     if (mode == MODE_BINARY) {
-        ktab = ar.alloc<double>(2 * (size_t)ktab_len);
+        ktab = ar.alloc<double>(3 * (size_t)ktab_len);
         k_ktab<<<grid1(ktab_len), 256, 0, st>>>(gamma, ktab_len, ktab);
         CK(cudaGetLastError());
         ++launches;
@@ -1676,7 +1678,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     const int ktab_len = 2 * h.maxnnz + 1;
     double *norm = nullptr, *ktab = nullptr;
     if (binary) {
-        ktab = W.take<double>(2 * (size_t)ktab_len);
+        ktab = W.take<double>(3 * (size_t)ktab_len);
         k_ktab<<<grid1(ktab_len), 256, 0, st>>>(P->gamma, ktab_len, ktab);
     } else {
         norm = W.take<double>(n);

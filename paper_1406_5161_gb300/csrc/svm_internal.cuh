@@ -73,6 +73,7 @@ struct SmoArgs {
     int64_t trace_len;
     const double *ktab;        // binary: exp(-gamma * k), k = 0 .. ktab_len - 1, followed by
                                // the correctly rounded 1 / (2 - 2 exp(-gamma * k)) (0 if <= 1e-12)
+                               // and by 2 - 2 exp(-gamma * k)
     int32_t ktab_len;
     int32_t maxnnz;            // longest row
     int32_t resident;          // segments held in shared memory
@@ -158,7 +159,7 @@ __host__ __device__ inline SmoLayout smo_layout(int mode, int d, int ktab_len, i
     size_t o = 0;
     L.tgt = o;    o = smo_align16(o + 2 * (size_t)d * tgt_sz);
     L.tcol = o;   o = smo_align16(o + (bits ? 0 : 4 * (size_t)(maxnnz > 0 ? maxnnz : 1) * 4));
-    L.ktab = o;   o = smo_align16(o + (mode == 0 || bits ? (size_t)ktab_len * 16 : 0));  // exp and 1/eta tables
+    L.ktab = o;   o = smo_align16(o + (mode == 0 || bits ? (size_t)ktab_len * 24 : 0));  // exp, 1/eta, eta tables
     if (!resident) rows = 0, nnz = 0;
     if (bits) nnz = 0;
     L.f = o;      o = smo_align16(o + (size_t)rows * 8);
