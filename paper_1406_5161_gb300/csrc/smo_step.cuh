@@ -30,6 +30,7 @@
 #pragma once
 
 #include <climits>
+#include <cstddef>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -314,7 +315,8 @@ struct Shared {
     int riup[8], rilow[8], rto[8];
     CandFull ccand[kMaxCluster];              // cluster leader: its CTAs' candidates
     CandFull xc[2][kMaxCluster];              // one cluster: every CTA's candidate, by epoch parity
-    CandFull mycand;                          // this CTA's candidate of the step
+    Side none[2];                             // empty I_up / I_low sides
+    int res_wu, res_wl;                       // one cluster: slots of the winning sides
     unsigned long long xbar[2];               // one cluster: mbarriers of the two parities
     ResultArea res;                           // exchange result pushed by the leader
     long long rcount[8];
@@ -452,6 +454,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     // asynchronous stores whose bytes each CTA counts on its own mbarrier
     // (one per epoch parity; the CTA's own arrival sets the expected bytes)
     constexpr bool solo = SOLO;
+    if (tid == 0) {
+        side_empty(sh.none[0], true);
+        side_empty(sh.none[1], false);
+    }
     if constexpr (SOLO) {
         if (nlead != 1) {   // launched over several clusters: refuse
             if (tid == 0) atomicExch(&A.ctrl->err, 1);
@@ -945,30 +951,31 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             warp_min_ki(k2, i2);
             const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
             const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
-            if (lane == 0) {
+            if constexpr (solo) {
+                // lane q sends the CTA's candidate to CTA q: the winning
+                // warps' sides straight from shared memory, then the count
+                if (lane < csize) {
+                    const uint32_t dst = cluster_addr(smem_u32(&sh.xc[par][crank]), lane);
+                    const uint32_t rbar = cluster_addr(smem_u32(&sh.xbar[par]), lane);
+                    const uint4 *su = reinterpret_cast<const uint4 *>(mu ? &sh.wup[__ffs(mu) - 1] : &sh.none[0]);
+                    const uint4 *sl = reinterpret_cast<const uint4 *>(ml ? &sh.wlow[__ffs(ml) - 1] : &sh.none[1]);
+                    constexpr int kSideV = (int)(sizeof(Side) / 16);
+#pragma unroll
+                    for (int j = 0; j < kSideV; ++j) st_async_v4(dst + 16 * j, su[j], rbar);
+#pragma unroll
+                    for (int j = 0; j < kSideV; ++j) st_async_v4(dst + (uint32_t)sizeof(Side) + 16 * j, sl[j], rbar);
+                    st_async_v4(dst + (uint32_t)offsetof(CandFull, count), make_uint4((unsigned)cnt, 0u, 0u, 0u), rbar);
+                }
+                if (lane == 0)
+                    mbar_arrive_expect_tx(smem_u32(&sh.xbar[par]), (uint32_t)(csize * sizeof(CandFull)));
+            } else if (lane == 0) {
                 CandFull cf;
                 if (mu) cf.up = sh.wup[__ffs(mu) - 1]; else side_empty(cf.up, true);
                 if (ml) cf.low = sh.wlow[__ffs(ml) - 1]; else side_empty(cf.low, false);
                 cf.count = cnt;
                 cf.pad[0] = cf.pad[1] = cf.pad[2] = 0;
-                if constexpr (solo) {
-                    sh.mycand = cf;
-                } else {
-                    CandFull *dst = cluster.map_shared_rank(sh.ccand, 0);
-                    dst[crank] = cf;
-                }
-            }
-            if constexpr (solo) {
-                __syncwarp();
-                if (lane < csize) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(&sh.mycand);
-                    const uint32_t dst = cluster_addr(smem_u32(&sh.xc[par][crank]), lane);
-                    const uint32_t rbar = cluster_addr(smem_u32(&sh.xbar[par]), lane);
-#pragma unroll
-                    for (int j = 0; j < (int)(sizeof(CandFull) / 16); ++j) st_async_v4(dst + 16 * j, src[j], rbar);
-                }
-                if (lane == 0)
-                    mbar_arrive_expect_tx(smem_u32(&sh.xbar[par]), (uint32_t)(csize * sizeof(CandFull)));
+                CandFull *dst = cluster.map_shared_rank(sh.ccand, 0);
+                dst[crank] = cf;
             }
             if (lane == 0) {
                 if (busy_on) busy += clock64() - cta_t0;
@@ -1015,11 +1022,15 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                 const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
                 if (lane == 0) {
-                    if (mu) copy_side(&sh.res.up, &sh.xc[par][__ffs(mu) - 1].up); else side_empty(sh.res.up, true);
-                    if (ml) copy_side(&sh.res.low, &sh.xc[par][__ffs(ml) - 1].low); else side_empty(sh.res.low, false);
+                    // the winners stay in their slots (rewritten two steps on)
+                    const int wu = mu ? __ffs(mu) - 1 : -1, wl = ml ? __ffs(ml) - 1 : -1;
+                    sh.res_wu = wu;
+                    sh.res_wl = wl;
                     sh.res.total = cc;
                     sh.res.flag = timed_out;
-                    sh.res.gap_open = dless(A.thr, sh.res.low.f - sh.res.up.f);
+                    const double fu = wu >= 0 ? sh.xc[par][wu].up.f : sh.none[0].f;
+                    const double fl = wl >= 0 ? sh.xc[par][wl].low.f : sh.none[1].f;
+                    sh.res.gap_open = dless(A.thr, fl - fu);
                 }
             }
             __syncthreads();
@@ -1133,8 +1144,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         prev_valid = first ? 0 : 1;
         prev_len_u = up.len;
         prev_len_l = low.len;
-        up = sh.res.up;
-        low = sh.res.low;
+        if constexpr (solo) {
+            const int wu = sh.res_wu, wl = sh.res_wl;
+            up = wu >= 0 ? sh.xc[par][wu].up : sh.none[0];
+            low = wl >= 0 ? sh.xc[par][wl].low : sh.none[1];
+        } else {
+            up = sh.res.up;
+            low = sh.res.low;
+        }
         total = sh.res.total;
         gap_open = sh.res.gap_open != 0;
         if (!first) {
