@@ -316,7 +316,6 @@ struct Shared {
     CandFull ccand[kMaxCluster];              // cluster leader: its CTAs' candidates
     CandFull xc[2][kMaxCluster];              // one cluster: every CTA's candidate, by epoch parity
     Side none[2];                             // empty I_up / I_low sides
-    int res_wu, res_wl;                       // one cluster: slots of the winning sides
     unsigned long long xbar[2];               // one cluster: mbarriers of the two parities
     ResultArea res;                           // exchange result pushed by the leader
     long long rcount[8];
@@ -1021,16 +1020,21 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
                 const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                 const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
+                // the winning sides into the result, one 8-byte word per lane
+                const Side *wsu = mu ? &sh.xc[par][__ffs(mu) - 1].up : &sh.none[0];
+                const Side *wsl = ml ? &sh.xc[par][__ffs(ml) - 1].low : &sh.none[1];
+                constexpr int kSideW = (int)(sizeof(Side) / 8);
+                static_assert(2 * kSideW <= 32, "a side is copied by one warp");
+                if (lane < 2 * kSideW) {
+                    const bool u = lane < kSideW;
+                    const int w = u ? lane : lane - kSideW;
+                    reinterpret_cast<unsigned long long *>(u ? &sh.res.up : &sh.res.low)[w] =
+                        reinterpret_cast<const unsigned long long *>(u ? wsu : wsl)[w];
+                }
                 if (lane == 0) {
-                    // the winners stay in their slots (rewritten two steps on)
-                    const int wu = mu ? __ffs(mu) - 1 : -1, wl = ml ? __ffs(ml) - 1 : -1;
-                    sh.res_wu = wu;
-                    sh.res_wl = wl;
                     sh.res.total = cc;
                     sh.res.flag = timed_out;
-                    const double fu = wu >= 0 ? sh.xc[par][wu].up.f : sh.none[0].f;
-                    const double fl = wl >= 0 ? sh.xc[par][wl].low.f : sh.none[1].f;
-                    sh.res.gap_open = dless(A.thr, fl - fu);
+                    sh.res.gap_open = dless(A.thr, wsl->f - wsu->f);
                 }
             }
             __syncthreads();
@@ -1144,14 +1148,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         prev_valid = first ? 0 : 1;
         prev_len_u = up.len;
         prev_len_l = low.len;
-        if constexpr (solo) {
-            const int wu = sh.res_wu, wl = sh.res_wl;
-            up = wu >= 0 ? sh.xc[par][wu].up : sh.none[0];
-            low = wl >= 0 ? sh.xc[par][wl].low : sh.none[1];
-        } else {
-            up = sh.res.up;
-            low = sh.res.low;
-        }
+        up = sh.res.up;
+        low = sh.res.low;
         total = sh.res.total;
         gap_open = sh.res.gap_open != 0;
         if (!first) {
