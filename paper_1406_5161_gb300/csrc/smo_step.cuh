@@ -829,8 +829,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     }
                     if (keep) {
                         const unsigned long long kup = key_up(fi), klo = key_low(fi);
-                        if (st_up(set) && ki_less(kup, i, bku, biu)) { bku = kup; biu = i; bru = r; }
-                        if (st_low(set) && ki_less(klo, i, bkl, bil)) { bkl = klo; bil = i; brl = r; }
+                        // a thread meets its rows in increasing index order:
+                        // a strict key test keeps the lowest index of a tie
+                        if (st_up(set) && kup < bku) { bku = kup; biu = i; bru = r; }
+                        if (st_low(set) && klo < bkl) { bkl = klo; bil = i; brl = r; }
                     }
                 }
             }
@@ -867,8 +869,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 }
                 if (keep) {
                     const unsigned long long kup = key_up(fi), klo = key_low(fi);
-                    if (st_up(set) && ki_less(kup, i, bku, biu)) { bku = kup; biu = i; bru = r; }
-                    if (st_low(set) && ki_less(klo, i, bkl, bil)) { bkl = klo; bil = i; brl = r; }
+                    // increasing index order per thread: strict key test
+                    if (st_up(set) && kup < bku) { bku = kup; biu = i; bru = r; }
+                    if (st_low(set) && klo < bkl) { bkl = klo; bil = i; brl = r; }
                 }
             }
         }
