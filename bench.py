@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--serve-cluster", type=int, default=0, help="CTAs per served job (0 = server default)")
     ap.add_argument("--serve-burst", action="store_true",
                     help="submit every job at time 0 (saturated server) instead of the Poisson times")
-    ap.add_argument("--workload", default="onehot", choices=["onehot", "batch", "serve"],
+    ap.add_argument("--workload", default="onehot", choices=["onehot", "batch", "serve", "recon"],
                     help="onehot: the benchmark line; batch: the one-vs-one x C x gamma grid "
                          "(405 jobs) batched vs one job at a time")
     ap.add_argument("--plain-sample", type=int, default=27,
@@ -435,6 +435,77 @@ def run_batch(args):
     return 0
 
 
+def run_recon(args):
+    """The reconstruction / decision contraction on the tensor cores at the
+    covtype shape (d = 54, 12 stored entries per row): out[q] = sum_k
+    alpha_k y_k K(x_k, z_q) - b over 100,000 support vectors and 100,000
+    query rows, mixed precision (BF16 values, FP32 accumulation and exp, FP64
+    sums across tiles). Every row is a support vector. The timed call is the
+    public svm_decision (SV compaction and BF16 densification included)."""
+    import numpy as np
+    import torch
+    import paper_1406_5161_gb300 as pkg
+    from paper_1406_5161_gb300 import synth
+
+    torch.cuda.set_device(0)
+    nsv = nq = 100_000
+    p = synth.covtype_like(n=nsv, n_test=nq, seed=3)
+    rng = np.random.default_rng(7)
+    alpha = rng.uniform(0.01, p.C, nsv)
+    Xd, Zd = pkg.to_device(p.X), pkg.to_device(p.Z)
+    yd = torch.as_tensor(p.y, device="cuda")
+    ad = torch.as_tensor(alpha, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def call():
+        return pkg.svm_decision(Xd, yd, ad, 0.25, p.gamma, Zd, precision=pkg.SVM_MIXED_BF16, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        call()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = pkg.svm_kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(stream)
+        out = call()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    launches = pkg.svm_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in ev)
+    d = p.X.d
+    flops = 2.0 * nsv * nq * d                      # algorithmic: the inner products
+    tflops = flops / (ms / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured bf16_tflops (burst cuBLAS)"
+    except (OSError, ValueError, KeyError):
+        peak, kind = 1900.0, "fallback"
+    # the epilogue evaluates one exp2 per pair on the SFU: 16 per clock per SM
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070.0
+    exp_peak = 16.0 * sms * mhz * 1e6
+    pairs_s = nsv * nq / (ms / 1e3)
+    line = {"metric": "RBF contraction TFLOP/s", "value": tflops, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"covtype-shaped contraction: {nsv} support vectors x {nq} queries, d={d}",
+                       "l2": "flushed between timed calls (256 MiB write)"},
+            "pairs_per_s": pairs_s, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "traffic": None, "kernel": "tc_rbf_kernel",
+                         "peak_source": kind,
+                         "note": "one exp2 per pair bounds the epilogue: SFU peak %.3g pairs/s, "
+                                 "achieved %.3f of it" % (exp_peak, pairs_s / exp_peak)},
+            "checksum": float(out.double().sum().item())}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """A Poisson stream (20 jobs/s) of training jobs of different n and d:
     served with continuous batching vs one svm_train at a time (FIFO)."""
@@ -509,6 +580,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "recon":
+        return run_recon(args)
     return run_gb300(args, rank, world, local)
 
 

@@ -12,7 +12,9 @@
 // FP32 accumulators in tensor memory); the four warps then read the
 // 128 x 128 FP32 tile from tensor memory (tcgen05.ld), apply the exp
 // epilogue and accumulate coef * K per query row (FP32 within a tile, FP64
-// across tiles). Padding rows carry coef = 0.
+// across tiles). Support tiles and accumulators are double-buffered, so the
+// load and MMA of the next tile overlap the epilogue. Padding rows carry
+// coef = 0.
 //
 // All waits on mbarriers are bounded; on expiry the CTA records an error,
 // waits (bounded) for its own asynchronous work, frees its tensor memory and
@@ -32,7 +34,7 @@ namespace {
 
 constexpr int kTile = 128;            // rows per query tile and per SV tile (M = N)
 constexpr int kKB = 64;               // BF16 elements per 128-byte swizzle row
-constexpr int kTcThreads = 128;       // 4 warps: one TMEM lane quadrant each
+constexpr int kTcThreads = 256;       // 8 warps: TMEM lane quadrant w % 4, column half w / 4
 constexpr int kMaxKBlocks = 4;        // d_pad <= 256
 constexpr uint32_t kTileBytes = kTile * kKB * 2;   // 16 KiB per k-block tile
 constexpr long long kWaitLimit = 1ll << 26;        // mbarrier polls before giving up
@@ -79,6 +81,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// bulk copy global -> shared counted on an mbarrier (16-byte aligned, size a
+// multiple of 16)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
 // of 128 bytes, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
@@ -114,6 +125,19 @@ struct TcArgs {
     int *err;
 };
 
+// 2^x on the special-function unit (flush to zero below 2^-126)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One CTA: a 128-row query tile against all support-vector tiles. Support
+// tiles are double-buffered in shared memory and their products in two
+// 128-column tensor-memory accumulators, so that the TMA load of tile t+1 and
+// the MMA of tile t run while the four warps evaluate the epilogue of tile
+// t-1.
 __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constant__ CUtensorMap mapZ,
                                                             const __grid_constant__ CUtensorMap mapX,
                                                             TcArgs a)
@@ -121,115 +145,156 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *tileA = dsm;                                   // [kblocks][16 KiB]
-    unsigned char *tileB = dsm + (size_t)a.kblocks * kTileBytes;  // [kblocks][16 KiB]
-    __shared__ __align__(8) uint64_t bar_load, bar_mma;
+    unsigned char *tileA = dsm;                                       // [kblocks][16 KiB]
+    unsigned char *tileB0 = dsm + (size_t)a.kblocks * kTileBytes;     // [2][kblocks][16 KiB]
+    __shared__ __align__(8) uint64_t bar_q, bar_load[2], bar_mma[2], bar_drain;
     __shared__ uint32_t tmem_base;
-    __shared__ float s_xc[kTile], s_coef[kTile];
+    __shared__ __align__(16) float s_xc[3][kTile], s_coef[3][kTile];   // per-SV constants of 3 tiles
+    __shared__ double s_acc[kTile];   // the second column half's row sums
     __shared__ int s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t q0 = (int64_t)blockIdx.x * kTile;
     if (tid == 0) {
-        mbar_init(&bar_load, 1);
-        mbar_init(&bar_mma, 1);
+        mbar_init(&bar_q, 1);
+        mbar_init(&bar_load[0], 1);
+        mbar_init(&bar_load[1], 1);
+        mbar_init(&bar_mma[0], 1);
+        mbar_init(&bar_mma[1], 1);
+        mbar_init(&bar_drain, 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_base)), "r"(kTile) : "memory");
+                     ::"r"(smem_u32(&tmem_base)), "r"(2 * kTile) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
+    const int64_t ntiles = (a.nsv + kTile - 1) / kTile;
 
-    // query tile (all k-blocks) stays in shared memory
-    uint32_t ph_load = 0, ph_mma = 0;
+    // support tile t: rows into buffer t & 1 (TMA), per-SV constants into
+    // slot t % 3 (bulk copies), issued by one thread
+    unsigned pending = 0;   // bit b: a load into buffer b not yet waited for
+    auto load_tile = [&](int64_t t) {
+        const int b = (int)(t & 1), cs = (int)(t % 3);
+        if (tid == 0) {
+            unsigned char *tb = tileB0 + (size_t)b * a.kblocks * kTileBytes;
+            // the buffer's last readers (generic proxy) passed a barrier before this
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar_load[b], (uint32_t)a.kblocks * kTileBytes + 2 * kTile * 4);
+            for (int kb = 0; kb < a.kblocks; ++kb)
+                tma_load_2d(tb + (size_t)kb * kTileBytes, &mapX, kb * kKB, (int)(t * kTile), &bar_load[b]);
+            bulk_load(s_xc[cs], a.xc + t * kTile, kTile * 4, &bar_load[b]);
+            bulk_load(s_coef[cs], a.coef + t * kTile, kTile * 4, &bar_load[b]);
+        }
+        pending |= 1u << b;
+    };
+    // the query tile (all k-blocks) stays in shared memory
     if (tid == 0) {
-        mbar_expect_tx(&bar_load, (uint32_t)a.kblocks * kTileBytes);
+        mbar_expect_tx(&bar_q, (uint32_t)a.kblocks * kTileBytes);
         for (int kb = 0; kb < a.kblocks; ++kb)
-            tma_load_2d(tileA + (size_t)kb * kTileBytes, &mapZ, kb * kKB, (int)q0, &bar_load);
+            tma_load_2d(tileA + (size_t)kb * kTileBytes, &mapZ, kb * kKB, (int)q0, &bar_q);
     }
-    bool ok = __syncthreads_and(mbar_wait(&bar_load, ph_load)) != 0;   // uniform decision
-    ph_load ^= 1;
+    bool q_pending = true;
+    load_tile(0);
+    if (ntiles > 1) load_tile(1);
+    bool ok = __syncthreads_and(mbar_wait(&bar_q, 0)) != 0;   // uniform decision
+    if (ok) q_pending = false;
 
-    const int my_row = warp * 32 + lane;                 // TMEM lane = query row in tile
+    const int quad = warp & 3, half = warp >> 2;
+    const int my_row = quad * 32 + lane;                 // TMEM lane = query row in tile
     const int64_t q = q0 + my_row;
     const float zc = (q < a.nq) ? a.zc[q] : 0.f;
     double acc = 0.0;
-    const int64_t ntiles = (a.nsv + kTile - 1) / kTile;
-    for (int64_t t = 0; t < ntiles && ok; ++t) {
-        // stage the per-SV constants of this tile; load the SV tile
-        for (int j = tid; j < kTile; j += kTcThreads) {
-            s_xc[j] = a.xc[t * kTile + j];
-            s_coef[j] = a.coef[t * kTile + j];
-        }
-        if (tid == 0) {
-            mbar_expect_tx(&bar_load, (uint32_t)a.kblocks * kTileBytes);
-            for (int kb = 0; kb < a.kblocks; ++kb)
-                tma_load_2d(tileB + (size_t)kb * kTileBytes, &mapX, kb * kKB, (int)(t * kTile), &bar_load);
-        }
-        ok = __syncthreads_and(mbar_wait(&bar_load, ph_load)) != 0;   // also publishes s_xc / s_coef
-        ph_load ^= 1;
-        if (!ok) break;
-        // one thread issues the MMAs: D = Z_tile * X_tile^T over all K
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int kb = 0; kb < a.kblocks; ++kb) {
-                const uint32_t sa = smem_u32(tileA + (size_t)kb * kTileBytes);
-                const uint32_t sb = smem_u32(tileB + (size_t)kb * kTileBytes);
+    uint32_t ph_load = 0, ph_mma = 0;   // bit b: parity of the next phase of buffer b
+    for (int64_t t = 0; t <= ntiles && ok; ++t) {
+        if (t < ntiles) {
+            // MMA of tile t: D[b] = Z_tile * X_tile^T over all K
+            const int b = (int)(t & 1);
+            ok = __syncthreads_and(mbar_wait(&bar_load[b], (ph_load >> b) & 1u)) != 0;
+            if (!ok) break;
+            ph_load ^= 1u << b;
+            pending &= ~(1u << b);
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned char *tb = tileB0 + (size_t)b * a.kblocks * kTileBytes;
+                const uint32_t dcol = tmem + (uint32_t)(b * kTile);
+                for (int kb = 0; kb < a.kblocks; ++kb) {
+                    const uint32_t sa = smem_u32(tileA + (size_t)kb * kTileBytes);
+                    const uint32_t sb = smem_u32(tb + (size_t)kb * kTileBytes);
 #pragma unroll
-                for (int ks = 0; ks < kKB / 16; ++ks) {
-                    const uint64_t da = smem_desc_sw128(sa + ks * 32);
-                    const uint64_t db = smem_desc_sw128(sb + ks * 32);
-                    const uint32_t accum = (kb | ks) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\t"
-                        "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                        ::"r"(tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
-                        : "memory");
+                    for (int ks = 0; ks < kKB / 16; ++ks) {
+                        const uint64_t da = smem_desc_sw128(sa + ks * 32);
+                        const uint64_t db = smem_desc_sw128(sb + ks * 32);
+                        const uint32_t accum = (kb | ks) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\t"
+                            "setp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                            ::"r"(dcol), "l"(da), "l"(db), "r"(kIdesc), "r"(accum)
+                            : "memory");
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&bar_mma[b])) : "memory");
+            }
+        }
+        if (t >= 1) {
+            // epilogue of tile t-1 while the MMA of tile t runs
+            const int pb = (int)((t - 1) & 1), pc = (int)((t - 1) % 3);
+            ok = __syncthreads_and(mbar_wait(&bar_mma[pb], (ph_mma >> pb) & 1u)) != 0;
+            if (!ok) break;
+            ph_mma ^= 1u << pb;
+            // the MMA of tile t-1 is done with buffer pb: load tile t+1 into
+            // it now, a whole epilogue ahead of its use (its constants go to
+            // slot (t+1) % 3, last read by the epilogue of tile t-2)
+            if (t + 1 < ntiles) load_tile(t + 1);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float part0 = 0.f, part1 = 0.f;
+#pragma unroll 1
+            for (int c0 = half * (kTile / 2); c0 < (half + 1) * (kTile / 2); c0 += 32) {
+                uint32_t r[32];
+                const uint32_t addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(pb * kTile + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(addr)
+                    : "memory");
+                // the tile's constants for these 32 columns, as vectors
+                float xc[32], cf[32];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const float4 x4 = reinterpret_cast<const float4 *>(&s_xc[pc][c0])[v];
+                    const float4 c4 = reinterpret_cast<const float4 *>(&s_coef[pc][c0])[v];
+                    xc[4 * v] = x4.x; xc[4 * v + 1] = x4.y; xc[4 * v + 2] = x4.z; xc[4 * v + 3] = x4.w;
+                    cf[4 * v] = c4.x; cf[4 * v + 1] = c4.y; cf[4 * v + 2] = c4.z; cf[4 * v + 3] = c4.w;
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                    // log2 K = -gamma log2(e) (||z||^2 + ||x||^2 - 2 <z, x>), clamped at 0
+                    const float e0 = fminf(fmaf(__uint_as_float(r[j]), a.g2, zc + xc[j]), 0.f);
+                    const float e1 = fminf(fmaf(__uint_as_float(r[j + 1]), a.g2, zc + xc[j + 1]), 0.f);
+                    part0 = fmaf(cf[j], ex2_approx(e0), part0);
+                    part1 = fmaf(cf[j + 1], ex2_approx(e1), part1);
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&bar_mma)) : "memory");
+            acc += (double)(part0 + part1);
+            // accumulator pb is rewritten by the MMA of tile t+1 only after
+            // the next iteration's barrier
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
-        ok = __syncthreads_and(mbar_wait(&bar_mma, ph_mma)) != 0;
-        ph_mma ^= 1;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: this thread's row, 32 columns at a time
-        float part = 0.f;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kTile; c0 += 32) {
-            uint32_t r[32];
-            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                  "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                  "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                  "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(addr)
-                : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                // log2 K = -gamma log2(e) (||z||^2 + ||x||^2 - 2 <z, x>), clamped at 0
-                const float e = fminf(fmaf(__uint_as_float(r[j]), a.g2, zc + s_xc[c0 + j]), 0.f);
-                part = fmaf(s_coef[c0 + j], exp2f(e), part);
-            }
-        }
-        acc += (double)part;
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();   // tile B and tensor memory free for the next tile
     }
     if (!ok && tid == 0) {
         s_fail = 1;
@@ -237,22 +302,32 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
     }
     __syncthreads();
     if (s_fail) {
-        // let any outstanding MMA of this CTA finish before freeing its memory
+        // let this CTA's outstanding asynchronous work finish (bounded)
+        // before its shared and tensor memory are released
+        // (a commit tracks every earlier MMA of the issuing thread)
         if (tid == 0) {
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&bar_mma)) : "memory");
+                         ::"r"(smem_u32(&bar_drain)) : "memory");
         }
-        (void)mbar_wait(&bar_mma, ph_mma);
-    } else if (q < a.nq) {
-        const int32_t row = a.qrow[q];
-        double v = acc + a.add_scalar;
-        if (a.yq) v -= (double)a.yq[row];
-        a.out[row] = v;
+        for (int b = 0; b < 2; ++b)
+            if ((pending >> b) & 1u) (void)mbar_wait(&bar_load[b], (ph_load >> b) & 1u);
+        if (q_pending) (void)mbar_wait(&bar_q, 0);
+        (void)mbar_wait(&bar_drain, 0);
+    } else {
+        // the two column halves of a row meet in shared memory (fixed order)
+        if (half == 1) s_acc[my_row] = acc;
+        __syncthreads();
+        if (half == 0 && q < a.nq) {
+            const int32_t row = a.qrow[q];
+            double v = (acc + s_acc[my_row]) + a.add_scalar;
+            if (a.yq) v -= (double)a.yq[row];
+            a.out[row] = v;
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTile)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile)
                      : "memory");
     }
 }
@@ -386,9 +461,10 @@ cudaError_t launch_rbf_contract_tc(const RbfContract &c, void *ws, int *err_host
     a.add_scalar = c.add_scalar;
     a.out = c.out;
     a.err = err;
-    // at least 52 KiB so that at most 4 CTAs share an SM: their 4 x 128
-    // tensor-memory columns then fit the SM's 512 without waiting
-    const size_t smem = std::max<size_t>(2 * (size_t)kblocks * kTileBytes + 1024, 52 * 1024);
+    // query tile + two support tiles; at least 80 KiB so that at most 2 CTAs
+    // share an SM: their 2 x 256 tensor-memory columns then fit the SM's 512
+    // without waiting
+    const size_t smem = std::max<size_t>(3 * (size_t)kblocks * kTileBytes + 1024, 80 * 1024);
     e = cudaFuncSetAttribute(tc_rbf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (c.nsv > 0) {
