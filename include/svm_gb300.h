@@ -120,7 +120,10 @@ typedef struct svm_params {
     int32_t lanes_per_row;   /* lanes sharing one row in the row pass (rounded up to
                                 a power of two <= 32); 0 = from the mean row length;
                                 bit-mask rows always use one lane */
-    int32_t reserved;
+    int32_t cache_mb;        /* kernel-row cache in device memory (MiB) for inputs that
+                                are not binary: 0 = automatic (FP64 precision only; up
+                                to half the free memory, at most 32 GiB), < 0 = off,
+                                > 0 = this budget (FP64 and mixed precision) */
 } svm_params;
 
 /* Keep every row segment in global memory even when it would fit in the
@@ -176,7 +179,9 @@ typedef struct svm_stats {
     double cta_busy_ms_min;  /* with SVM_FLAG_PHASE_TIMES: least and most time a */
     double cta_busy_ms_max;  /* CTA spent from step start to publishing its candidate */
     int32_t bit_rows;        /* 1 when the row pass read binary rows as bit masks */
-    int32_t reserved;
+    int32_t cache_slots;     /* kernel rows the cache holds (0: no cache) */
+    int64_t cache_hits;      /* steps x sides whose kernel row came from the cache */
+    int64_t cache_misses;    /* ... that were computed (and stored) */
 } svm_stats;
 
 /*

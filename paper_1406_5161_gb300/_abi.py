@@ -43,7 +43,7 @@ class svm_params(ct.Structure):
                 ("max_iter", ct.c_int64), ("precision", ct.c_int32), ("tie_break", ct.c_int32),
                 ("stream", ct.c_void_p), ("trace", ct.c_void_p), ("trace_len", ct.c_int64),
                 ("flags", ct.c_int32), ("ctas", ct.c_int32),
-                ("lanes_per_row", ct.c_int32), ("reserved", ct.c_int32)]
+                ("lanes_per_row", ct.c_int32), ("cache_mb", ct.c_int32)]
 
 
 class svm_shrink_policy(ct.Structure):
@@ -61,7 +61,8 @@ class svm_stats(ct.Structure):
                 ("resident", ct.c_int32), ("ctas", ct.c_int32), ("lanes_per_row", ct.c_int32),
                 ("cluster_size", ct.c_int32), ("phase_ms", ct.c_double * 8),
                 ("cta_busy_ms_min", ct.c_double), ("cta_busy_ms_max", ct.c_double),
-                ("bit_rows", ct.c_int32), ("reserved", ct.c_int32)]
+                ("bit_rows", ct.c_int32), ("cache_slots", ct.c_int32),
+                ("cache_hits", ct.c_int64), ("cache_misses", ct.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
@@ -188,8 +189,9 @@ def _stream_ptr(stream):
 def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int = 0,
               precision: int = SVM_FP64, shrink: tuple | None = None, stream=None,
               trace_len: int = 0, alpha_out=None, flags: int = 0, ctas: int = 0,
-              lanes_per_row: int = 0, check: bool = True) -> dict:
+              lanes_per_row: int = 0, cache_mb: int = 0, check: bool = True) -> dict:
     """Train by SMO. ``shrink`` = (kind, value, recon[, first_factor]) or None.
+    ``cache_mb``: kernel-row cache budget in MiB (0 automatic, < 0 off).
     X is a host CSR (numpy arrays) or a DeviceCSR; y matches X's memory space.
     Returns dict(status, alpha, b, iters, stats, trace)."""
     lib = load()
@@ -210,7 +212,7 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
     trace = np.full((max(trace_len, 0), 2), -1, dtype=np.int32)
     p = svm_params(float(C), float(gamma), float(tau), int(max_iter), int(precision), 0,
                    _stream_ptr(stream), trace.ctypes.data if trace_len else None, int(trace_len),
-                   int(flags), int(ctas), int(lanes_per_row), 0)
+                   int(flags), int(ctas), int(lanes_per_row), int(cache_mb))
     pol = None
     if shrink is not None:
         kind, value, recon = shrink[:3]

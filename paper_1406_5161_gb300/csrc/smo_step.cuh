@@ -31,6 +31,7 @@
 
 #include <climits>
 #include <cstddef>
+#include <type_traits>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -316,6 +317,7 @@ struct Shared {
     CandFull ccand[kMaxCluster];              // cluster leader: its CTAs' candidates
     CandFull xc[2][kMaxCluster];              // one cluster: every CTA's candidate, by epoch parity
     Side none[2];                             // empty I_up / I_low sides
+    int kc_su, kc_sl, kc_hu, kc_hl;           // kernel-row cache: slots of x_up / x_low, hits
     unsigned long long xbar[2];               // one cluster: mbarriers of the two parities
     ResultArea res;                           // exchange result pushed by the leader
     long long rcount[8];
@@ -358,8 +360,15 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     const int cid = cta / csize;                   // cluster index = leader slot
     const int nlead = G / csize;
     const int d = A.d;
+    // kernel-row cache: K(x_up, .) and K(x_low, .) of recent steps, per CTA
+    // segment, in device memory (FP64 and mixed modes)
+    constexpr bool KC_MODE = MODE == MODE_FP64 || MODE == MODE_MIXED;
+    using KT = typename std::conditional<MODE == MODE_FP64, double, float>::type;
+    const bool kc_on = KC_MODE && A.kc != nullptr;
     const SmoLayout L = smo_layout(MODE, d, A.ktab_len, A.maxnnz, RES ? 1 : 0, A.seg_rows_max,
-                                   A.seg_nnz_max);
+                                   A.seg_nnz_max,
+                                   kc_on ? smo_kdir_bytes(A.n, A.kc_slots, A.kc_direct) : 0);
+    uint32_t *kdir = reinterpret_cast<uint32_t *>(dsm + L.kdir);
     Tgt *tbuf = reinterpret_cast<Tgt *>(dsm + L.tgt);            // [2][d]
     int *tcol = reinterpret_cast<int *>(dsm + L.tcol);           // [2 buf][2 side][maxnnz]
     double *ktab = reinterpret_cast<double *>(dsm + L.ktab);
@@ -412,6 +421,18 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         }
         for (int k = tid; k < cnt; k += kThreads) act_s[k] = A.act[lo + k];
     }
+    if (kc_on) {
+        // empty directory: no valid rows (direct), no tags and zero stamps (4-way sets)
+        if (A.kc_direct) {
+            for (int w = tid; w < (int)((A.n + 31) / 32); w += kThreads) kdir[w] = 0;
+        } else {
+            for (int w = tid; w < A.kc_slots; w += kThreads) {
+                kdir[w] = 0xffffffffu;
+                kdir[A.kc_slots + w] = 0;
+            }
+        }
+    }
+    int64_t kc_hits = 0, kc_misses = 0;
     SmoCtrl C0 = *A.ctrl;
     int64_t iter = C0.iter, counter = C0.counter, row_visits = C0.row_visits;
     int64_t shrink_events = C0.shrink_events;
@@ -552,6 +573,44 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         if (!first) {
             if (!gap_open) { exit_reason = 0; break; }
             if (iter >= A.iter_limit) { exit_reason = 1; break; }
+            // ---- 0. kernel-row cache: this step's rows of x_up and x_low
+            //         (the same decisions in every CTA; a row found here was
+            //         stored by this CTA in an earlier step of this launch)
+            if (kc_on && tid == 0) {
+                auto lookup = [&](int i, int &slot, int &hit) {
+                    if (A.kc_direct) {
+                        const uint32_t bit = 1u << (i & 31);
+                        hit = (kdir[i >> 5] & bit) != 0;
+                        kdir[i >> 5] |= bit;
+                        slot = i;
+                    } else {
+                        const int nsets = A.kc_slots >> 2;
+                        const int set = i % nsets;
+                        uint32_t *tags = kdir + 4 * set, *stamps = kdir + A.kc_slots + 4 * set;
+                        int way = -1;
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            if (tags[w] == (uint32_t)i) way = w;
+                        hit = way >= 0;
+                        if (!hit) {   // least recently used way
+                            way = 0;
+#pragma unroll
+                            for (int w = 1; w < 4; ++w)
+                                if (stamps[w] < stamps[way]) way = w;
+                            tags[way] = (uint32_t)i;
+                        }
+                        stamps[way] = (uint32_t)(iter + 1);
+                        slot = 4 * set + way;
+                    }
+                };
+                int su_, hu_, sl_, hl_;
+                lookup(up.i, su_, hu_);
+                lookup(low.i, sl_, hl_);
+                sh.kc_su = su_; sh.kc_hu = hu_;
+                sh.kc_sl = sl_; sh.kc_hl = hl_;
+                kc_hits += hu_ + hl_;
+                kc_misses += 2 - hu_ - hl_;
+            }
             // ---- 1. targets: x_up into .x / byte 0, x_low into .y / byte 1
             //         (bit-mask modes: the masks came with the exchange)
             if constexpr (!BITS) for (int k = tid; k < up.len; k += kThreads) {
@@ -713,6 +772,12 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             constexpr int kRowWarps = kWarps - 1;
             const int gl = lane & (LPR - 1);
             const int gw = lane / LPR;
+            // kernel-row cache rows of this step (both found: no row sums)
+            const bool kc_step = kc_on && !first;
+            const bool kc_hu = kc_step && sh.kc_hu, kc_hl = kc_step && sh.kc_hl;
+            KT *kc_ru = kc_step ? static_cast<KT *>(A.kc) + (size_t)sh.kc_su * A.kc_ld : nullptr;
+            KT *kc_rl = kc_step ? static_cast<KT *>(A.kc) + (size_t)sh.kc_sl * A.kc_ld : nullptr;
+            const bool skip_sums = kc_hu && kc_hl;
             double du = 0.0, dl = 0.0, au_new = 0.0, al_new = 0.0;
             unsigned char st_u = 0, st_l = 0;
             bool have_step = first;
@@ -747,7 +812,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                   __popc(v.z ^ low.m[4 * q + 2]) + __popc(v.w ^ low.m[4 * q + 3]);
                         }
                     }
-                } else if (!first) {
+                } else if (!first && !skip_sums) {
                     for (int64_t p = p0 + gl; p < p1; p += LPR) {
                         const int c = COL(p);
                         if constexpr (MODE == MODE_BINARY) {
@@ -782,18 +847,32 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         int du2 = up.len + len - 2 * su, dl2 = low.len + len - 2 * sl;
                         ku = ktab[du2 < 0 ? 0 : du2];
                         kl = ktab[dl2 < 0 ? 0 : dl2];
-                    } else if constexpr (MODE == MODE_FP64) {
-                        const double nrm_i = NRM(r);
-                        double d2u = up.nrm + nrm_i - 2.0 * su;
-                        double d2l = low.nrm + nrm_i - 2.0 * sl;
-                        ku = exp(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
-                        kl = exp(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
                     } else {
-                        const float nf = (float)NRM(r);
-                        float d2u = (float)up.nrm + nf - 2.0f * su;
-                        float d2l = (float)low.nrm + nf - 2.0f * sl;
-                        ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
-                        kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
+                        const int64_t gi = lo + r;
+                        if (kc_hu) {
+                            ku = (double)kc_ru[gi];
+                        } else {
+                            if constexpr (MODE == MODE_FP64) {
+                                const double d2u = up.nrm + NRM(r) - 2.0 * su;
+                                ku = exp(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
+                            } else {
+                                const float d2u = (float)up.nrm + (float)NRM(r) - 2.0f * su;
+                                ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
+                            }
+                            if (kc_step) kc_ru[gi] = (KT)ku;
+                        }
+                        if (kc_hl) {
+                            kl = (double)kc_rl[gi];
+                        } else {
+                            if constexpr (MODE == MODE_FP64) {
+                                const double d2l = low.nrm + NRM(r) - 2.0 * sl;
+                                kl = exp(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
+                            } else {
+                                const float d2l = (float)low.nrm + (float)NRM(r) - 2.0f * sl;
+                                kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
+                            }
+                            if (kc_step) kc_rl[gi] = (KT)kl;
+                        }
                     }
                 }
                 if (!have_step) {
@@ -1198,6 +1277,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         c->exit_reason = exit_reason;
         c->shrink_events = shrink_events;
         for (int k = 0; k < 8; ++k) c->phase_cycles[k] += ph[k];
+        c->kc_hits += kc_hits;
+        c->kc_misses += kc_misses;
     }
 }
 

@@ -548,19 +548,49 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     if (G > 256) G = 256;
     const int kt = mode == MODE_BINARY ? ktab_len : 0;
     const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
+    // kernel-row cache (FP64 and mixed inputs): every slot holds one kernel
+    // row over all n samples; all n rows when they fit (direct), else up to
+    // 8192 rows in 4-way sets; the directory goes into each CTA's shared
+    // memory, so its size is part of the layout
+    int kc_slots = 0, kc_direct = 0;
+    int64_t kc_ld = 0;
+    size_t kdir = 0;
+    // automatic for FP64 rows (their exp costs ~20 FP64 instructions per
+    // value); the mixed mode's FP32 exp is cheaper than the cache traffic, so
+    // there the cache is used only when a budget is given
+    if ((kmode == MODE_FP64 && P->cache_mb >= 0) || (kmode == MODE_MIXED && P->cache_mb > 0)) {
+        const size_t esz = kmode == MODE_FP64 ? 8 : 4;
+        kc_ld = (n + 31) / 32 * 32;
+        size_t budget = (size_t)P->cache_mb << 20;
+        if (P->cache_mb == 0) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+            budget = std::min<size_t>(fr / 2, (size_t)32 << 30);
+        }
+        const size_t row_bytes = (size_t)kc_ld * esz;
+        if ((size_t)n * row_bytes <= budget && smo_kdir_bytes(n, 0, 1) <= lim_dyn / 4) {
+            kc_slots = (int)n;
+            kc_direct = 1;
+        } else {
+            int64_t sl = std::min<int64_t>((int64_t)(budget / row_bytes), 8192);
+            while (sl >= 64 && smo_kdir_bytes(n, (int)sl, 0) > lim_dyn / 2) sl /= 2;
+            kc_slots = sl >= 64 ? (int)(sl / 4 * 4) : 0;
+        }
+        if (kc_slots > 0) kdir = smo_kdir_bytes(n, kc_slots, kc_direct);
+    }
     // thread-block clusters for the hierarchical exchange: one cluster of 16
     // when its segments stay in shared memory (no global exchange at all),
     // else clusters of 8 with a leader exchange through global memory
     int cs = 1;
     {
-        const SmoLayout L0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0);
+        const SmoLayout L0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0, kdir);
         const bool clusters_ok = (P->flags & SVM_FLAG_NO_CLUSTERS) == 0 && L0.total <= lim_dyn;
         bool single = false;
         if (clusters_ok && (P->ctas == 0 || P->ctas == 16) && n >= 16 * 32 &&
             (P->flags & SVM_FLAG_STREAM_ROWS) == 0) {
             const int rows16 = (int)((n + 15) / 16);
             const int64_t nnz16 = (int64_t)(1.25 * (double)D.nnz / 16.0) + D.maxnnz;   // segment estimate
-            const SmoLayout L16 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, rows16, nnz16);
+            const SmoLayout L16 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, rows16, nnz16, kdir);
             if (L16.total <= lim_dyn && smo_max_clusters(kmode, lpr, 2, L16.total, 16) >= 1 &&
                 (P->ctas == 16 || n <= 200000)) {
                 single = true;
@@ -592,8 +622,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         seg_nnz_max = 0;
         for (int64_t v : segnnz) seg_nnz_max = std::max(seg_nnz_max, v);
         seg_rows_max = (int)((n + G - 1) / G);
-        Ls = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max, seg_nnz_max);
-        Lr = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max, seg_nnz_max);
+        Ls = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max, seg_nnz_max, kdir);
+        Lr = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max, seg_nnz_max, kdir);
         resident = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 && seg_nnz_max < ((int64_t)1 << 31) &&
                    Lr.total <= lim_dyn;
         if (resident && cs > 1 && smo_max_clusters(kmode, lpr, G == cs ? 2 : 1, Lr.total, cs) * cs < G) resident = 0;
@@ -601,7 +631,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         // the single cluster was chosen for on-chip segments that do not
         // fit after all: clusters of 8 over the whole GPU instead
         cs = 8;
-        const size_t s0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0).total;
+        const size_t s0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0, kdir).total;
         G = 8 * std::max(1, std::min(smo_max_clusters(kmode, lpr, 0, s0, 8), std::min(sms, 256) / 8));
     }
     const size_t smem = resident ? Lr.total : Ls.total;
@@ -681,6 +711,12 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.C = P->C;
     A.gamma = P->gamma;
     A.phase_times = (P->flags & SVM_FLAG_PHASE_TIMES) != 0;
+    if (kc_slots > 0) {
+        A.kc = ar.alloc<unsigned char>((size_t)kc_slots * (size_t)kc_ld * (kmode == MODE_FP64 ? 8 : 4));
+        A.kc_ld = kc_ld;
+        A.kc_slots = kc_slots;
+        A.kc_direct = kc_direct;
+    }
     int64_t *cta_cycles = nullptr;
     if (A.phase_times) {
         cta_cycles = ar.alloc<int64_t>(G);
@@ -852,7 +888,9 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         stats->cluster_size = cs;
         stats->lanes_per_row = lpr;
         stats->bit_rows = mode_bits(kmode) ? 1 : 0;
-        stats->reserved = 0;
+        stats->cache_slots = kc_slots;
+        stats->cache_hits = hc.kc_hits;
+        stats->cache_misses = hc.kc_misses;
         int dev = 0, khz = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);

@@ -45,6 +45,7 @@ struct SmoCtrl {
     // 0 target rows, 1 pair step (FP64 part), 2 row pass + CTA reduction,
     // 3 publish, 4 grid exchange, 5 other, 6 pair step (K(up,low) part)
     int64_t phase_cycles[8];
+    int64_t kc_hits, kc_misses;   // kernel-row cache lookups (CTA 0)
 };
 
 // Kernel arguments. Sample indices in the active lists are local to their
@@ -86,6 +87,14 @@ struct SmoArgs {
     int32_t phase_times;       // record per-phase cycle counts (CTA 0)
     int64_t *cta_cycles;       // with phase_times: per-CTA cycles of work per launch (G)
     int64_t timeout_ns;
+    // kernel-row cache (FP64 / mixed modes): kc_slots rows of kc_ld values
+    // (double / float); each CTA stores and reads only its own segment's part
+    // of a row; the directory lives in each CTA's shared memory (kc_direct:
+    // slot = sample index, one valid bit per sample; else 4-way sets)
+    void *kc;
+    int64_t kc_ld;
+    int32_t kc_slots;
+    int32_t kc_direct;
 };
 
 // ---- batched and served solves: one job = one two-class problem
@@ -145,13 +154,13 @@ cudaError_t launch_smo_batch(int mode, int lpr, int dense, const BatchArgs &a, s
 
 // Dynamic shared-memory layout of the step kernel (byte offsets).
 struct SmoLayout {
-    size_t tgt, tcol, ktab, f, alpha, nrm, rowptr, act, st, col, val, bits, dist, total;
+    size_t tgt, tcol, ktab, f, alpha, nrm, rowptr, act, st, col, val, bits, dist, kdir, total;
 };
 
 __host__ __device__ inline size_t smo_align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 __host__ __device__ inline SmoLayout smo_layout(int mode, int d, int ktab_len, int maxnnz,
-                                                int resident, int rows, int64_t nnz)
+                                                int resident, int rows, int64_t nnz, size_t kdir_bytes = 0)
 {
     SmoLayout L;
     const bool bits = mode_bits(mode);
@@ -172,6 +181,7 @@ __host__ __device__ inline SmoLayout smo_layout(int mode, int d, int ktab_len, i
     L.val = o;    o = smo_align16(o + (size_t)nnz * (mode == 0 ? 0 : 4));
     L.bits = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 * mode_words(mode) : 0));
     L.dist = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 : 0));   // two 16-bit distances per row
+    L.kdir = o;   o = smo_align16(o + kdir_bytes);                     // kernel-row cache directory
     L.total = o;
     return L;
 }
@@ -191,6 +201,11 @@ cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t sm
 // one cluster (the kernel that launch_smo_persistent picks when G == cs)
 int smo_max_clusters(int mode, int lpr, int resident, size_t smem, int cs);
 size_t smo_cand_bytes();   // bytes of one global candidate slot
+// shared-memory bytes of a kernel-row cache directory
+__host__ __device__ inline size_t smo_kdir_bytes(int64_t n, int slots, int direct)
+{
+    return direct ? (size_t)((n + 31) / 32) * 4 : (size_t)slots * 8;
+}
 // global exchange flags: one per leader and epoch parity, kSeqStride words
 // apart (a 128-byte line each); the array holds smo_seq_words(G) words
 constexpr int kSeqStride = 32;

@@ -285,3 +285,51 @@ def test_shrinking_dense_fp64_matches_plain_optimum():
         kind, value, recon = pkg.POLICIES[name]
         r, _, _ = gpu_train(p, shrink=(kind, value, recon))
         check_end_state(p, r, plain)
+
+
+# ---------------------------------------------------------------- kernel-row cache
+def _cache_pair(p, **kw):
+    Xd = pkg.to_device(p.X)
+    yd = torch.as_tensor(p.y, device="cuda")
+    on = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, trace_len=2000, **kw)
+    off = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, trace_len=2000, cache_mb=-1,
+                        **{k: v for k, v in kw.items() if k != "cache_mb"})
+    return on, off
+
+
+def _same(on, off):
+    assert on["iters"] == off["iters"]
+    assert np.array_equal(on["trace"], off["trace"])
+    assert np.array_equal(on["alpha"].cpu().numpy(), off["alpha"].cpu().numpy())
+    assert on["b"] == off["b"]
+    assert off["stats"]["cache_slots"] == 0
+
+
+@pytest.mark.parametrize("flags", [0, pkg.SVM_FLAG_STREAM_ROWS], ids=["resident", "streamed"])
+def test_kernel_row_cache_direct_is_exact(c1, flags):
+    """All n rows cached (direct slots): the solve is bit-for-bit the one
+    that recomputes every kernel row, and most rows come from the cache."""
+    p, ref = c1
+    on, off = _cache_pair(p, flags=flags)
+    assert on["stats"]["cache_slots"] == p.X.n
+    _same(on, off)
+    s = on["stats"]
+    assert s["cache_hits"] + s["cache_misses"] == 2 * on["iters"]
+    assert s["cache_hits"] > s["cache_misses"]
+    check_end_state(p, on, ref)
+
+
+@pytest.mark.parametrize("precision", [pkg.SVM_FP64, pkg.SVM_MIXED_BF16_SIMT], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("shrink", [None, "Multi5pc"])
+def test_kernel_row_cache_with_evictions_is_exact(precision, shrink):
+    """A cache far smaller than n rows (4-way sets, least recently used way
+    evicted), with and without shrinking, FP64 and mixed rows: identical to
+    the solve without a cache."""
+    p = synth.covtype_like(n=12000, n_test=0, seed=17)
+    pol = pkg.POLICIES[shrink] if shrink else None
+    on, off = _cache_pair(p, precision=precision, shrink=pol, cache_mb=8)
+    s = on["stats"]
+    assert 64 <= s["cache_slots"] < p.X.n
+    assert s["cache_misses"] > s["cache_slots"]          # rows were evicted and recomputed
+    assert s["cache_hits"] > 0
+    _same(on, off)
