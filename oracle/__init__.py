@@ -92,6 +92,8 @@ def _bind(path: str):
     lib.or_kkt.argtypes = [P, P, P, ct.c_double, ct.c_double, P, P]
     lib.or_decision.restype = None
     lib.or_decision.argtypes = [P, P, P, ct.c_double, ct.c_double, P, P]
+    lib.or_set_kernel.restype = None
+    lib.or_set_kernel.argtypes = [ct.c_int, ct.c_double, ct.c_int]
     lib.or_set_threads.restype = None
     lib.or_set_threads.argtypes = [ct.c_int]
     lib.or_max_threads.restype = ct.c_int
@@ -136,6 +138,32 @@ class _Keep:
 
 def _ptr(a):
     return None if a is None else a.ctypes.data
+
+
+KERNEL_RBF, KERNEL_LINEAR, KERNEL_POLY, KERNEL_SIGMOID = 0, 1, 2, 3
+
+
+def set_kernel(kind: int = KERNEL_RBF, coef0: float = 0.0, degree: int = 3, lib=None) -> None:
+    """Select the kernel of later calls: RBF exp(-gamma ||x-z||^2) (default),
+    linear <x,z>, polynomial (gamma <x,z> + coef0)^degree, sigmoid
+    tanh(gamma <x,z> + coef0)."""
+    (lib or _load()).or_set_kernel(int(kind), float(coef0), int(degree))
+
+
+class kernel_spec:
+    """Context manager: the oracle uses the given kernel inside the block."""
+
+    def __init__(self, kind: int, coef0: float = 0.0, degree: int = 3, lib=None):
+        self.args = (kind, coef0, degree)
+        self.lib = lib
+
+    def __enter__(self):
+        set_kernel(*self.args, lib=self.lib)
+        return self
+
+    def __exit__(self, *exc):
+        set_kernel(KERNEL_RBF, lib=self.lib)
+        return False
 
 
 def set_threads(t: int, lib=None) -> None:

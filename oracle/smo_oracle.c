@@ -17,7 +17,11 @@
  *   or_dot            Algorithm 2 (merge-style inner product of two CSR rows)
  *   or_kernel         RBF kernel exp(-gamma * ||x - z||^2), distance from
  *                     ||x||^2 + ||z||^2 - 2<x,z> (Section IV-E, Eq. for the
- *                     Gaussian kernel in Section V-A, gamma = 1/(2 sigma^2))
+ *                     Gaussian kernel in Section V-A, gamma = 1/(2 sigma^2));
+ *                     or, selected by or_set_kernel, one of the other standard
+ *                     kernels that Section V calls straightforward to use:
+ *                     linear <x,z>, polynomial (gamma <x,z> + coef0)^degree,
+ *                     sigmoid tanh(gamma <x,z> + coef0)
  *   or_smo            Algorithm 1: Keerthi's modification 2 SMO without
  *                     shrinking; Eqs. (fcache), (fup), (setinfo), (bminmax),
  *                     (kktterm), (alphaup), (rho); threshold beta of Sec. III-A
@@ -92,10 +96,32 @@ double or_sqnorm(const or_csr *A, int64_t i)
     return s;
 }
 
-/* K(x,z) = exp(-gamma * ||x-z||^2), ||x-z||^2 = ||x||^2 + ||z||^2 - 2<x,z>
- * (the "simple linear algebra trick"), clamped at 0 against rounding. */
+/* The kernel in use (one per process; set before a call, read-only during
+ * it). kind: 0 RBF, 1 linear, 2 polynomial, 3 sigmoid. */
+static int g_kind = 0;
+static double g_coef0 = 0.0;
+static int g_degree = 3;
+
+void or_set_kernel(int kind, double coef0, int degree)
+{
+    g_kind = kind;
+    g_coef0 = coef0;
+    g_degree = degree;
+}
+
+/* RBF: K(x,z) = exp(-gamma * ||x-z||^2), ||x-z||^2 = ||x||^2 + ||z||^2 - 2<x,z>
+ * (the "simple linear algebra trick"), clamped at 0 against rounding.
+ * Polynomial: the power by repeated multiplication, degree >= 1. */
 double or_kernel(double gamma, double nx, double nz, double dot)
 {
+    if (g_kind == 1) return dot;
+    if (g_kind == 2) {
+        const double b = gamma * dot + g_coef0;
+        double r = b;
+        for (int k = 1; k < g_degree; ++k) r *= b;
+        return r;
+    }
+    if (g_kind == 3) return tanh(gamma * dot + g_coef0);
     double d2 = nx + nz - 2.0 * dot;
     if (d2 < 0.0) d2 = 0.0;
     return exp(-gamma * d2);

@@ -24,7 +24,7 @@ import oracle
 from paper_1406_5161_gb300 import synth
 import os as _os, sys as _sys
 _sys.path.insert(0, _os.path.dirname(__file__))
-from qp_reference import dual_bruteforce, dual_objective, rbf_matrix
+from qp_reference import dual_bruteforce, dual_objective, kernel_matrix, rbf_matrix
 
 
 # every run is capped: a wrong oracle may never converge
@@ -232,6 +232,79 @@ def check_shrink_keeps_path(lib=None):
     assert first >= 0.5 * plain["iters"], (first, plain["iters"])
 
 
+# ---------------------------------------------------------------- other kernels
+# Section V: other kernels are straightforward to use. Linear <x,z>,
+# polynomial (gamma <x,z> + coef0)^degree, sigmoid tanh(gamma <x,z> + coef0).
+KERNEL_CASES = [(oracle.KERNEL_LINEAR, 0.0, 1), (oracle.KERNEL_POLY, 1.0, 2),
+                (oracle.KERNEL_POLY, 0.5, 3)]
+
+
+def check_linear_two_point_closed_form(lib=None):
+    # two points of opposite labels, linear kernel: the hard-margin optimum is
+    # alpha = 2 / ||x1 - x2||^2 (both on the margin), clipped at C
+    with oracle.kernel_spec(oracle.KERNEL_LINEAR, lib=lib):
+        for x1, x2, C in [((0.0, 0.0), (1.0, 0.0), 100.0), ((0.5, -1.0), (2.0, 1.0), 100.0),
+                          ((0.0, 0.0), (0.25, 0.0), 10.0), ((1.0, 2.0), (-1.0, 0.5), 0.3)]:
+            x = np.array([x1, x2], dtype=np.float32)
+            X = synth.csr_from_dense(x, keep_zeros=True)
+            y = np.array([1, -1], dtype=np.int8)
+            d2 = float(((x[0].astype(np.float64) - x[1]) ** 2).sum())
+            a_star = min(C, 2.0 / d2)
+            r = oracle.smo(X, y, C, 1.0, 1e-9, max_iter=10, lib=lib)
+            assert r["iters"] == 1, r["iters"]
+            assert np.allclose(r["alpha"], a_star, rtol=1e-13, atol=0), (r["alpha"], a_star)
+            if a_star < C:   # both points on the margin: f_1 = f_2 = b
+                assert abs(r["f"][0] - r["f"][1]) <= 1e-12 * max(1.0, abs(r["f"][0]))
+                assert abs(r["b"] - r["f"][0]) <= 1e-12 * max(1.0, abs(r["b"]))
+
+
+def check_kernels_bruteforce(lib=None):
+    for kind, c0, deg in KERNEL_CASES:
+        with oracle.kernel_spec(kind, c0, deg, lib=lib):
+            for n, seed, C in ((5, 41, 1.0), (7, 42, 3.0), (8, 43, 0.5)):
+                p = synth.small_dense(n, 3, seed, sep=0.3, C=C, gamma=0.4, tau=1e-10)
+                D = _dense(p.X)
+                K = kernel_matrix(D, D, kind, p.gamma, c0, deg)
+                w_star, a_star = dual_bruteforce(K, p.y.astype(np.float64), C)
+                r = oracle.smo(p.X, p.y, C, p.gamma, 1e-10, max_iter=MAXIT, lib=lib)
+                w = dual_objective(r["alpha"], p.y.astype(np.float64), K)
+                assert abs(w - w_star) <= 1e-9 * max(1.0, abs(w_star)), (kind, n, w, w_star)
+                assert np.abs(r["alpha"] - a_star).max() <= 1e-6, (kind, n, r["alpha"], a_star)
+
+
+def check_linear_decision_is_primal(lib=None):
+    # linear kernel: sum_j a_j y_j <x_j, z> - b = <w, z> - b, w = sum_j a_j y_j x_j
+    p = synth.random_sparse(90, 12, 0.4, seed=44, min_nnz=1, C=1.0, gamma=1.0)
+    q = synth.random_sparse(40, 12, 0.4, seed=45, min_nnz=1)
+    with oracle.kernel_spec(oracle.KERNEL_LINEAR, lib=lib):
+        r = oracle.smo(p.X, p.y, p.C, 1.0, 1e-3, max_iter=MAXIT, lib=lib)
+        assert r["status"] == 0
+        w = (r["alpha"] * p.y) @ _dense(p.X)
+        dv = oracle.decision(p.X, p.y, r["alpha"], r["b"], 1.0, q.X, lib=lib)
+    ref = _dense(q.X) @ w - r["b"]
+    assert np.abs(dv - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
+
+
+def check_kernels_invariants(lib=None):
+    # every kernel, sigmoid included (not positive definite): box, equality
+    # constraint, maintained f equal to the numpy Gram matrix's, KKT at exit
+    for kind, c0, deg in KERNEL_CASES + [(oracle.KERNEL_SIGMOID, -0.5, 0)]:
+        with oracle.kernel_spec(kind, c0, deg, lib=lib):
+            p = synth.small_dense(70, 4, 46 + kind, sep=0.4, C=1.0, gamma=0.1, tau=1e-4)
+            D = _dense(p.X)
+            K = kernel_matrix(D, D, kind, p.gamma, c0, deg)
+            y = p.y.astype(np.float64)
+            r = oracle.smo(p.X, p.y, p.C, p.gamma, 1e-4, max_iter=MAXIT, lib=lib)
+            a = r["alpha"]
+            assert r["status"] == 0, kind
+            assert abs(y @ a) <= 1e-12 * len(a) and (a >= 0).all() and (a <= p.C).all()
+            f_ref = K @ (a * y) - y
+            assert np.abs(r["f"] - f_ref).max() <= 1e-10 * max(1.0, np.abs(f_ref).max()), kind
+            up = ((a > 0) & (a < p.C)) | ((y > 0) & (a == 0)) | ((y < 0) & (a == p.C))
+            low = ((a > 0) & (a < p.C)) | ((y > 0) & (a == p.C)) | ((y < 0) & (a == 0))
+            assert f_ref[low].max() - f_ref[up].min() <= 2e-4 + 1e-12, kind
+
+
 ALL_CHECKS = [
     check_dot_and_norm,
     check_kernel_closed_form,
@@ -242,4 +315,8 @@ ALL_CHECKS = [
     check_shrink_same_optimum,
     check_shrink_none_is_plain,
     check_shrink_keeps_path,
+    check_linear_two_point_closed_form,
+    check_kernels_bruteforce,
+    check_linear_decision_is_primal,
+    check_kernels_invariants,
 ]

@@ -2,7 +2,8 @@
 
 * ``rbf_matrix``: the RBF Gram matrix from dense float64 rows by numpy,
   exp(-gamma * ||x_i - x_j||^2) with the distance taken directly, not through
-  the norm expansion the oracle uses.
+  the norm expansion the oracle uses; ``kernel_matrix`` the other kernels
+  (linear, polynomial, sigmoid) from the dense inner products.
 * ``dual_bruteforce``: exact maximiser of the SVM dual QP for tiny n by
   enumerating, for every sample, the three faces {alpha = 0, alpha = C,
   free} and solving the equality-constrained stationarity system on the
@@ -20,6 +21,20 @@ def rbf_matrix(A: np.ndarray, B: np.ndarray, gamma: float) -> np.ndarray:
     B = np.asarray(B, dtype=np.float64)
     diff = A[:, None, :] - B[None, :, :]
     return np.exp(-gamma * np.einsum("ijk,ijk->ij", diff, diff))
+
+
+def kernel_matrix(A: np.ndarray, B: np.ndarray, kind: int, gamma: float, coef0: float = 0.0,
+                  degree: int = 3) -> np.ndarray:
+    """Gram matrix of the kernel kind (0 RBF, 1 linear, 2 polynomial,
+    3 sigmoid) from dense float64 rows by numpy."""
+    if kind == 0:
+        return rbf_matrix(A, B, gamma)
+    G = np.asarray(A, dtype=np.float64) @ np.asarray(B, dtype=np.float64).T
+    if kind == 1:
+        return G
+    if kind == 2:
+        return np.power(gamma * G + coef0, degree)
+    return np.tanh(gamma * G + coef0)
 
 
 def dual_objective(alpha, y, K) -> float:
