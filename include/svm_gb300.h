@@ -124,7 +124,30 @@ typedef struct svm_params {
                                 are not binary: 0 = automatic (FP64 precision only; up
                                 to half the free memory, at most 32 GiB), < 0 = off,
                                 > 0 = this budget (FP64 and mixed precision) */
+    int32_t kernel;          /* enum svm_kernel_kind; 0 = RBF (Section V-A) */
+    int32_t degree;          /* SVM_KERNEL_POLY: degree >= 1 */
+    double coef0;            /* SVM_KERNEL_POLY / SVM_KERNEL_SIGMOID: offset */
 } svm_params;
+
+/* Kernels. RBF exp(-gamma ||x - z||^2) is the paper's (Section V-A); the
+ * others are the standard ones Section V calls straightforward to use:
+ * linear <x, z>, polynomial (gamma <x, z> + coef0)^degree, sigmoid
+ * tanh(gamma <x, z> + coef0). They run on the FP64 and mixed row passes and
+ * the CUDA-core contraction; binary inputs take the general (values) path,
+ * and the tensor-core contraction, batches and the server are RBF only. */
+typedef enum svm_kernel_kind {
+    SVM_KERNEL_RBF = 0,
+    SVM_KERNEL_LINEAR = 1,
+    SVM_KERNEL_POLY = 2,
+    SVM_KERNEL_SIGMOID = 3
+} svm_kernel_kind;
+
+typedef struct svm_kernel {
+    int32_t kind;            /* enum svm_kernel_kind */
+    int32_t degree;          /* polynomial degree >= 1 */
+    double gamma;            /* > 0 */
+    double coef0;
+} svm_kernel;
 
 /* Keep every row segment in global memory even when it would fit in the
  * SM's shared memory (the default holds rows, f, alpha and the index sets of
@@ -214,6 +237,15 @@ int svm_train(const svm_csr *X, const int8_t *y, const svm_params *params,
 int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double b,
                  double gamma, const svm_csr *Z, int32_t precision, void *stream,
                  double *out);
+
+/*
+ * svm_decision_kernel -- svm_decision for any svm_kernel (the RBF kernel
+ * gives the same values as svm_decision). Non-RBF kernels use the CUDA-core
+ * contraction in FP64 or mixed precision.
+ */
+int svm_decision_kernel(const svm_csr *X, const int8_t *y, const double *alpha, double b,
+                        const svm_kernel *kernel, const svm_csr *Z, int32_t precision,
+                        void *stream, double *out);
 
 /* ------------------------------------------------------------ batching */
 

@@ -26,6 +26,7 @@ SVM_FLAG_STREAM_ROWS = 1
 SVM_FLAG_PHASE_TIMES = 2
 SVM_FLAG_NO_CLUSTERS = 4
 SVM_FLAG_CSR_ROWS = 8
+SVM_KERNEL_RBF, SVM_KERNEL_LINEAR, SVM_KERNEL_POLY, SVM_KERNEL_SIGMOID = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "SVM_OK", 1: "SVM_NOT_CONVERGED", 2: "SVM_PENDING", -1: "SVM_ERR_ARG",
                 -2: "SVM_ERR_OOM", -3: "SVM_ERR_BUDGET", -4: "SVM_ERR_TIMEOUT",
@@ -43,7 +44,13 @@ class svm_params(ct.Structure):
                 ("max_iter", ct.c_int64), ("precision", ct.c_int32), ("tie_break", ct.c_int32),
                 ("stream", ct.c_void_p), ("trace", ct.c_void_p), ("trace_len", ct.c_int64),
                 ("flags", ct.c_int32), ("ctas", ct.c_int32),
-                ("lanes_per_row", ct.c_int32), ("cache_mb", ct.c_int32)]
+                ("lanes_per_row", ct.c_int32), ("cache_mb", ct.c_int32),
+                ("kernel", ct.c_int32), ("degree", ct.c_int32), ("coef0", ct.c_double)]
+
+
+class svm_kernel(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("degree", ct.c_int32), ("gamma", ct.c_double),
+                ("coef0", ct.c_double)]
 
 
 class svm_shrink_policy(ct.Structure):
@@ -99,6 +106,8 @@ def load(build_if_missing: bool = True):
             lib.svm_train.argtypes = [P, P, P, P, P, P, P, P]
             lib.svm_decision.restype = ct.c_int
             lib.svm_decision.argtypes = [P, P, P, ct.c_double, ct.c_double, P, ct.c_int32, P, P]
+            lib.svm_decision_kernel.restype = ct.c_int
+            lib.svm_decision_kernel.argtypes = [P, P, P, ct.c_double, P, P, ct.c_int32, P, P]
             lib.svm_last_error.restype = ct.c_char_p
             lib.svm_last_error.argtypes = []
             lib.svm_version.restype = ct.c_char_p
@@ -189,9 +198,12 @@ def _stream_ptr(stream):
 def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int = 0,
               precision: int = SVM_FP64, shrink: tuple | None = None, stream=None,
               trace_len: int = 0, alpha_out=None, flags: int = 0, ctas: int = 0,
-              lanes_per_row: int = 0, cache_mb: int = 0, check: bool = True) -> dict:
+              lanes_per_row: int = 0, cache_mb: int = 0, kernel: int = SVM_KERNEL_RBF,
+              degree: int = 3, coef0: float = 0.0, check: bool = True) -> dict:
     """Train by SMO. ``shrink`` = (kind, value, recon[, first_factor]) or None.
     ``cache_mb``: kernel-row cache budget in MiB (0 automatic, < 0 off).
+    ``kernel``: SVM_KERNEL_* (RBF default; polynomial uses degree, coef0;
+    sigmoid uses coef0).
     X is a host CSR (numpy arrays) or a DeviceCSR; y matches X's memory space.
     Returns dict(status, alpha, b, iters, stats, trace)."""
     lib = load()
@@ -212,7 +224,8 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
     trace = np.full((max(trace_len, 0), 2), -1, dtype=np.int32)
     p = svm_params(float(C), float(gamma), float(tau), int(max_iter), int(precision), 0,
                    _stream_ptr(stream), trace.ctypes.data if trace_len else None, int(trace_len),
-                   int(flags), int(ctas), int(lanes_per_row), int(cache_mb))
+                   int(flags), int(ctas), int(lanes_per_row), int(cache_mb), int(kernel), int(degree),
+                   float(coef0))
     pol = None
     if shrink is not None:
         kind, value, recon = shrink[:3]
@@ -232,8 +245,9 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
 
 
 def svm_decision(X, y, alpha, b: float, gamma: float, Z, *, precision: int = SVM_FP64,
-                 stream=None, out=None, check: bool = True):
-    """Eq. (classi) before the sign for the rows of Z."""
+                 stream=None, out=None, kernel: int = SVM_KERNEL_RBF, degree: int = 3,
+                 coef0: float = 0.0, check: bool = True):
+    """Eq. (classi) before the sign for the rows of Z (any kernel)."""
     lib = load()
     h = _Hold()
     cx, devx = _csr(h, X)
@@ -254,8 +268,13 @@ def svm_decision(X, y, alpha, b: float, gamma: float, Z, *, precision: int = SVM
         if out is None:
             out = np.zeros(m)
         op = out.ctypes.data
-    rc = lib.svm_decision(ct.byref(cx), yp, ap, float(b), float(gamma), ct.byref(cz),
-                          int(precision), _stream_ptr(stream), op)
+    if kernel == SVM_KERNEL_RBF:
+        rc = lib.svm_decision(ct.byref(cx), yp, ap, float(b), float(gamma), ct.byref(cz),
+                              int(precision), _stream_ptr(stream), op)
+    else:
+        k = svm_kernel(int(kernel), int(degree), float(gamma), float(coef0))
+        rc = lib.svm_decision_kernel(ct.byref(cx), yp, ap, float(b), ct.byref(k), ct.byref(cz),
+                                     int(precision), _stream_ptr(stream), op)
     if check and rc < 0:
         raise SvmError(rc, svm_last_error())
     return out

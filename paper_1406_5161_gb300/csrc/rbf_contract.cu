@@ -1,5 +1,7 @@
 // RBF contraction of query rows against the support vectors on CUDA cores:
 //   out[q] = sum_k coef_k * exp(-gamma * (||z_q||^2 + ||x_k||^2 - 2 <z_q, x_k>))
+//   (or, in the FP64 and mixed modes, K = a function of <z_q, x_k> for the
+//   linear, polynomial and sigmoid kernels)
 // This is the inner loop of gradient reconstruction (Algorithm 6, f of the
 // shrunk samples from all alpha > 0) and of the decision function
 // (Eq. classi). A CTA holds a tile of TQ query rows densified in shared
@@ -94,10 +96,16 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
                 for (int q = 0; q < TQ; ++q) acc[q] = fma(v, zc[q], acc[q]);
             }
             const double xn = c.x_norm[j];
+            if (c.kernel == KERNEL_RBF) {
 #pragma unroll
-            for (int q = 0; q < TQ; ++q) {
-                double d2 = zn[q] + xn - 2.0 * acc[q];
-                part[q] = fma(coef, exp(-c.gamma * (d2 < 0.0 ? 0.0 : d2)), part[q]);
+                for (int q = 0; q < TQ; ++q) {
+                    double d2 = zn[q] + xn - 2.0 * acc[q];
+                    part[q] = fma(coef, exp(-c.gamma * (d2 < 0.0 ? 0.0 : d2)), part[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < TQ; ++q)
+                    part[q] = fma(coef, kernel_of_dot(c.kernel, c.gamma, c.coef0, c.degree, acc[q]), part[q]);
             }
         } else {
             float acc[TQ];
@@ -111,10 +119,17 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
             }
             const float xn = c.x_normf[j];
             const float g = (float)c.gamma;
+            if (c.kernel == KERNEL_RBF) {
 #pragma unroll
-            for (int q = 0; q < TQ; ++q) {
-                float d2 = (float)zn[q] + xn - 2.0f * acc[q];
-                part[q] = fma(coef, (double)__expf(-g * fmaxf(d2, 0.f)), part[q]);
+                for (int q = 0; q < TQ; ++q) {
+                    float d2 = (float)zn[q] + xn - 2.0f * acc[q];
+                    part[q] = fma(coef, (double)__expf(-g * fmaxf(d2, 0.f)), part[q]);
+                }
+            } else {
+                const float c0 = (float)c.coef0;
+#pragma unroll
+                for (int q = 0; q < TQ; ++q)
+                    part[q] = fma(coef, (double)kernel_of_dot(c.kernel, g, c0, c.degree, acc[q]), part[q]);
             }
         }
     }

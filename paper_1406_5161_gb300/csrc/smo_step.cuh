@@ -673,14 +673,30 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         eta = etab[dist];
                         curved = __double_as_longlong(rinv) != 0;   // eta > 1e-12
                     } else {
-                        if constexpr (MODE == MODE_FP64) {
-                            double d2 = up.nrm + low.nrm - 2.0 * s;
-                            kul = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                        if (A.kernel == KERNEL_RBF) {
+                            if constexpr (MODE == MODE_FP64) {
+                                double d2 = up.nrm + low.nrm - 2.0 * s;
+                                kul = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                            } else {
+                                float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
+                                kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
+                            }
+                            eta = 2.0 - 2.0 * kul;   // K(x,x) = 1
                         } else {
-                            float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
-                            kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
+                            // eta = K_uu + K_ll - 2 K_ul, K_uu from ||x_up||^2
+                            double kuu, kll;
+                            if constexpr (MODE == MODE_FP64) {
+                                kul = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, s);
+                                kuu = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, up.nrm);
+                                kll = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, low.nrm);
+                            } else {
+                                const float c0 = (float)A.coef0;
+                                kul = (double)kernel_of_dot(A.kernel, gammaf, c0, A.degree, (float)s);
+                                kuu = (double)kernel_of_dot(A.kernel, gammaf, c0, A.degree, (float)up.nrm);
+                                kll = (double)kernel_of_dot(A.kernel, gammaf, c0, A.degree, (float)low.nrm);
+                            }
+                            eta = __dsub_rn(__dadd_rn(kuu, kll), __dmul_rn(2.0, kul));
                         }
-                        eta = 2.0 - 2.0 * kul;
                         curved = dless(1e-12, eta);
                     }
                     // Eq. (alphaup) with rho = -eta (Eq. rho), K(x,x) = 1,
@@ -852,7 +868,12 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         if (kc_hu) {
                             ku = (double)kc_ru[gi];
                         } else {
-                            if constexpr (MODE == MODE_FP64) {
+                            if (A.kernel != KERNEL_RBF) {
+                                if constexpr (MODE == MODE_FP64)
+                                    ku = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, (double)su);
+                                else
+                                    ku = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)su);
+                            } else if constexpr (MODE == MODE_FP64) {
                                 const double d2u = up.nrm + NRM(r) - 2.0 * su;
                                 ku = exp(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
                             } else {
@@ -864,7 +885,12 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         if (kc_hl) {
                             kl = (double)kc_rl[gi];
                         } else {
-                            if constexpr (MODE == MODE_FP64) {
+                            if (A.kernel != KERNEL_RBF) {
+                                if constexpr (MODE == MODE_FP64)
+                                    kl = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, (double)sl);
+                                else
+                                    kl = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)sl);
+                            } else if constexpr (MODE == MODE_FP64) {
                                 const double d2l = low.nrm + NRM(r) - 2.0 * sl;
                                 kl = exp(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
                             } else {

@@ -373,8 +373,16 @@ struct DevCSR {
     int64_t npos = 0;
 };
 
+__global__ void k_fill_ones(int64_t m, float *v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) v[i] = 1.0f;
+}
+
+// binary_ok = false: binary rows are kept on the general (values) path,
+// with explicit 1.0 values when the matrix has none
 void ingest(Arena &ar, const svm_csr *X, const int8_t *y, bool need_fp64, bool need_mixed,
-            cudaStream_t st, DevCSR &out, int *launches)
+            cudaStream_t st, DevCSR &out, int *launches, bool binary_ok = true)
 {
     if (!X) ARG_FAIL("matrix is NULL");
     if (X->n < 1 || X->d < 1) ARG_FAIL("n and d must be >= 1 (n=%lld d=%lld)", (long long)X->n, (long long)X->d);
@@ -428,6 +436,16 @@ void ingest(Arena &ar, const svm_csr *X, const int8_t *y, bool need_fp64, bool n
     if (h.nonfinite) ARG_FAIL("values must be finite");
     if (y && h.bad_y) ARG_FAIL("labels must be +1 or -1");
     out.binary = !h.not_binary;
+    if (out.binary && !binary_ok) {
+        out.binary = false;
+        if (!out.values && nnz > 0) {
+            float *v = ar.alloc<float>(nnz);
+            k_fill_ones<<<grid1(nnz), 256, 0, st>>>(nnz, v);
+            CK(cudaGetLastError());
+            ++*launches;
+            out.values = v;
+        }
+    }
     out.maxnnz = h.maxnnz;
     out.npos = (int64_t)h.npos;
     if (!out.binary && need_fp64) out.norm = ar.alloc<double>(X->n);
@@ -494,13 +512,17 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     if (sp.kind < SVM_SHRINK_NONE || sp.kind > SVM_SHRINK_FRACTION) ARG_FAIL("unknown shrink kind %d", sp.kind);
     if (sp.recon != SVM_RECON_SINGLE && sp.recon != SVM_RECON_MULTI) ARG_FAIL("unknown reconstruction mode %d", sp.recon);
     if (sp.kind != SVM_SHRINK_NONE && !(sp.value > 0)) ARG_FAIL("shrink value must be > 0");
+    if (P->kernel < SVM_KERNEL_RBF || P->kernel > SVM_KERNEL_SIGMOID) ARG_FAIL("unknown kernel %d", P->kernel);
+    if (P->kernel == SVM_KERNEL_POLY && (P->degree < 1 || P->degree > 64)) ARG_FAIL("polynomial degree must be 1..64");
+    if (!std::isfinite(P->coef0)) ARG_FAIL("coef0 must be finite");
+    const bool rbf = P->kernel == SVM_KERNEL_RBF;
     cudaStream_t st = as_stream(P->stream);
     int launches = 0;
     Arena ar(st);
     DevCSR D;
     const bool mixed = P->precision != SVM_FP64;
-    const bool use_tc = P->precision == SVM_MIXED_BF16;
-    ingest(ar, X, y, !mixed, mixed, st, D, &launches);
+    const bool use_tc = P->precision == SVM_MIXED_BF16 && rbf;
+    ingest(ar, X, y, !mixed, mixed, st, D, &launches, rbf);
     const int64_t n = D.n;
     if (D.npos == 0 || D.npos == n) ARG_FAIL("both classes must be present");
 
@@ -711,6 +733,9 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.C = P->C;
     A.gamma = P->gamma;
     A.phase_times = (P->flags & SVM_FLAG_PHASE_TIMES) != 0;
+    A.kernel = P->kernel;
+    A.degree = P->degree;
+    A.coef0 = P->coef0;
     if (kc_slots > 0) {
         A.kc = ar.alloc<unsigned char>((size_t)kc_slots * (size_t)kc_ld * (kmode == MODE_FP64 ? 8 : 4));
         A.kc_ld = kc_ld;
@@ -800,6 +825,9 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             c.d = (int32_t)D.d;
             c.mode = mode;
             c.gamma = P->gamma;
+            c.kernel = P->kernel;
+            c.degree = P->degree;
+            c.coef0 = P->coef0;
             c.ktab = ktab;
             c.ktab_len = ktab_len;
             c.out_by_row = 1;
@@ -911,11 +939,16 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     return status_code;
 }
 
-int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double b, double gamma,
+int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double b, const svm_kernel &K,
                   const svm_csr *Z, int32_t precision, void *stream, double *out)
 {
     if (!X || !Z || !y || !alpha || !out) ARG_FAIL("NULL argument");
+    const double gamma = K.gamma;
     if (!(gamma > 0)) ARG_FAIL("gamma must be > 0");
+    if (K.kind < SVM_KERNEL_RBF || K.kind > SVM_KERNEL_SIGMOID) ARG_FAIL("unknown kernel %d", K.kind);
+    if (K.kind == SVM_KERNEL_POLY && (K.degree < 1 || K.degree > 64)) ARG_FAIL("polynomial degree must be 1..64");
+    if (!std::isfinite(K.coef0)) ARG_FAIL("coef0 must be finite");
+    const bool rbf = K.kind == SVM_KERNEL_RBF;
     if (Z->d != X->d) ARG_FAIL("Z->d (%lld) must equal X->d (%lld)", (long long)Z->d, (long long)X->d);
     if (precision < SVM_FP64 || precision > SVM_MIXED_BF16_SIMT) ARG_FAIL("unknown precision %d", precision);
     if (Z->n == 0) return SVM_OK;
@@ -924,8 +957,8 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     Arena ar(st);
     const bool mixed = precision != SVM_FP64;
     DevCSR DX, DZ;
-    ingest(ar, X, y, !mixed, mixed, st, DX, &launches);
-    ingest(ar, Z, nullptr, !mixed, mixed, st, DZ, &launches);
+    ingest(ar, X, y, !mixed, mixed, st, DX, &launches, rbf);
+    ingest(ar, Z, nullptr, !mixed, mixed, st, DZ, &launches, rbf);
     const int64_t n = DX.n;
     const double *alpha_d = alpha;
     if (!X->on_device) {
@@ -985,13 +1018,16 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     c.d = (int32_t)DX.d;
     c.mode = mode;
     c.gamma = gamma;
+    c.kernel = K.kind;
+    c.degree = K.degree;
+    c.coef0 = K.coef0;
     c.ktab = ktab;
     c.ktab_len = ktab_len;
     c.out_by_row = 0;
     c.out = out_d;
     c.yq = nullptr;
     c.add_scalar = -b;
-    if (precision == SVM_MIXED_BF16 && mode == MODE_MIXED && nsv > 0 && tc_rbf_supported((int)DX.d)) {
+    if (rbf && precision == SVM_MIXED_BF16 && mode == MODE_MIXED && nsv > 0 && tc_rbf_supported((int)DX.d)) {
         void *ws = ar.alloc<unsigned char>(tc_rbf_workspace_bytes(DZ.n, nsv, (int)DX.d));
         int tc_err = 0;
         CK(launch_rbf_contract_tc(c, ws, &tc_err, st));
@@ -1678,6 +1714,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     if (!(P->gamma > 0) || !std::isfinite(P->gamma)) ARG_FAIL("gamma must be > 0");
     if (!(P->tau > 0) || !std::isfinite(P->tau)) ARG_FAIL("tau must be > 0");
     if (P->precision != SVM_FP64) ARG_FAIL("the fixed-workspace call supports SVM_FP64 only");
+    if (P->kernel != SVM_KERNEL_RBF) ARG_FAIL("the fixed-workspace call supports the RBF kernel only");
     if (P->tie_break != 0) ARG_FAIL("only the lowest-index tie-break (0) is implemented");
     if (X->n < 2 || X->d < 1) ARG_FAIL("need n >= 2 and d >= 1");
     if (X->n > kFixedMaxRows) {
@@ -1844,7 +1881,28 @@ int svm_decision(const svm_csr *X, const int8_t *y, const double *alpha, double 
 {
     g_err.clear();
     try {
-        return decision_impl(X, y, alpha, b, gamma, Z, precision, stream, out);
+        svm_kernel K;
+        K.kind = SVM_KERNEL_RBF;
+        K.degree = 3;
+        K.gamma = gamma;
+        K.coef0 = 0.0;
+        return decision_impl(X, y, alpha, b, K, Z, precision, stream, out);
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_decision_kernel(const svm_csr *X, const int8_t *y, const double *alpha, double b,
+                        const svm_kernel *kernel, const svm_csr *Z, int32_t precision, void *stream,
+                        double *out)
+{
+    g_err.clear();
+    try {
+        if (!kernel) ARG_FAIL("kernel is NULL");
+        return decision_impl(X, y, alpha, b, *kernel, Z, precision, stream, out);
     } catch (const Fail &f) {
         return f.code;
     } catch (...) {

@@ -23,6 +23,36 @@ __host__ __device__ __forceinline__ uint8_t st_of(int8_t y, double a, double C)
 
 // Row-pass arithmetic of the fused step.
 enum { MODE_BINARY = 0, MODE_FP64 = 1, MODE_MIXED = 2, MODE_BITS4 = 3, MODE_BITS8 = 4 };
+
+// Kernels (svm_kernel_kind). The RBF kernel is evaluated where its squared
+// distance is formed; the others are functions of the inner product.
+enum { KERNEL_RBF = 0, KERNEL_LINEAR = 1, KERNEL_POLY = 2, KERNEL_SIGMOID = 3 };
+
+// linear <x,z>, polynomial (gamma <x,z> + coef0)^degree (power by repeated
+// products), sigmoid tanh(gamma <x,z> + coef0); each FP64 operation rounded
+// on its own, in this order
+__device__ __forceinline__ double kernel_of_dot(int kind, double gamma, double coef0, int degree, double dot)
+{
+    if (kind == KERNEL_LINEAR) return dot;
+    const double b = __dadd_rn(__dmul_rn(gamma, dot), coef0);
+    if (kind == KERNEL_POLY) {
+        double r = b;
+        for (int k = 1; k < degree; ++k) r = __dmul_rn(r, b);
+        return r;
+    }
+    return tanh(b);
+}
+__device__ __forceinline__ float kernel_of_dot(int kind, float gamma, float coef0, int degree, float dot)
+{
+    if (kind == KERNEL_LINEAR) return dot;
+    const float b = __fadd_rn(__fmul_rn(gamma, dot), coef0);
+    if (kind == KERNEL_POLY) {
+        float r = b;
+        for (int k = 1; k < degree; ++k) r = __fmul_rn(r, b);
+        return r;
+    }
+    return tanhf(b);
+}
 // Binary rows held as bit masks of 4 or 8 words (d <= 128 or d <= 256): the
 // squared distance of two binary rows is the popcount of their XOR.
 __host__ __device__ constexpr bool mode_bits(int m) { return m == MODE_BITS4 || m == MODE_BITS8; }
@@ -95,6 +125,8 @@ struct SmoArgs {
     int64_t kc_ld;
     int32_t kc_slots;
     int32_t kc_direct;
+    int32_t kernel, degree;    // kernel kind (KERNEL_*); polynomial degree
+    double coef0;              // polynomial / sigmoid offset
 };
 
 // ---- batched and served solves: one job = one two-class problem
@@ -238,6 +270,8 @@ struct RbfContract {
     int32_t d;
     int32_t mode;              // MODE_BINARY / MODE_FP64 / MODE_MIXED
     double gamma;
+    int32_t kernel, degree;    // kernel kind (KERNEL_*; binary and tensor-core paths: RBF)
+    double coef0;
     const double *ktab;        // binary: exp(-gamma * k)
     int32_t ktab_len;
     int32_t out_by_row;        // 1: out[row id], 0: out[list position]

@@ -333,3 +333,57 @@ def test_kernel_row_cache_with_evictions_is_exact(precision, shrink):
     assert s["cache_misses"] > s["cache_slots"]          # rows were evicted and recomputed
     assert s["cache_hits"] > 0
     _same(on, off)
+
+
+# ---------------------------------------------------------------- other kernels
+KERNELS = [(pkg.SVM_KERNEL_LINEAR, 0.0, 1), (pkg.SVM_KERNEL_POLY, 1.0, 3),
+           (pkg.SVM_KERNEL_SIGMOID, -1.0, 0)]
+
+
+@pytest.mark.parametrize("kind,c0,deg", KERNELS, ids=["linear", "poly3", "sigmoid"])
+@pytest.mark.parametrize("binary", [False, True], ids=["dense", "binary"])
+def test_other_kernels_match_oracle(kind, c0, deg, binary):
+    """Linear, polynomial and sigmoid kernels (FP64): pairs as the oracle's,
+    the oracle's KKT check and objective, decision values; binary inputs take
+    the general path with explicit unit values."""
+    if binary:
+        p = synth.random_sparse(1500, 60, 0.1, seed=61, binary=True, C=1.0, gamma=0.05)
+        Z = synth.random_sparse(500, 60, 0.1, seed=62, binary=True).X
+    else:
+        p = synth.gaussian_mixture(n=1500, n_test=500, seed=63)
+        Z = p.Z
+    with oracle.kernel_spec(kind, c0, deg):
+        ref = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, trace_len=300, max_iter=200000)
+        assert ref["status"] == 0
+        r, Xd, yd = gpu_train(p, trace_len=300, kernel=kind, degree=deg, coef0=c0)
+        assert r["status"] == pkg.SVM_OK
+        assert r["stats"]["binary_input"] == 0
+        t = first_mismatch(r["trace"], ref["trace"], ref["margin"], 300)
+        assert t >= min(200, ref["iters"])
+        check_end_state(p, r, ref)
+        dz = pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, pkg.to_device(Z), kernel=kind,
+                              degree=deg, coef0=c0).cpu().numpy()
+        dref = oracle.decision(p.X, p.y, ref["alpha"], ref["b"], p.gamma, Z)
+    assert np.abs(dz - dref).max() <= 1e-3 * max(1.0, np.abs(dref).max())
+    assert (np.sign(dz) == np.sign(dref)).mean() >= 0.999
+
+
+@pytest.mark.parametrize("kind,c0,deg", KERNELS[:2], ids=["linear", "poly3"])
+def test_other_kernels_mixed_precision(kind, c0, deg):
+    """The mixed row pass with another kernel reaches the FP64 optimum within
+    the perturbation of BF16 values."""
+    p = synth.gaussian_mixture(n=1500, n_test=0, seed=64)
+    with oracle.kernel_spec(kind, c0, deg):
+        ref = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=200000)
+        r, _, _ = gpu_train(p, kernel=kind, degree=deg, coef0=c0, precision=pkg.SVM_MIXED_BF16)
+        assert r["status"] == pkg.SVM_OK
+        kk = oracle.kkt(p.X, p.y, r["alpha"].cpu().numpy(), p.C, p.gamma)
+    assert abs(kk["objective"] - ref["objective"]) <= 2e-3 * abs(ref["objective"])
+
+
+def test_kernel_arguments_are_checked():
+    p = synth.small_dense(20, 3, seed=1)
+    r = pkg.svm_train(p.X, p.y, 1.0, 0.1, 1e-3, kernel=9, check=False)
+    assert r["status"] == pkg.SVM_ERR_ARG and "kernel" in pkg.svm_last_error()
+    r = pkg.svm_train(p.X, p.y, 1.0, 0.1, 1e-3, kernel=pkg.SVM_KERNEL_POLY, degree=0, check=False)
+    assert r["status"] == pkg.SVM_ERR_ARG and "degree" in pkg.svm_last_error()
