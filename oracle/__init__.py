@@ -80,6 +80,9 @@ def _bind(path: str):
     lib.or_smo.restype = ct.c_int
     lib.or_smo.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_double, ct.c_int64,
                            P, P, P, P, P, P, ct.c_int64]
+    lib.or_smo_wss2.restype = ct.c_int
+    lib.or_smo_wss2.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_double, ct.c_int64,
+                                P, P, P, P, P, ct.c_int64]
     lib.or_smo_shrink.restype = ct.c_int
     lib.or_smo_shrink.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_double,
                                   ct.c_int64, ct.c_int, ct.c_double, ct.c_int,
@@ -220,6 +223,31 @@ def smo(X, y, C: float, gamma: float, tau: float, max_iter: int = 10**9,
         out["margin"] = margin[:m]
         if objs is not None:
             out["objectives"] = objs[:m]
+    return out
+
+
+def smo_wss2(X, y, C: float, gamma: float, tau: float, max_iter: int = 10**9,
+             trace_len: int = 0, lib=None) -> dict:
+    """SMO with the second-order choice of i_low (no shrinking). The trace's
+    margins are, per step, the I_up margin (second best minus best f) and the
+    chosen gain's relative lead over the runner-up."""
+    k = _Keep()
+    n = int(X.n)
+    alpha = np.zeros(n)
+    f = np.zeros(n)
+    res = _Result()
+    trace = np.full((max(trace_len, 0), 2), -1, dtype=np.int64)
+    margin = np.zeros((max(trace_len, 0), 2))
+    (lib or _load()).or_smo_wss2(k.csr(X), _ptr(k.arr(y, np.int8)), C, gamma, tau, int(max_iter),
+                                 _ptr(alpha), _ptr(f), ct.byref(res),
+                                 _ptr(trace) if trace_len else None,
+                                 _ptr(margin) if trace_len else None, int(trace_len))
+    out = _result(res)
+    out.update(alpha=alpha, f=f)
+    if trace_len:
+        m = min(trace_len, res.iters)
+        out["trace"] = trace[:m]
+        out["margin"] = margin[:m]
     return out
 
 

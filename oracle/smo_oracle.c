@@ -25,6 +25,12 @@
  *   or_smo            Algorithm 1: Keerthi's modification 2 SMO without
  *                     shrinking; Eqs. (fcache), (fup), (setinfo), (bminmax),
  *                     (kktterm), (alphaup), (rho); threshold beta of Sec. III-A
+ *   or_smo_wss2       or_smo with a second-order choice of i_low (the
+ *                     working-set selection the paper leaves to future work,
+ *                     Section VI): i_up as in Eq. (bminmax); i_low maximises
+ *                     (f_t - f_up)^2 / (K_uu + K_tt - 2 K_ut) over t in I_low
+ *                     with f_t > f_up (Fan, Chen and Lin, JMLR 2005); same
+ *                     stopping rule (kktterm)
  *   or_smo_shrink     Algorithms 4 and 5 (adaptive shrinking, Eq. (shrink),
  *                     shrink counter heuristics of Sec. III-C and Table 3)
  *                     with single or multiple gradient reconstructions
@@ -514,6 +520,109 @@ enum { OR_RECON_SINGLE = 0, OR_RECON_MULTI = 1 };
  *           keep shrinking; every later reconstruction is triggered at 2 tau.
  * Rows removed in an iteration take no part in that iteration's selection.
  */
+/* i_low of the second-order rule: the largest gain (f_t - f_u)^2 / a_ut over
+ * t in I_low with f_t > f_u, a_ut = K_uu + K_tt - 2 K_ut floored at 1e-12;
+ * lowest index on ties. *gap2 = the gain's relative lead over the runner-up. */
+static int64_t select_low2(const or_csr *X, const double *nrm, double gamma, int64_t n,
+                           const double *f, const uint8_t *set, int64_t u, double *gap2)
+{
+    const double kuu = kern(X, nrm, gamma, u, u);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    double *bg = (double *)malloc(sizeof(double) * 2 * (size_t)nt);
+    int64_t *bi = (int64_t *)malloc(sizeof(int64_t) * (size_t)nt);
+    for (int t = 0; t < nt; ++t) { bg[2 * t] = -1.0; bg[2 * t + 1] = -1.0; bi[t] = -1; }
+#pragma omp parallel if (n >= 4096)
+    {
+        int me = 0;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+#endif
+        double g1 = -1.0, g2 = -1.0;
+        int64_t i1 = -1;
+#pragma omp for schedule(static)
+        for (int64_t t = 0; t < n; ++t) {
+            if (!in_low(set[t]) || !(f[t] > f[u])) continue;
+            const double b = f[t] - f[u];
+            double a = kuu + kern(X, nrm, gamma, t, t) - 2.0 * kern(X, nrm, gamma, u, t);
+            if (a <= 0.0) a = 1e-12;
+            const double g = (b * b) / a;
+            if (g > g1) { g2 = g1; g1 = g; i1 = t; }
+            else if (g > g2) g2 = g;
+        }
+        bg[2 * me] = g1;
+        bg[2 * me + 1] = g2;
+        bi[me] = i1;
+    }
+    /* merge in thread order: threads hold increasing index ranges */
+    double g1 = -1.0, g2 = -1.0;
+    int64_t i1 = -1;
+    for (int t = 0; t < nt; ++t) {
+        if (bi[t] < 0) continue;
+        if (bg[2 * t] > g1) { g2 = g1 > bg[2 * t + 1] ? g1 : bg[2 * t + 1]; g1 = bg[2 * t]; i1 = bi[t]; }
+        else { const double c = bg[2 * t] > bg[2 * t + 1] ? bg[2 * t] : bg[2 * t + 1]; if (c > g2) g2 = c; }
+    }
+    free(bg);
+    free(bi);
+    *gap2 = g1 > 0.0 ? (g1 - g2) / g1 : 0.0;
+    return i1;
+}
+
+int or_smo_wss2(const or_csr *X, const int8_t *y, double C, double gamma, double tau,
+                int64_t max_iter, double *alpha, double *f, or_result *res,
+                int64_t *trace, double *margin, int64_t trace_len)
+{
+    int64_t n = X->n;
+    double *nrm = row_norms(X);
+    uint8_t *set = (uint8_t *)malloc((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        alpha[i] = 0.0;
+        f[i] = -(double)y[i];
+        set[i] = (uint8_t)set_of(y[i], 0.0, C);
+    }
+    int64_t it = 0;
+    or_sel s = select_pair(n, NULL, f, set);
+    int status = 0;
+    while (s.b_low - s.b_up > 2.0 * tau) {
+        if (it >= max_iter) { status = 1; break; }
+        int64_t u = s.i_up;
+        double gap2 = 0.0;
+        int64_t l = select_low2(X, nrm, gamma, n, f, set, u, &gap2);
+        if (trace && it < trace_len) {
+            trace[2 * it] = u;
+            trace[2 * it + 1] = l;
+            if (margin) {
+                margin[2 * it] = s.up2 - s.b_up;
+                margin[2 * it + 1] = gap2;
+            }
+        }
+        double kuu = kern(X, nrm, gamma, u, u), kll = kern(X, nrm, gamma, l, l);
+        double kul = kern(X, nrm, gamma, u, l);
+        or_step st = alpha_step(C, y[u], y[l], alpha[u], alpha[l], f[u], f[l], kuu, kll, kul);
+        alpha[u] = st.au;
+        alpha[l] = st.al;
+        set[u] = (uint8_t)set_of(y[u], alpha[u], C);
+        set[l] = (uint8_t)set_of(y[l], alpha[l], C);
+        update_f(X, nrm, gamma, n, NULL, f, u, l, st.du, st.dl);
+        ++it;
+        s = select_pair(n, NULL, f, set);
+    }
+    res->iters = it;
+    res->b_up = s.b_up;
+    res->b_low = s.b_low;
+    res->b = threshold_b(n, f, set, s.b_up, s.b_low);
+    res->objective = objective(n, y, alpha, f);
+    res->n_shrink = 0;
+    res->n_recon = 0;
+    res->final_active = n;
+    res->status = status;
+    free(set);
+    free(nrm);
+    return status;
+}
+
 int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, double tau,
                   int64_t max_iter, int kind, double value, int recon, double first_factor,
                   double *alpha, double *f, or_result *res,

@@ -305,6 +305,44 @@ def check_kernels_invariants(lib=None):
             assert f_ref[low].max() - f_ref[up].min() <= 2e-4 + 1e-12, kind
 
 
+def check_wss2(lib=None):
+    # second-order choice of i_low: the same optimum as the first-order rule
+    # (brute force for tiny n, KKT and objective for larger), and its first
+    # choice is the argmax of the gain computed here from the Gram matrix
+    for n, seed, C in ((6, 51, 1.0), (8, 52, 3.0)):
+        p = synth.small_dense(n, 3, seed, sep=0.3, C=C, gamma=0.5, tau=1e-10)
+        K = rbf_matrix(_dense(p.X), _dense(p.X), p.gamma)
+        w_star, _ = dual_bruteforce(K, p.y.astype(np.float64), C)
+        r = oracle.smo_wss2(p.X, p.y, C, p.gamma, 1e-10, max_iter=MAXIT, lib=lib)
+        assert abs(r["objective"] - w_star) <= 1e-9 * max(1.0, abs(w_star))
+    p = synth.small_dense(120, 5, 53, sep=0.4, C=1.0, gamma=0.2, tau=1e-4)
+    K = rbf_matrix(_dense(p.X), _dense(p.X), p.gamma)
+    y = p.y.astype(np.float64)
+    r1 = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=MAXIT, lib=lib)
+    r2 = oracle.smo_wss2(p.X, p.y, p.C, p.gamma, p.tau, max_iter=MAXIT, trace_len=5, lib=lib)
+    assert r2["status"] == 0
+    assert abs(r2["objective"] - r1["objective"]) <= 1e-4 * abs(r1["objective"])
+    a = r2["alpha"]
+    f = K @ (a * y) - y
+    up = ((a > 0) & (a < p.C)) | ((y > 0) & (a == 0)) | ((y < 0) & (a == p.C))
+    low = ((a > 0) & (a < p.C)) | ((y > 0) & (a == p.C)) | ((y < 0) & (a == 0))
+    assert f[low].max() - f[up].min() <= 2 * p.tau + 1e-12
+    # each of the first steps: replay the state after k steps, recompute f,
+    # i_up and the gains (f_t - f_i)^2 / (2 - 2 K(i, t)) here, and compare
+    # with the pair the oracle chose at step k
+    tr = oracle.smo_wss2(p.X, p.y, p.C, p.gamma, p.tau, max_iter=MAXIT, trace_len=12, lib=lib)["trace"]
+    for k in range(12):
+        a = oracle.smo_wss2(p.X, p.y, p.C, p.gamma, p.tau, max_iter=k, lib=lib)["alpha"]
+        f = K @ (a * y) - y
+        up = ((a > 0) & (a < p.C)) | ((y > 0) & (a == 0)) | ((y < 0) & (a == p.C))
+        low = ((a > 0) & (a < p.C)) | ((y > 0) & (a == p.C)) | ((y < 0) & (a == 0))
+        i = int(np.nonzero(up)[0][np.argmin(f[up])])
+        cand = np.nonzero(low & (f > f[i]))[0]
+        gain = (f[cand] - f[i]) ** 2 / np.maximum(2.0 - 2.0 * K[i, cand], 1e-12)
+        j = int(cand[np.argmax(gain)])
+        assert tuple(tr[k]) == (i, j), (k, tr[k], i, j)
+
+
 ALL_CHECKS = [
     check_dot_and_norm,
     check_kernel_closed_form,
@@ -319,4 +357,5 @@ ALL_CHECKS = [
     check_kernels_bruteforce,
     check_linear_decision_is_primal,
     check_kernels_invariants,
+    check_wss2,
 ]

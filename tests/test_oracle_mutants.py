@@ -39,6 +39,7 @@ MUTANTS = {
     "poly_power_off_by_one": ("for (int k = 1; k < g_degree; ++k) r *= b;", "for (int k = 2; k < g_degree; ++k) r *= b;"),
     "poly_drops_coef0": ("const double b = gamma * dot + g_coef0;", "const double b = gamma * dot;"),
     "linear_scaled": ("if (g_kind == 1) return dot;", "if (g_kind == 1) return dot * 0.5;"),
+    "wss2_gain_not_squared": ("const double g = (b * b) / a;", "const double g = b / a;"),
     "recon_never_resets": ("for (int64_t i = 0; i < n; ++i) { act[i] = i; live[i] = 1; }\n        m = n;",
                            "for (int64_t i = 0; i < n; ++i) { live[i] = 1; }"),
 }
@@ -48,7 +49,7 @@ ORDER = [P.check_kernel_closed_form, P.check_dot_and_norm, P.check_two_point_clo
          P.check_invariants, P.check_gradient_and_decision, P.check_bruteforce,
          P.check_shrink_none_is_plain, P.check_shrink_keeps_path, P.check_shrink_same_optimum,
          P.check_linear_two_point_closed_form, P.check_kernels_bruteforce,
-         P.check_linear_decision_is_primal, P.check_kernels_invariants]
+         P.check_linear_decision_is_primal, P.check_kernels_invariants, P.check_wss2]
 
 
 def _build(tmp_path, name, old, new):
