@@ -45,6 +45,9 @@ struct __align__(16) BatchFinish {
     int pad[2];
 };
 
+// per warp: 16 k-steps x 32 lanes of packed BF16 target pairs (uint2)
+constexpr size_t kFragBytes = (size_t)kWarps * 16 * 32 * sizeof(uint2);
+
 struct BatchShared {
     Side wup[kWarps], wlow[kWarps];
     unsigned long long wkup[kWarps], wklow[kWarps];
@@ -329,7 +332,93 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                 };
                 bool blocked = false;
                 if constexpr (LPR == 32) blocked = dense && d <= 256;
-                if (blocked) {
+                bool tiles = false;   // dense BF16 rows on the tensor cores
+                if constexpr (LPR == 16 && MODE == MODE_MIXED) tiles = dense && (d & 31) == 0 && d <= 256;
+                if (tiles) {
+                    if constexpr (LPR == 16 && MODE == MODE_MIXED) {
+                        // Tiles of 16 rows x the two target rows on the
+                        // tensor cores (mma m16n8k16, BF16 inputs, FP32
+                        // accumulation; columns 2..7 of B are zero). Inside
+                        // each 32-column block the K order is permuted so
+                        // that a thread reads 8 consecutive values of a row
+                        // with one 16-byte load: in k-step h of the block,
+                        // logical k = 2t + i maps to column 8t + 4h + i and
+                        // k = 2t + 8 + i to 8t + 4h + 2 + i; the targets use
+                        // the same map, so the dot products are unchanged.
+                        const int g = lane >> 2, t = lane & 3;
+                        const int nblk = d >> 5;
+                        // this warp's target fragments: [k-step][lane], k-step = 2 * block + h
+                        uint2 *frag = reinterpret_cast<uint2 *>(dsm + L.total) + (size_t)warp * 16 * 32;
+#pragma unroll
+                        for (int b = 0; b < 8; ++b) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                uint32_t r0 = 0, r1 = 0;
+                                if (!first && g < 2 && b < nblk) {
+                                    const int c = 32 * b + 8 * t + 4 * h;
+                                    float e[4];
+#pragma unroll
+                                    for (int x = 0; x < 4; ++x) e[x] = g == 0 ? T[c + x].x : T[c + x].y;
+                                    const __nv_bfloat162 p0 = __floats2bfloat162_rn(e[0], e[1]);
+                                    const __nv_bfloat162 p1 = __floats2bfloat162_rn(e[2], e[3]);
+                                    r0 = *reinterpret_cast<const uint32_t *>(&p0);
+                                    r1 = *reinterpret_cast<const uint32_t *>(&p1);
+                                }
+                                frag[(2 * b + h) * 32 + lane] = make_uint2(r0, r1);
+                            }
+                        }
+                        __syncwarp();
+                        for (int base = lo + (warp - 1) * 16;; base += kRowWarps * 16) {
+                            const bool round0 = base == lo + (warp - 1) * 16;
+                            if (!round0 && base >= hi) break;
+                            const int ra = base + g, rb = base + g + 8;
+                            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                            if (!first) {
+                                const __nv_bfloat16 *pa = ra < hi ? dmat + (size_t)rows[ra] * d + 8 * t : nullptr;
+                                const __nv_bfloat16 *pb = rb < hi ? dmat + (size_t)rows[rb] * d + 8 * t : nullptr;
+                                // all blocks' loads in flight before their MMAs
+#pragma unroll
+                                for (int b0 = 0; b0 < 8; b0 += 8) {
+                                    uint4 uu[8], vv[8];
+#pragma unroll
+                                    for (int q = 0; q < 8; ++q) {
+                                        const int b = b0 + q;
+                                        uu[q] = (pa && b < nblk) ? __ldg(reinterpret_cast<const uint4 *>(pa + 32 * b)) : make_uint4(0, 0, 0, 0);
+                                        vv[q] = (pb && b < nblk) ? __ldg(reinterpret_cast<const uint4 *>(pb + 32 * b)) : make_uint4(0, 0, 0, 0);
+                                    }
+#pragma unroll
+                                    for (int q = 0; q < 8; ++q) {
+                                    const int b = b0 + q;
+                                    if (b < nblk) {
+                                        const uint4 u = uu[q], v = vv[q];
+                                        const uint2 f0 = frag[(2 * b) * 32 + lane], f1 = frag[(2 * b + 1) * 32 + lane];
+                                        asm volatile(
+                                            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                                            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                                            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3])
+                                            : "r"(u.x), "r"(v.x), "r"(u.y), "r"(v.y), "r"(f0.x), "r"(f0.y));
+                                        asm volatile(
+                                            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                                            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                                            : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3])
+                                            : "r"(u.z), "r"(v.z), "r"(u.w), "r"(v.w), "r"(f1.x), "r"(f1.y));
+                                    }
+                                    }
+                                }
+                            }
+                            // lanes with t == 0 hold the two sums of rows ra and rb
+                            const bool lead = t == 0;
+                            double fa = 0.0, fb = 0.0;
+                            uint8_t sa = 0, sbb = 0;
+                            int ga = 0, gb = 0;
+                            if (lead && ra < hi) { ga = rows[ra]; fa = fj[ra]; sa = sj[ra]; }
+                            if (lead && rb < hi) { gb = rows[rb]; fb = fj[rb]; sbb = sj[rb]; }
+                            wait_step();
+                            if (lead && ra < hi) finish_row(ra, ga, d, acc[0], acc[1], fa, sa);
+                            if (lead && rb < hi) finish_row(rb, gb, d, acc[2], acc[3], fb, sbb);
+                        }
+                    }
+                } else if (blocked) {
                     if constexpr (LPR == 32 && MODE == MODE_MIXED) {
                         // 8 rows per warp at a time; lane l covers columns
                         // [8l, 8l+8) of all 8 rows with its target columns in
@@ -679,7 +768,8 @@ void *batch_fn(int mode, int lpr)
 
 size_t smo_batch_smem(int mode, int d, int ktab_len, int maxnnz)
 {
-    return smo_layout(mode, d, ktab_len, maxnnz, 0, 0, 0).total;
+    // mixed mode: each warp's target fragments of the tensor-core row tiles
+    return smo_layout(mode, d, ktab_len, maxnnz, 0, 0, 0).total + (mode == MODE_MIXED ? smo::kFragBytes : 0);
 }
 
 int smo_batch_max_clusters(int mode, int lpr, int dense, size_t smem, int cs)

@@ -126,3 +126,25 @@ def test_batch_launch_shapes_agree(small_mc, lanes, cluster):
         ref = alone(mc, job, pkg.SVM_MIXED_BF16)
         w = ref["stats"]["objective"]
         assert abs(r["objective"] - w) <= 1e-7 * abs(w)
+
+
+def test_batch_tensor_core_tiles_match_alone():
+    """Dense BF16 rows with d a multiple of 32 at 16 lanes per row run on the
+    tensor cores (mma m16n8k16 tiles of 16 rows x the two targets, FP32
+    accumulation in another order than the CUDA-core sums of svm_train):
+    each job's objective equals the job trained alone within 1e-5 relative,
+    the tolerance the batched form is held to, and its box and equality
+    constraints hold."""
+    mc = synth.multiclass(n=2400, d=64, classes=3, seed=43, mean_sd=0.6, Cs=(0.5, 2.0),
+                          gammas=(0.02, 0.1))
+    jobs = ovo_jobs(mc)
+    out = pkg.svm_train_batch(pkg.to_device(mc.X), dev_jobs(jobs), precision=pkg.SVM_MIXED_BF16,
+                              cluster_size=2, lanes_per_row=16)
+    assert out["status"] == pkg.SVM_OK and out["lanes_per_row"] == 16
+    for job, r in zip(jobs, out["results"]):
+        assert r["status"] == pkg.SVM_OK
+        w = alone(mc, job, pkg.SVM_MIXED_BF16)["stats"]["objective"]
+        assert abs(r["objective"] - w) <= 1e-5 * abs(w), (r["objective"], w)
+        a = r["alpha"].cpu().numpy()
+        assert (a >= 0).all() and (a <= job["C"]).all()
+        assert abs((a * job["y"]).sum()) <= 1e-10 * len(a) * job["C"]
