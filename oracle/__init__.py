@@ -86,7 +86,7 @@ def _bind(path: str):
     lib.or_smo_shrink.restype = ct.c_int
     lib.or_smo_shrink.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_double,
                                   ct.c_int64, ct.c_int, ct.c_double, ct.c_int,
-                                  ct.c_double, P, P, P, P, ct.c_int64, P]
+                                  ct.c_double, P, P, P, P, ct.c_int64, P, ct.c_int]
     lib.or_gradient.restype = None
     lib.or_gradient.argtypes = [P, P, P, ct.c_double, P]
     lib.or_reconstruct.restype = None
@@ -253,8 +253,9 @@ def smo_wss2(X, y, C: float, gamma: float, tau: float, max_iter: int = 10**9,
 
 def smo_shrink(X, y, C: float, gamma: float, tau: float, kind: int, value: float,
                recon: int, first_factor: float = 20.0, max_iter: int = 10**9,
-               trace_len: int = 0, lib=None) -> dict:
-    """Algorithms 4/5 (+ the multiple-reconstruction variant) with Algorithm 6."""
+               trace_len: int = 0, wss: int = 1, lib=None) -> dict:
+    """Algorithms 4/5 (+ the multiple-reconstruction variant) with Algorithm 6.
+    ``wss=2`` chooses i_low by the second-order gain over the active rows."""
     k = _Keep()
     n = int(X.n)
     alpha = np.zeros(n)
@@ -266,7 +267,7 @@ def smo_shrink(X, y, C: float, gamma: float, tau: float, kind: int, value: float
                           int(kind), float(value), int(recon), float(first_factor),
                           _ptr(alpha), _ptr(f), ct.byref(res),
                           _ptr(trace) if trace_len else None, int(trace_len),
-                          _ptr(act) if trace_len else None)
+                          _ptr(act) if trace_len else None, int(wss))
     out = _result(res)
     out.update(alpha=alpha, f=f)
     if trace_len:

@@ -34,7 +34,10 @@
  *   or_smo_shrink     Algorithms 4 and 5 (adaptive shrinking, Eq. (shrink),
  *                     shrink counter heuristics of Sec. III-C and Table 3)
  *                     with single or multiple gradient reconstructions
- *                     (Algorithm 6)
+ *                     (Algorithm 6); wss = 2 takes i_low by the
+ *                     second-order rule over the active rows (the future
+ *                     work of Section VI) while the shrink rule and the
+ *                     stopping tests keep the first-order b_up / b_low
  *   or_reconstruct    Algorithm 6 (gradient reconstruction of given samples)
  *   or_gradient       Eq. (fcache) evaluated from scratch
  *   or_decision       Eq. (classi) without the sign: sum_j a_j y_j K(x_j,z) - b
@@ -519,12 +522,18 @@ enum { OR_RECON_SINGLE = 0, OR_RECON_MULTI = 1 };
  *   MULTI : reset the active set to all rows, restart the counter at h and
  *           keep shrinking; every later reconstruction is triggered at 2 tau.
  * Rows removed in an iteration take no part in that iteration's selection.
+ * With wss = 2 the pair is (i_up, the second-order i_low over the active
+ * rows); b_up and b_low stay the first-order extremes of Eq. (bminmax), so
+ * Eq. (shrink) and Eq. (kktterm) read the same values as without it.
  */
 /* i_low of the second-order rule: the largest gain (f_t - f_u)^2 / a_ut over
  * t in I_low with f_t > f_u, a_ut = K_uu + K_tt - 2 K_ut floored at 1e-12;
- * lowest index on ties. *gap2 = the gain's relative lead over the runner-up. */
-static int64_t select_low2(const or_csr *X, const double *nrm, double gamma, int64_t n,
-                           const double *f, const uint8_t *set, int64_t u, double *gap2)
+ * lowest index on ties. Candidates t are act[0 .. m) (increasing sample
+ * indices), or 0 .. m-1 when act is NULL. *gap2 = the gain's relative lead
+ * over the runner-up. */
+static int64_t select_low2(const or_csr *X, const double *nrm, double gamma, int64_t m,
+                           const int64_t *act, const double *f, const uint8_t *set, int64_t u,
+                           double *gap2)
 {
     const double kuu = kern(X, nrm, gamma, u, u);
     int nt = 1;
@@ -534,7 +543,7 @@ static int64_t select_low2(const or_csr *X, const double *nrm, double gamma, int
     double *bg = (double *)malloc(sizeof(double) * 2 * (size_t)nt);
     int64_t *bi = (int64_t *)malloc(sizeof(int64_t) * (size_t)nt);
     for (int t = 0; t < nt; ++t) { bg[2 * t] = -1.0; bg[2 * t + 1] = -1.0; bi[t] = -1; }
-#pragma omp parallel if (n >= 4096)
+#pragma omp parallel if (m >= 4096)
     {
         int me = 0;
 #ifdef _OPENMP
@@ -543,7 +552,8 @@ static int64_t select_low2(const or_csr *X, const double *nrm, double gamma, int
         double g1 = -1.0, g2 = -1.0;
         int64_t i1 = -1;
 #pragma omp for schedule(static)
-        for (int64_t t = 0; t < n; ++t) {
+        for (int64_t k = 0; k < m; ++k) {
+            const int64_t t = act ? act[k] : k;
             if (!in_low(set[t]) || !(f[t] > f[u])) continue;
             const double b = f[t] - f[u];
             double a = kuu + kern(X, nrm, gamma, t, t) - 2.0 * kern(X, nrm, gamma, u, t);
@@ -589,7 +599,7 @@ int or_smo_wss2(const or_csr *X, const int8_t *y, double C, double gamma, double
         if (it >= max_iter) { status = 1; break; }
         int64_t u = s.i_up;
         double gap2 = 0.0;
-        int64_t l = select_low2(X, nrm, gamma, n, f, set, u, &gap2);
+        int64_t l = select_low2(X, nrm, gamma, n, NULL, f, set, u, &gap2);
         if (trace && it < trace_len) {
             trace[2 * it] = u;
             trace[2 * it + 1] = l;
@@ -626,7 +636,7 @@ int or_smo_wss2(const or_csr *X, const int8_t *y, double C, double gamma, double
 int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, double tau,
                   int64_t max_iter, int kind, double value, int recon, double first_factor,
                   double *alpha, double *f, or_result *res,
-                  int64_t *trace, int64_t trace_len, int64_t *active_trace)
+                  int64_t *trace, int64_t trace_len, int64_t *active_trace, int wss)
 {
     int64_t n = X->n;
     double *nrm = row_norms(X);
@@ -656,6 +666,10 @@ int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, doub
         while (s.b_low - s.b_up > thr) {
             if (it >= max_iter) { status = 1; break; }
             int64_t u = s.i_up, l = s.i_low;
+            if (wss == 2) {
+                double gap2;
+                l = select_low2(X, nrm, gamma, m, act, f, set, u, &gap2);
+            }
             if (trace && it < trace_len) { trace[2 * it] = u; trace[2 * it + 1] = l; }
             if (active_trace && it < trace_len) active_trace[it] = m;
             double kuu = kern(X, nrm, gamma, u, u), kll = kern(X, nrm, gamma, l, l);

@@ -343,6 +343,37 @@ def check_wss2(lib=None):
         assert tuple(tr[k]) == (i, j), (k, tr[k], i, j)
 
 
+def check_wss2_shrink(lib=None):
+    """Second-order i_low with adaptive shrinking. A shrunk row is never a
+    candidate of the gain rule (I1/I2 rows are not in I_low; I3/I4 rows lie
+    below b_up <= f_up), so the shrunk run follows the unshrunk second-order
+    run's pairs until late, and reaches its optimum."""
+    p = synth.small_dense(200, 5, 51, C=1.0, gamma=0.1)
+    a = oracle.smo_wss2(p.X, p.y, p.C, p.gamma, p.tau, max_iter=MAXIT, lib=lib)
+    b = oracle.smo_shrink(p.X, p.y, p.C, p.gamma, p.tau, oracle.SHRINK_NONE, 0, 0,
+                          max_iter=MAXIT, wss=2, lib=lib)
+    assert a["status"] == 0 and a["iters"] == b["iters"]
+    assert np.array_equal(a["alpha"], b["alpha"]) and np.array_equal(a["f"], b["f"])
+    q = _shrink_problem()
+    plain = oracle.smo_wss2(q.X, q.y, q.C, q.gamma, q.tau, max_iter=MAXIT, trace_len=MAXIT, lib=lib)
+    first_order = oracle.smo(q.X, q.y, q.C, q.gamma, q.tau, max_iter=MAXIT, lib=lib)
+    assert plain["status"] == 0 and plain["iters"] < first_order["iters"]
+    for kind, value, rec in SHRINK_POLICIES:
+        s = oracle.smo_shrink(q.X, q.y, q.C, q.gamma, q.tau, kind, value, rec, max_iter=MAXIT,
+                              trace_len=MAXIT, wss=2, lib=lib)
+        assert s["status"] == 0
+        kk = oracle.kkt(q.X, q.y, s["alpha"], q.C, q.gamma, lib=lib)
+        assert kk["gap"] <= 2 * q.tau + 1e-9, (kind, value, rec, kk["gap"])
+        assert abs(kk["objective"] - first_order["objective"]) <= 1e-5 * abs(first_order["objective"])
+        assert np.abs(s["f"] - kk["f"]).max() <= 1e-9
+        m = min(len(plain["trace"]), len(s["trace"]))
+        diff = np.nonzero((plain["trace"][:m] != s["trace"][:m]).any(axis=1))[0]
+        first = int(diff[0]) if len(diff) else m
+        assert first >= 0.5 * plain["iters"], (kind, value, rec, first, plain["iters"])
+        if (kind, value, rec) == (oracle.SHRINK_FRACTION, 0.05, oracle.RECON_MULTI):
+            assert s["n_shrink"] >= 1 and s["active"].min() < q.X.n // 2
+
+
 ALL_CHECKS = [
     check_dot_and_norm,
     check_kernel_closed_form,
@@ -358,4 +389,5 @@ ALL_CHECKS = [
     check_linear_decision_is_primal,
     check_kernels_invariants,
     check_wss2,
+    check_wss2_shrink,
 ]

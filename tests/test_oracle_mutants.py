@@ -40,6 +40,9 @@ MUTANTS = {
     "poly_drops_coef0": ("const double b = gamma * dot + g_coef0;", "const double b = gamma * dot;"),
     "linear_scaled": ("if (g_kind == 1) return dot;", "if (g_kind == 1) return dot * 0.5;"),
     "wss2_gain_not_squared": ("const double g = (b * b) / a;", "const double g = b / a;"),
+    "wss2_shrink_first_order": ("l = select_low2(X, nrm, gamma, m, act, f, set, u, &gap2);",
+                                "l = s.i_low; (void)gap2;"),
+    "wss2_shrink_ignores_active": ("const int64_t t = act ? act[k] : k;", "const int64_t t = k;"),
     "recon_never_resets": ("for (int64_t i = 0; i < n; ++i) { act[i] = i; live[i] = 1; }\n        m = n;",
                            "for (int64_t i = 0; i < n; ++i) { live[i] = 1; }"),
 }
@@ -49,7 +52,8 @@ ORDER = [P.check_kernel_closed_form, P.check_dot_and_norm, P.check_two_point_clo
          P.check_invariants, P.check_gradient_and_decision, P.check_bruteforce,
          P.check_shrink_none_is_plain, P.check_shrink_keeps_path, P.check_shrink_same_optimum,
          P.check_linear_two_point_closed_form, P.check_kernels_bruteforce,
-         P.check_linear_decision_is_primal, P.check_kernels_invariants, P.check_wss2]
+         P.check_linear_decision_is_primal, P.check_kernels_invariants, P.check_wss2,
+         P.check_wss2_shrink]
 
 
 def _build(tmp_path, name, old, new):
