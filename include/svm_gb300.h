@@ -166,6 +166,15 @@ typedef struct svm_kernel {
  * x_up / x_low being the popcount of an XOR; this flag keeps the CSR column
  * gather instead. The results are identical either way. */
 #define SVM_FLAG_CSR_ROWS 8
+/* Second-order working-set selection (the paper's future work, Section VI;
+ * Fan, Chen and Lin, JMLR 6, 2005): i_up as in Eq. (bminmax), i_low the row
+ * t of I_low with f_t > f_up of largest gain (f_t - f_up)^2 / eta_ut,
+ * eta_ut = K_uu + K_tt - 2 K_ut (1e-12 when not positive), over the active
+ * rows, lowest index on ties. The stopping test (Eq. kktterm), the shrink
+ * rule (Eq. shrink) and the reported b_up / b_low keep the first-order
+ * extremes. Each step adds a sweep over the active rows and a second
+ * candidate exchange. svm_train and svm_train_fixed_workspace only. */
+#define SVM_FLAG_WSS2 16
 
 typedef struct svm_shrink_policy {
     int32_t kind;            /* enum svm_shrink_kind */

@@ -26,6 +26,7 @@ SVM_FLAG_STREAM_ROWS = 1
 SVM_FLAG_PHASE_TIMES = 2
 SVM_FLAG_NO_CLUSTERS = 4
 SVM_FLAG_CSR_ROWS = 8
+SVM_FLAG_WSS2 = 16
 SVM_KERNEL_RBF, SVM_KERNEL_LINEAR, SVM_KERNEL_POLY, SVM_KERNEL_SIGMOID = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "SVM_OK", 1: "SVM_NOT_CONVERGED", 2: "SVM_PENDING", -1: "SVM_ERR_ARG",
@@ -282,7 +283,7 @@ def svm_decision(X, y, alpha, b: float, gamma: float, Z, *, precision: int = SVM
 
 def svm_train_fixed_workspace(X, y, C: float, gamma: float, tau: float = 1e-3, *,
                               max_iter: int = 0, stream=None, alpha_out=None,
-                              check: bool = True) -> dict:
+                              flags: int = 0, check: bool = True) -> dict:
     """Plain FP64 solve that allocates no device memory (see the header for
     who needs it and its limits). X, y and alpha_out are device buffers."""
     import torch
@@ -295,7 +296,7 @@ def svm_train_fixed_workspace(X, y, C: float, gamma: float, tau: float = 1e-3, *
     if alpha_out is None:
         alpha_out = torch.empty(int(X.n), dtype=torch.float64, device=X.indptr.device)
     p = svm_params(float(C), float(gamma), float(tau), int(max_iter), SVM_FP64, 0,
-                   _stream_ptr(stream), None, 0, 0, 0, 0, 0)
+                   _stream_ptr(stream), None, 0, int(flags), 0, 0, 0)
     b = ct.c_double(0.0)
     it = ct.c_int64(0)
     rc = lib.svm_train_fixed_workspace(ct.byref(cx), yp, ct.byref(p), alpha_out.data_ptr(),

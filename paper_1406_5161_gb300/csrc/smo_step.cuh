@@ -339,8 +339,9 @@ __device__ __forceinline__ void tgt_clear(typename RowMath<MODE>::Tgt &t)
 
 // SOLO: the grid is one thread-block cluster (exchange through distributed
 // shared memory only); a separate instantiation, so that the kernels for
-// several clusters carry none of its code.
-template <int MODE, int LPR, bool RES, bool SOLO>
+// several clusters carry none of its code. WSS: i_low by the second-order
+// gain (a second sweep and exchange per step), also its own instantiation.
+template <int MODE, int LPR, bool RES, bool SOLO, bool WSS>
 __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
 {
     using Tgt = typename RowMath<MODE>::Tgt;
@@ -561,6 +562,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     // with phase_times every CTA counts the cycles from step start to publish
     const bool busy_on = A.phase_times && A.cta_cycles;
     uint64_t cta_t0 = 0, busy = 0;
+    // second-order selection: low is the gain winner, beta_low the first-order
+    // b_low (Eq. bminmax) that the shrink rule and the stopping test read
+    double beta_low = low.f;
 
     for (;;) {
         const int buf = (int)(iter & 1);
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         int *tcu = tcol + (size_t)(buf * 2 + 0) * maxnnz;
         int *tcl = tcol + (size_t)(buf * 2 + 1) * maxnnz;
         bool shrink_now = false;
-        const double bup_sel = up.f, blow_sel = low.f;   // values that chose this pair
+        const double bup_sel = up.f, blow_sel = WSS ? beta_low : low.f;   // values that chose this pair
         if (busy_on && tid == 0) cta_t0 = clock64();
         if (!first) {
             if (!gap_open) { exit_reason = 0; break; }
@@ -1007,20 +1011,28 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             }
             return sd;
         };
-        // ---- CTA reduction: warp minima of (key, index); winners' payloads
-        {
-            unsigned long long k1 = bku, k2 = bkl;
-            int i1 = biu, i2 = bil;
+        // ---- CTA reduction: warp minima of (key, index); winners' payloads.
+        //      Gain exchange (gx): both sides are the gain winner's row, the
+        //      I_up side carrying -gain in place of f as its key.
+        auto cta_reduce = [&](bool gx, unsigned long long ku_, int iu_, int ru_, unsigned long long kl_,
+                              int il_, int rl_, double gneg) {
+            unsigned long long k1 = ku_, k2 = kl_;
+            int i1 = iu_, i2 = il_;
             warp_min_ki(k1, i1);
             warp_min_ki(k2, i2);
             if (lane == 0) {
                 sh.wkup[warp] = k1; sh.wiup[warp] = i1;
                 sh.wklow[warp] = k2; sh.wilow[warp] = i2;
             }
-            if (i1 != INT_MAX && biu == i1) sh.wup[warp] = make_side(bru);
-            if (i2 != INT_MAX && bil == i2) sh.wlow[warp] = make_side(brl);
-        }
-        __syncthreads();
+            if (i1 != INT_MAX && iu_ == i1) {
+                Side sd = make_side(ru_);
+                if (gx) sd.f = gneg;
+                sh.wup[warp] = sd;
+            }
+            if (i2 != INT_MAX && il_ == i2) sh.wlow[warp] = make_side(rl_);
+            __syncthreads();
+        };
+        cta_reduce(false, bku, biu, bru, bkl, bil, brl, 0.0);
         // ---- 5. compaction of the active list on shrink steps
         if (shrink_now) {
             int kept = 0;
@@ -1037,220 +1049,227 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             cnt = kept;
         }
         if (timed && tid == 0) { uint64_t t = clock64(); ph[2] += t - tp; tp = t; }
-        // ---- 4. grid-wide exchange. One cluster over the whole grid: each
-        //         CTA writes its candidate into every CTA's shared memory and
-        //         arrives on that CTA's mbarrier; every CTA reduces the same
-        //         candidates in the same order. Several clusters: the CTAs of a
-        //         cluster hand their candidates to its first CTA through
-        //         distributed shared memory; only those leaders exchange
-        //         through global memory (release/acquire flags, bounded
-        //         waits) and push the result back to their cluster.
-        ++epoch;
-        const int par = (int)(epoch & 1);
-        if (warp == 0) {
-            unsigned long long k1 = lane < kWarps ? sh.wkup[lane] : kNoKey;
-            unsigned long long k2 = lane < kWarps ? sh.wklow[lane] : kNoKey;
-            int i1 = lane < kWarps ? sh.wiup[lane] : INT_MAX;
-            int i2 = lane < kWarps ? sh.wilow[lane] : INT_MAX;
-            const unsigned long long k1s = k1, k2s = k2;
-            const int i1s = i1, i2s = i2;
-            warp_min_ki(k1, i1);
-            warp_min_ki(k2, i2);
-            const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
-            const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
-            if constexpr (solo) {
-                // lane q sends the CTA's candidate to CTA q: the winning
-                // warps' sides straight from shared memory, then the count
-                if (lane < csize) {
-                    const uint32_t dst = cluster_addr(smem_u32(&sh.xc[par][crank]), lane);
-                    const uint32_t rbar = cluster_addr(smem_u32(&sh.xbar[par]), lane);
-                    const uint4 *su = reinterpret_cast<const uint4 *>(mu ? &sh.wup[__ffs(mu) - 1] : &sh.none[0]);
-                    const uint4 *sl = reinterpret_cast<const uint4 *>(ml ? &sh.wlow[__ffs(ml) - 1] : &sh.none[1]);
-                    constexpr int kSideV = (int)(sizeof(Side) / 16);
-#pragma unroll
-                    for (int j = 0; j < kSideV; ++j) st_async_v4(dst + 16 * j, su[j], rbar);
-#pragma unroll
-                    for (int j = 0; j < kSideV; ++j) st_async_v4(dst + (uint32_t)sizeof(Side) + 16 * j, sl[j], rbar);
-                    st_async_v4(dst + (uint32_t)offsetof(CandFull, count), make_uint4((unsigned)cnt, 0u, 0u, 0u), rbar);
-                }
-                if (lane == 0)
-                    mbar_arrive_expect_tx(smem_u32(&sh.xbar[par]), (uint32_t)(csize * sizeof(CandFull)));
-            } else if (lane == 0) {
-                CandFull cf;
-                if (mu) cf.up = sh.wup[__ffs(mu) - 1]; else side_empty(cf.up, true);
-                if (ml) cf.low = sh.wlow[__ffs(ml) - 1]; else side_empty(cf.low, false);
-                cf.count = cnt;
-                cf.pad[0] = cf.pad[1] = cf.pad[2] = 0;
-                CandFull *dst = cluster.map_shared_rank(sh.ccand, 0);
-                dst[crank] = cf;
-            }
-            if (lane == 0) {
-                if (busy_on) busy += clock64() - cta_t0;
-                if (timed) { uint64_t t = clock64(); ph[3] += t - tp; tp = t; }
-            }
-        }
-        // the previous step's target rows are cleared while others wait
-        if (!BITS && prev_valid && warp >= 8) {
-            Tgt *P = tbuf + (size_t)(1 - buf) * d;
-            const int *pcu = tcol + (size_t)((1 - buf) * 2 + 0) * maxnnz;
-            const int *pcl = tcol + (size_t)((1 - buf) * 2 + 1) * maxnnz;
-            for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) tgt_clear<MODE>(P[pcu[k]]);
-            for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) tgt_clear<MODE>(P[pcl[k]]);
-        }
-        if constexpr (solo) {
+        auto exchange = [&](bool gx) {
+            // ---- 4. grid-wide exchange. One cluster over the whole grid: each
+            //         CTA writes its candidate into every CTA's shared memory and
+            //         arrives on that CTA's mbarrier; every CTA reduces the same
+            //         candidates in the same order. Several clusters: the CTAs of a
+            //         cluster hand their candidates to its first CTA through
+            //         distributed shared memory; only those leaders exchange
+            //         through global memory (release/acquire flags, bounded
+            //         waits) and push the result back to their cluster.
+            ++epoch;
+            const int par = (int)(epoch & 1);
+            const int phs = gx ? 7 : 3;
             if (warp == 0) {
-                // this epoch's csize candidates; the k-th use of a barrier
-                // completes its phase of parity k & 1
-                const uint32_t bar = smem_u32(&sh.xbar[par]);
-                const uint32_t parity = (uint32_t)((epoch - 1) >> 1) & 1u;
-                int timed_out = 0, spins = 0;
-                uint64_t t0 = 0;
-                while (!mbar_try_wait_cluster(bar, parity)) {
-                    if (++spins >= 64) {
-                        spins = 0;
-                        const uint64_t now = global_ns();
-                        if (t0 == 0) t0 = now;
-                        else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
-                        if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
-                    }
-                }
-                timed_out = __any_sync(0xffffffffu, timed_out);
-                if (timed_out && lane == 0) atomicExch(&A.ctrl->err, 1);
-                unsigned long long k1 = kNoKey, k2 = kNoKey;
-                int i1 = INT_MAX, i2 = INT_MAX;
-                long long cc = 0;
-                if (lane < csize && !timed_out) cand_keys(sh.xc[par][lane], k1, i1, k2, i2, cc);
+                unsigned long long k1 = lane < kWarps ? sh.wkup[lane] : kNoKey;
+                unsigned long long k2 = lane < kWarps ? sh.wklow[lane] : kNoKey;
+                int i1 = lane < kWarps ? sh.wiup[lane] : INT_MAX;
+                int i2 = lane < kWarps ? sh.wilow[lane] : INT_MAX;
                 const unsigned long long k1s = k1, k2s = k2;
                 const int i1s = i1, i2s = i2;
                 warp_min_ki(k1, i1);
                 warp_min_ki(k2, i2);
-#pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
                 const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                 const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
-                // the winning sides into the result, one 8-byte word per lane
-                const Side *wsu = mu ? &sh.xc[par][__ffs(mu) - 1].up : &sh.none[0];
-                const Side *wsl = ml ? &sh.xc[par][__ffs(ml) - 1].low : &sh.none[1];
-                constexpr int kSideW = (int)(sizeof(Side) / 8);
-                static_assert(2 * kSideW <= 32, "a side is copied by one warp");
-                if (lane < 2 * kSideW) {
-                    const bool u = lane < kSideW;
-                    const int w = u ? lane : lane - kSideW;
-                    reinterpret_cast<unsigned long long *>(u ? &sh.res.up : &sh.res.low)[w] =
-                        reinterpret_cast<const unsigned long long *>(u ? wsu : wsl)[w];
+                if constexpr (solo) {
+                    // lane q sends the CTA's candidate to CTA q: the winning
+                    // warps' sides straight from shared memory, then the count
+                    if (lane < csize) {
+                        const uint32_t dst = cluster_addr(smem_u32(&sh.xc[par][crank]), lane);
+                        const uint32_t rbar = cluster_addr(smem_u32(&sh.xbar[par]), lane);
+                        const uint4 *su = reinterpret_cast<const uint4 *>(mu ? &sh.wup[__ffs(mu) - 1] : &sh.none[0]);
+                        const uint4 *sl = reinterpret_cast<const uint4 *>(ml ? &sh.wlow[__ffs(ml) - 1] : &sh.none[1]);
+                        constexpr int kSideV = (int)(sizeof(Side) / 16);
+    #pragma unroll
+                        for (int j = 0; j < kSideV; ++j) st_async_v4(dst + 16 * j, su[j], rbar);
+    #pragma unroll
+                        for (int j = 0; j < kSideV; ++j) st_async_v4(dst + (uint32_t)sizeof(Side) + 16 * j, sl[j], rbar);
+                        st_async_v4(dst + (uint32_t)offsetof(CandFull, count), make_uint4((unsigned)cnt, 0u, 0u, 0u), rbar);
+                    }
+                    if (lane == 0)
+                        mbar_arrive_expect_tx(smem_u32(&sh.xbar[par]), (uint32_t)(csize * sizeof(CandFull)));
+                } else if (lane == 0) {
+                    CandFull cf;
+                    if (mu) cf.up = sh.wup[__ffs(mu) - 1]; else side_empty(cf.up, true);
+                    if (ml) cf.low = sh.wlow[__ffs(ml) - 1]; else side_empty(cf.low, false);
+                    cf.count = cnt;
+                    cf.pad[0] = cf.pad[1] = cf.pad[2] = 0;
+                    CandFull *dst = cluster.map_shared_rank(sh.ccand, 0);
+                    dst[crank] = cf;
                 }
                 if (lane == 0) {
-                    sh.res.total = cc;
-                    sh.res.flag = timed_out;
-                    sh.res.gap_open = dless(A.thr, wsl->f - wsu->f);
+                    if (busy_on) busy += clock64() - cta_t0;
+                    if (timed) { uint64_t t = clock64(); ph[phs] += t - tp; tp = t; }
                 }
             }
-            __syncthreads();
-        } else {
-            cluster.sync();
-            const int rwarps = (nlead + 31) / 32;
-            if (crank == 0) {
+            // the previous step's target rows are cleared while others wait
+            if (!BITS && !gx && prev_valid && warp >= 8) {
+                Tgt *P = tbuf + (size_t)(1 - buf) * d;
+                const int *pcu = tcol + (size_t)((1 - buf) * 2 + 0) * maxnnz;
+                const int *pcl = tcol + (size_t)((1 - buf) * 2 + 1) * maxnnz;
+                for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) tgt_clear<MODE>(P[pcu[k]]);
+                for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) tgt_clear<MODE>(P[pcl[k]]);
+            }
+            if constexpr (solo) {
                 if (warp == 0) {
-                    // cluster winner -> this leader's global slot
+                    // this epoch's csize candidates; the k-th use of a barrier
+                    // completes its phase of parity k & 1
+                    const uint32_t bar = smem_u32(&sh.xbar[par]);
+                    const uint32_t parity = (uint32_t)((epoch - 1) >> 1) & 1u;
+                    int timed_out = 0, spins = 0;
+                    uint64_t t0 = 0;
+                    while (!mbar_try_wait_cluster(bar, parity)) {
+                        if (++spins >= 64) {
+                            spins = 0;
+                            const uint64_t now = global_ns();
+                            if (t0 == 0) t0 = now;
+                            else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
+                            if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+                        }
+                    }
+                    timed_out = __any_sync(0xffffffffu, timed_out);
+                    if (timed_out && lane == 0) atomicExch(&A.ctrl->err, 1);
                     unsigned long long k1 = kNoKey, k2 = kNoKey;
                     int i1 = INT_MAX, i2 = INT_MAX;
                     long long cc = 0;
-                    if (lane < csize) cand_keys(sh.ccand[lane], k1, i1, k2, i2, cc);
+                    if (lane < csize && !timed_out) cand_keys(sh.xc[par][lane], k1, i1, k2, i2, cc);
+                    if (gx) { k2 = k1; i2 = i1; }   // the gain winner's row on both sides
                     const unsigned long long k1s = k1, k2s = k2;
                     const int i1s = i1, i2s = i2;
                     warp_min_ki(k1, i1);
                     warp_min_ki(k2, i2);
-#pragma unroll
+    #pragma unroll
                     for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
                     const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                     const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
+                    // the winning sides into the result, one 8-byte word per lane
+                    const Side *wsu = mu ? &sh.xc[par][__ffs(mu) - 1].up : &sh.none[0];
+                    const Side *wsl = ml ? &sh.xc[par][__ffs(ml) - 1].low : &sh.none[1];
+                    constexpr int kSideW = (int)(sizeof(Side) / 8);
+                    static_assert(2 * kSideW <= 32, "a side is copied by one warp");
+                    if (lane < 2 * kSideW) {
+                        const bool u = lane < kSideW;
+                        const int w = u ? lane : lane - kSideW;
+                        reinterpret_cast<unsigned long long *>(u ? &sh.res.up : &sh.res.low)[w] =
+                            reinterpret_cast<const unsigned long long *>(u ? wsu : wsl)[w];
+                    }
                     if (lane == 0) {
-                        CandFull *out = reinterpret_cast<CandFull *>(static_cast<unsigned char *>(A.cand) +
-                                                                     ((size_t)par * nlead + cid) * kCandStride);
-                        if (mu) copy_side(&out->up, &sh.ccand[__ffs(mu) - 1].up);
-                        else { Side e; side_empty(e, true); copy_side(&out->up, &e); }
-                        if (ml) copy_side(&out->low, &sh.ccand[__ffs(ml) - 1].low);
-                        else { Side e; side_empty(e, false); copy_side(&out->low, &e); }
-                        out->count = (int32_t)cc;
-                        st_release_u32(A.seq + ((size_t)par * nlead + cid) * kSeqStride, epoch);
+                        sh.res.total = cc;
+                        sh.res.flag = timed_out;
+                        sh.res.gap_open = dless(A.thr, wsl->f - wsu->f);
                     }
-                }
-                if (warp < rwarps) {
-                    const int c = warp * 32 + lane;
-                    int ai = INT_MAX, bi = INT_MAX;
-                    double af = 0.0, bf = 0.0;
-                    const CandFull *gp = nullptr;
-                    long long cc = 0;
-                    int timed_out = 0;
-                    if (c < nlead) {
-                        const unsigned *sp = A.seq + ((size_t)par * nlead + c) * kSeqStride;
-                        uint64_t t0 = 0;
-                        int spins = 0;
-                        while (ld_relaxed_u32(sp) < epoch) {
-                            if (++spins >= 256) {
-                                spins = 0;
-                                uint64_t now = global_ns();
-                                if (t0 == 0) t0 = now;
-                                else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
-                                if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
-                            }
-                        }
-                        if (!timed_out) {
-                            fence_acq_rel_gpu();   // acquire: the slot written before the flag
-                            // L2 reads (bypass L1, which is not coherent across SMs);
-                            // the winners' full sides are copied below
-                            gp = reinterpret_cast<const CandFull *>(static_cast<const unsigned char *>(A.cand) +
-                                                                    ((size_t)par * nlead + c) * kCandStride);
-                            ai = __ldcg(&gp->up.i);
-                            bi = __ldcg(&gp->low.i);
-                            af = __ldcg(&gp->up.f);
-                            bf = __ldcg(&gp->low.f);
-                            cc = __ldcg(&gp->count);
-                        }
-                    }
-                    const int any_to = __any_sync(0xffffffffu, timed_out);
-                    if (any_to && lane == 0) atomicExch(&A.ctrl->err, 1);
-                    unsigned long long k1 = ai == INT_MAX ? kNoKey : key_up(af);
-                    unsigned long long k2 = bi == INT_MAX ? kNoKey : key_low(bf);
-                    int i1 = ai, i2 = bi;
-                    warp_min_ki(k1, i1);
-                    warp_min_ki(k2, i2);
-#pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
-                    if (lane == 0) {
-                        sh.rkup[warp] = k1; sh.riup[warp] = i1;
-                        sh.rklow[warp] = k2; sh.rilow[warp] = i2;
-                        sh.rcount[warp] = cc;
-                        sh.rto[warp] = any_to;
-                    }
-                    if (i1 != INT_MAX && ai == i1) copy_side_ldcg(&sh.rup[warp], &gp->up);
-                    if (i2 != INT_MAX && bi == i2) copy_side_ldcg(&sh.rlow[warp], &gp->low);
                 }
                 __syncthreads();
-                if (warp == 0) {
-                    // final winner, pushed to every CTA of the cluster
-                    unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
-                    int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0, to = sh.rto[0];
-                    long long cc = sh.rcount[0];
-                    for (int w = 1; w < rwarps; ++w) {
-                        if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
-                        if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
-                        cc += sh.rcount[w];
-                        to |= sh.rto[w];
+            } else {
+                cluster.sync();
+                const int rwarps = (nlead + 31) / 32;
+                if (crank == 0) {
+                    if (warp == 0) {
+                        // cluster winner -> this leader's global slot
+                        unsigned long long k1 = kNoKey, k2 = kNoKey;
+                        int i1 = INT_MAX, i2 = INT_MAX;
+                        long long cc = 0;
+                        if (lane < csize) cand_keys(sh.ccand[lane], k1, i1, k2, i2, cc);
+                        if (gx) { k2 = k1; i2 = i1; }
+                        const unsigned long long k1s = k1, k2s = k2;
+                        const int i1s = i1, i2s = i2;
+                        warp_min_ki(k1, i1);
+                        warp_min_ki(k2, i2);
+    #pragma unroll
+                        for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
+                        const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
+                        const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
+                        if (lane == 0) {
+                            CandFull *out = reinterpret_cast<CandFull *>(static_cast<unsigned char *>(A.cand) +
+                                                                         ((size_t)par * nlead + cid) * kCandStride);
+                            if (mu) copy_side(&out->up, &sh.ccand[__ffs(mu) - 1].up);
+                            else { Side e; side_empty(e, true); copy_side(&out->up, &e); }
+                            if (ml) copy_side(&out->low, &sh.ccand[__ffs(ml) - 1].low);
+                            else { Side e; side_empty(e, false); copy_side(&out->low, &e); }
+                            out->count = (int32_t)cc;
+                            st_release_u32(A.seq + ((size_t)par * nlead + cid) * kSeqStride, epoch);
+                        }
                     }
-                    if (lane == 0) {
-                        if (iu != INT_MAX) copy_side(&sh.res.up, &sh.rup[wu]); else side_empty(sh.res.up, true);
-                        if (il != INT_MAX) copy_side(&sh.res.low, &sh.rlow[wl]); else side_empty(sh.res.low, false);
-                        sh.res.total = cc;
-                        sh.res.flag = to;
-                        sh.res.gap_open = dless(A.thr, sh.res.low.f - sh.res.up.f);
+                    if (warp < rwarps) {
+                        const int c = warp * 32 + lane;
+                        int ai = INT_MAX, bi = INT_MAX;
+                        double af = 0.0, bf = 0.0;
+                        const CandFull *gp = nullptr;
+                        long long cc = 0;
+                        int timed_out = 0;
+                        if (c < nlead) {
+                            const unsigned *sp = A.seq + ((size_t)par * nlead + c) * kSeqStride;
+                            uint64_t t0 = 0;
+                            int spins = 0;
+                            while (ld_relaxed_u32(sp) < epoch) {
+                                if (++spins >= 256) {
+                                    spins = 0;
+                                    uint64_t now = global_ns();
+                                    if (t0 == 0) t0 = now;
+                                    else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
+                                    if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+                                }
+                            }
+                            if (!timed_out) {
+                                fence_acq_rel_gpu();   // acquire: the slot written before the flag
+                                // L2 reads (bypass L1, which is not coherent across SMs);
+                                // the winners' full sides are copied below
+                                gp = reinterpret_cast<const CandFull *>(static_cast<const unsigned char *>(A.cand) +
+                                                                        ((size_t)par * nlead + c) * kCandStride);
+                                ai = __ldcg(&gp->up.i);
+                                bi = __ldcg(&gp->low.i);
+                                af = __ldcg(&gp->up.f);
+                                bf = __ldcg(&gp->low.f);
+                                cc = __ldcg(&gp->count);
+                            }
+                        }
+                        const int any_to = __any_sync(0xffffffffu, timed_out);
+                        if (any_to && lane == 0) atomicExch(&A.ctrl->err, 1);
+                        unsigned long long k1 = ai == INT_MAX ? kNoKey : key_up(af);
+                        unsigned long long k2 = bi == INT_MAX ? kNoKey : key_low(bf);
+                        int i1 = ai, i2 = bi;
+                        if (gx) { k2 = k1; i2 = i1; }
+                        warp_min_ki(k1, i1);
+                        warp_min_ki(k2, i2);
+    #pragma unroll
+                        for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
+                        if (lane == 0) {
+                            sh.rkup[warp] = k1; sh.riup[warp] = i1;
+                            sh.rklow[warp] = k2; sh.rilow[warp] = i2;
+                            sh.rcount[warp] = cc;
+                            sh.rto[warp] = any_to;
+                        }
+                        if (i1 != INT_MAX && ai == i1) copy_side_ldcg(&sh.rup[warp], &gp->up);
+                        if (i2 != INT_MAX && bi == i2) copy_side_ldcg(&sh.rlow[warp], &gp->low);
                     }
-                    __syncwarp();
-                    if (lane > 0 && lane < csize) copy_result(cluster.map_shared_rank(&sh.res, lane), &sh.res);
+                    __syncthreads();
+                    if (warp == 0) {
+                        // final winner, pushed to every CTA of the cluster
+                        unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
+                        int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0, to = sh.rto[0];
+                        long long cc = sh.rcount[0];
+                        for (int w = 1; w < rwarps; ++w) {
+                            if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
+                            if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
+                            cc += sh.rcount[w];
+                            to |= sh.rto[w];
+                        }
+                        if (lane == 0) {
+                            if (iu != INT_MAX) copy_side(&sh.res.up, &sh.rup[wu]); else side_empty(sh.res.up, true);
+                            if (il != INT_MAX) copy_side(&sh.res.low, &sh.rlow[wl]); else side_empty(sh.res.low, false);
+                            sh.res.total = cc;
+                            sh.res.flag = to;
+                            sh.res.gap_open = dless(A.thr, sh.res.low.f - sh.res.up.f);
+                        }
+                        __syncwarp();
+                        if (lane > 0 && lane < csize) copy_result(cluster.map_shared_rank(&sh.res, lane), &sh.res);
+                    }
                 }
+                cluster.sync();
             }
-            cluster.sync();
-        }
+        };
+        exchange(false);
         if (timed && tid == 0) { uint64_t t = clock64(); ph[4] += t - tp; tp = t; }
         if (sh.res.flag) break;
         prev_valid = first ? 0 : 1;
@@ -1269,6 +1288,126 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             }
         }
         first = false;
+        if constexpr (WSS) {
+            // ---- 6. second-order choice of x_low (the paper's future work,
+            //         Section VI): over the active rows t of I_low with
+            //         f_t > f_up, the largest gain (f_t - f_up)^2 / eta_ut,
+            //         eta_ut = K_uu + K_tt - 2 K_ut (1e-12 when not positive),
+            //         lowest index on ties; the first-order b_low stays the
+            //         stopping test's and the shrink rule's. Runs only when
+            //         another step follows.
+            beta_low = low.f;
+            if (gap_open && iter < A.iter_limit) {
+                unsigned long long gk = kNoKey;   // dkey(-gain): larger gain, smaller key
+                int gi = INT_MAX, gr = 0;
+                double gneg = 0.0;
+                auto consider = [&](double ft, double eta, int i, int r) {
+                    const double b = ft - up.f;
+                    const double a = dless(0.0, eta) ? eta : 1e-12;
+                    const double g = __ddiv_rn(__dmul_rn(b, b), a);
+                    const double ng = neg_if(g, true);
+                    const unsigned long long key = dkey(ng);
+                    // rows met in increasing index order: strict test keeps the lowest
+                    if (key < gk) { gk = key; gi = i; gr = r; gneg = ng; }
+                };
+                const unsigned long long kfu = dkey(up.f);
+                if constexpr (BITS) {
+                    for (int k = tid; k < cnt; k += kThreads) {
+                        const int r = ACT(k);
+                        const uint8_t sb = GETST(r);
+                        const double ft = GETF(r);
+                        if (!st_low(set_bits(sb)) || !(kfu < dkey(ft))) continue;
+                        const uint4 *rb = RES ? bits_s + (size_t)r * W4 : bits_g + (size_t)(lo + r) * W4;
+                        int dist = 0;
+#pragma unroll
+                        for (int q = 0; q < W4; ++q) {
+                            const uint4 v = RES ? rb[q] : __ldg(rb + q);
+                            dist += __popc(v.x ^ up.m[4 * q]) + __popc(v.y ^ up.m[4 * q + 1]) +
+                                    __popc(v.z ^ up.m[4 * q + 2]) + __popc(v.w ^ up.m[4 * q + 3]);
+                        }
+                        consider(ft, etab[dist], (int)(lo + r), r);
+                    }
+                } else {
+                    // x_up into the next step's (clean) target buffer, as the
+                    // next step's own fill will write it
+                    Tgt *Tn = tbuf + (size_t)(iter & 1) * d;
+                    for (int k = tid; k < up.len; k += kThreads) {
+                        const int c = A.indices[up.p0 + k];
+                        if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(Tn + c)[0] = 1;
+                        else if constexpr (MODE == MODE_FP64) Tn[c].x = (double)A.values[up.p0 + k];
+                        else Tn[c].x = A.vmix[up.p0 + k];
+                    }
+                    __syncthreads();
+                    double kuu = 0.0;   // K(x_up, x_up) of a non-RBF kernel
+                    if (A.kernel != KERNEL_RBF) {
+                        if constexpr (MODE == MODE_FP64)
+                            kuu = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, up.nrm);
+                        else if constexpr (MODE == MODE_MIXED)
+                            kuu = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)up.nrm);
+                    }
+                    constexpr int RPW = 32 / LPR;
+                    const int gl = lane & (LPR - 1);
+                    const int gw = lane / LPR;
+                    for (int kb = warp * RPW; kb < cnt; kb += kWarps * RPW) {   // warp-uniform
+                        const int k = kb + gw;
+                        int r = 0;
+                        int64_t p0 = 0, p1 = 0;
+                        double ft = 0.0;
+                        bool cand = false;
+                        if (k < cnt) {
+                            r = ACT(k);
+                            const uint8_t sb = GETST(r);
+                            ft = GETF(r);
+                            cand = st_low(set_bits(sb)) && kfu < dkey(ft);
+                            if (cand) ROWP(r, p0, p1);
+                        }
+                        Acc su = 0;
+                        for (int64_t p = p0 + gl; p < p1; p += LPR) {
+                            const int c = COL(p);
+                            if constexpr (MODE == MODE_BINARY) su += (int)(Tn[c] & 0xff);
+                            else if constexpr (MODE == MODE_FP64) su = fma((double)VAL(p), Tn[c].x, su);
+                            else su = fmaf(VAL(p), Tn[c].x, su);
+                        }
+#pragma unroll
+                        for (int off = LPR / 2; off >= 1; off >>= 1) su += __shfl_xor_sync(0xffffffffu, su, off);
+                        if (cand && gl == 0) {
+                            double eta;
+                            if constexpr (MODE == MODE_BINARY) {
+                                int dist = up.len + (int)(p1 - p0) - 2 * su;
+                                eta = etab[dist < 0 ? 0 : dist];
+                            } else if (A.kernel == KERNEL_RBF) {
+                                double kut;
+                                if constexpr (MODE == MODE_FP64) {
+                                    const double d2 = up.nrm + NRM(r) - 2.0 * su;
+                                    kut = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                                } else {
+                                    const float d2 = (float)up.nrm + (float)NRM(r) - 2.0f * su;
+                                    kut = (double)__expf(-gammaf * fmaxf(d2, 0.f));
+                                }
+                                eta = 2.0 - 2.0 * kut;   // K(x,x) = 1
+                            } else {
+                                double kut, ktt;
+                                if constexpr (MODE == MODE_FP64) {
+                                    kut = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, (double)su);
+                                    ktt = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, NRM(r));
+                                } else {
+                                    const float c0 = (float)A.coef0;
+                                    kut = (double)kernel_of_dot(A.kernel, gammaf, c0, A.degree, (float)su);
+                                    ktt = (double)kernel_of_dot(A.kernel, gammaf, c0, A.degree, (float)NRM(r));
+                                }
+                                eta = __dsub_rn(__dadd_rn(kuu, ktt), __dmul_rn(2.0, kut));
+                            }
+                            consider(ft, eta, (int)(lo + r), r);
+                        }
+                    }
+                }
+                cta_reduce(true, gk, gi, gr, gk, gi, gr, gneg);
+                exchange(true);
+                if (timed && tid == 0) { uint64_t t = clock64(); ph[7] += t - tp; tp = t; }
+                if (sh.res.flag) break;
+                low = sh.res.low;
+            }
+        }
         if (cta == 0 && tid == 0 && iter < A.trace_len) {
             A.trace[2 * iter] = up.i == INT_MAX ? -1 : up.i;
             A.trace[2 * iter + 1] = low.i == INT_MAX ? -1 : low.i;
@@ -1308,19 +1447,19 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     }
 }
 
-template <int MODE, bool RES, bool SOLO>
+template <int MODE, bool RES, bool SOLO, bool WSS>
 void *kernel_for(int lpr)
 {
     if constexpr (mode_bits(MODE)) {
-        return lpr == 1 ? (void *)smo_persistent_kernel<MODE, 1, RES, SOLO> : nullptr;
+        return lpr == 1 ? (void *)smo_persistent_kernel<MODE, 1, RES, SOLO, WSS> : nullptr;
     } else {
         switch (lpr) {
-        case 1: return (void *)smo_persistent_kernel<MODE, 1, RES, SOLO>;
-        case 2: return (void *)smo_persistent_kernel<MODE, 2, RES, SOLO>;
-        case 4: return (void *)smo_persistent_kernel<MODE, 4, RES, SOLO>;
-        case 8: return (void *)smo_persistent_kernel<MODE, 8, RES, SOLO>;
-        case 16: return (void *)smo_persistent_kernel<MODE, 16, RES, SOLO>;
-        case 32: return (void *)smo_persistent_kernel<MODE, 32, RES, SOLO>;
+        case 1: return (void *)smo_persistent_kernel<MODE, 1, RES, SOLO, WSS>;
+        case 2: return (void *)smo_persistent_kernel<MODE, 2, RES, SOLO, WSS>;
+        case 4: return (void *)smo_persistent_kernel<MODE, 4, RES, SOLO, WSS>;
+        case 8: return (void *)smo_persistent_kernel<MODE, 8, RES, SOLO, WSS>;
+        case 16: return (void *)smo_persistent_kernel<MODE, 16, RES, SOLO, WSS>;
+        case 32: return (void *)smo_persistent_kernel<MODE, 32, RES, SOLO, WSS>;
         default: return nullptr;
         }
     }
@@ -1328,17 +1467,21 @@ void *kernel_for(int lpr)
 
 // resident: 0 streamed segments, 1 on-chip segments, 2 on-chip segments in
 // one cluster over the whole grid
-template <int MODE>
+template <int MODE, bool WSS = false>
 void *kernel_pick(int lpr, int resident)
 {
-    if (resident == 0) return kernel_for<MODE, false, false>(lpr);
-    return resident == 2 ? kernel_for<MODE, true, true>(lpr) : kernel_for<MODE, true, false>(lpr);
+    if (resident == 0) return kernel_for<MODE, false, false, WSS>(lpr);
+    return resident == 2 ? kernel_for<MODE, true, true, WSS>(lpr) : kernel_for<MODE, true, false, WSS>(lpr);
 }
+
+// second-order instantiations, compiled in translation units of their own
+void *smo_kernel_wss(int mode, int lpr, int resident);
 
 template <int MODE>
 cudaError_t launch_mode(int lpr, const SmoArgs &a, size_t smem, cudaStream_t st, int cs)
 {
-    void *fn = kernel_pick<MODE>(lpr, a.resident ? (a.G == cs ? 2 : 1) : 0);
+    const int res = a.resident ? (a.G == cs ? 2 : 1) : 0;
+    void *fn = a.wss2 ? smo_kernel_wss(MODE, lpr, res) : kernel_pick<MODE>(lpr, res);
     if (!fn) return cudaErrorInvalidValue;
     if (cs < 1 || a.G % cs != 0 || a.G / cs > 256 || cs > kMaxCluster) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -733,6 +733,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.C = P->C;
     A.gamma = P->gamma;
     A.phase_times = (P->flags & SVM_FLAG_PHASE_TIMES) != 0;
+    A.wss2 = (P->flags & SVM_FLAG_WSS2) != 0;
     A.kernel = P->kernel;
     A.degree = P->degree;
     A.coef0 = P->coef0;
@@ -1832,6 +1833,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     A.iter_limit = P->max_iter > 0 ? P->max_iter : 100 * n + 1000000;
     A.h = 0;
     A.select_only = 1;
+    A.wss2 = (P->flags & SVM_FLAG_WSS2) != 0;
     A.timeout_ns = 10ll * 1000 * 1000 * 1000;
     // every call starts from a zeroed exchange area and a fresh control block
     CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));

@@ -127,6 +127,7 @@ struct SmoArgs {
     int32_t kc_direct;
     int32_t kernel, degree;    // kernel kind (KERNEL_*); polynomial degree
     double coef0;              // polynomial / sigmoid offset
+    int32_t wss2;              // i_low by the second-order gain (its own kernel instantiation)
 };
 
 // ---- batched and served solves: one job = one two-class problem

@@ -19,11 +19,11 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU container
     pytest.skip("needs a GPU", allow_module_level=True)
 
 
-def _both(p):
+def _both(p, flags=0):
     Xd = pkg.to_device(p.X)
     yd = torch.as_tensor(p.y, device="cuda")
-    ref = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau)
-    fix = pkg.svm_train_fixed_workspace(Xd, yd, p.C, p.gamma, p.tau)
+    ref = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, flags=flags)
+    fix = pkg.svm_train_fixed_workspace(Xd, yd, p.C, p.gamma, p.tau, flags=flags)
     return ref, fix
 
 
@@ -52,6 +52,13 @@ def test_two_calls_in_a_row_match_svm_train():
     # and the first problem again after the second
     r3, f3 = _both(p1)
     _check(p1, r3, f3)
+
+
+def test_second_order_selection_matches_svm_train():
+    for p in (synth.gaussian_mixture(n=1500, n_test=0, seed=31), synth.onehot_sparse(n=3000, n_test=0, seed=32)):
+        r, f = _both(p, flags=pkg.SVM_FLAG_WSS2)
+        _check(p, r, f)
+        assert f["iters"] == r["iters"]
 
 
 def test_limit_is_reported():
