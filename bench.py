@@ -62,6 +62,9 @@ def parse():
                          "(405 jobs) batched vs one job at a time")
     ap.add_argument("--plain-sample", type=int, default=27,
                     help="batch workload: jobs trained one at a time for the comparison")
+    ap.add_argument("--wss2", action="store_true",
+                    help="onehot / covtype: choose i_low by the second-order gain "
+                         "(SVM_FLAG_WSS2) instead of the first-order rule")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap SMO steps per solve (profiling of small cases; not a bench value)")
     return ap.parse_args()
@@ -244,6 +247,7 @@ def run_gb300(args, rank, world, local):
     pkg.load()
     p = workload()
     policy = pkg.POLICIES[args.policy]
+    flags = pkg.SVM_FLAG_WSS2 if args.wss2 else 0
     Xd = pkg.to_device(p.X)
     yd = torch.as_tensor(p.y, device="cuda")
     Zd = pkg.to_device(p.Z)
@@ -252,7 +256,7 @@ def run_gb300(args, rank, world, local):
 
     def step():
         r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream,
-                          max_iter=args.max_iter)
+                          max_iter=args.max_iter, flags=flags)
         dz = pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
         return r, dz
 
@@ -276,7 +280,7 @@ def run_gb300(args, rank, world, local):
         flush.zero_()                    # L2 flushed between timed steps
         e0[k].record(stream)
         r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream,
-                          max_iter=args.max_iter)
+                          max_iter=args.max_iter, flags=flags)
         e1[k].record(stream)
         pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
         e2[k].record(stream)
@@ -317,7 +321,7 @@ def run_gb300(args, rank, world, local):
         n_e2e = max(1, min(3, args.steps))
         for _ in range(n_e2e):
             r = pkg.svm_train(Xh, yh, p.C, p.gamma, p.tau, shrink=policy, alpha_out=alpha_h,
-                              max_iter=args.max_iter)
+                              max_iter=args.max_iter, flags=flags)
             pkg.svm_decision(Xh, yh, alpha_h, r["b"], p.gamma, Zh, out=out_h)
             e2e_iters += r["iters"]
         dt, e2e_all = job_totals(dist, time.perf_counter() - t0, float(e2e_iters), "cuda")
@@ -360,6 +364,8 @@ def run_gb300(args, rank, world, local):
             "clocks": clk, "roofline": roofline, "e2e": e2e}
     if args.max_iter:
         line["config"]["max_iter"] = args.max_iter
+    if args.wss2:
+        line["config"]["selection"] = "second-order i_low (SVM_FLAG_WSS2)"
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)
@@ -451,10 +457,12 @@ def run_covtype(args):
     yd = torch.as_tensor(p.y, device="cuda")
     policy = pkg.POLICIES[args.policy]
     prec = pkg.SVM_MIXED_BF16
+    flags = pkg.SVM_FLAG_WSS2 if args.wss2 else 0
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 1)):
-        pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream)
+        pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream,
+                      flags=flags)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -465,7 +473,8 @@ def run_covtype(args):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream)
+        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream,
+                          flags=flags)
         e1.record(stream)
         ev.append((e0, e1))
         s = r["stats"]
@@ -496,6 +505,8 @@ def run_covtype(args):
                          "peak_source": f"{kind} hbm_gbs (burst copy)", "bytes_per_row_visit": b_row,
                          "row_visits_per_step": visits / args.steps,
                          "kernel_ms_per_step": ms_smo / args.steps}}
+    if args.wss2:
+        line["config"]["selection"] = "second-order i_low (SVM_FLAG_WSS2)"
     print(json.dumps(line), flush=True)
     return 0
 
