@@ -798,6 +798,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             KT *kc_ru = kc_step ? static_cast<KT *>(A.kc) + (size_t)sh.kc_su * A.kc_ld : nullptr;
             KT *kc_rl = kc_step ? static_cast<KT *>(A.kc) + (size_t)sh.kc_sl * A.kc_ld : nullptr;
             const bool skip_sums = kc_hu && kc_hl;
+            // streamed segment with no row shrunk: its active list is the
+            // identity (lists are reset to it and compacted in order), so the
+            // row index needs no load
+            const bool ident = !RES && cnt == nseg;
             double du = 0.0, dl = 0.0, au_new = 0.0, al_new = 0.0;
             unsigned char st_u = 0, st_l = 0;
             bool have_step = first;
@@ -810,12 +814,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 int64_t p0 = 0, p1 = 0;
                 double fi = 0.0;
                 uint8_t sb = 0;
+                double nr = 0.0;
                 if (valid) {
-                    r = ACT(k);
+                    r = ident ? k : ACT(k);
                     if constexpr (!BITS) ROWP(r, p0, p1);
                     if (gl == 0) {
                         fi = GETF(r);
                         sb = GETST(r);
+                        if constexpr (!RES) nr = NRM(r);   // issued with the row's other loads
                     }
                 }
                 Acc su = 0, sl = 0;
@@ -831,6 +837,42 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             sl += __popc(v.x ^ low.m[4 * q]) + __popc(v.y ^ low.m[4 * q + 1]) +
                                   __popc(v.z ^ low.m[4 * q + 2]) + __popc(v.w ^ low.m[4 * q + 3]);
                         }
+                    }
+                } else if (!RES && !first && !skip_sums) {
+                    // streamed rows: each lane loads its next 8 entries at once
+                    // (one memory round trip per 8 entries, not one per entry)
+                    for (int64_t pb = p0 + gl; pb < p1; pb += 8 * LPR) {
+                        int cb[8];
+                        float vb[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int64_t p = pb + (int64_t)j * LPR;
+                            const bool in = p < p1;
+                            cb[j] = in ? COL(p) : 0;
+                            if constexpr (MODE != MODE_BINARY) vb[j] = in ? VAL(p) : 0.f;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (pb + (int64_t)j * LPR >= p1) break;
+                            if constexpr (MODE == MODE_BINARY) {
+                                unsigned short t = T[cb[j]];
+                                su += (int)(t & 0xff);
+                                sl += (int)(t >> 8);
+                            } else if constexpr (MODE == MODE_FP64) {
+                                double2 t = T[cb[j]];
+                                su = fma((double)vb[j], t.x, su);
+                                sl = fma((double)vb[j], t.y, sl);
+                            } else {
+                                float2 t = T[cb[j]];
+                                su = fmaf(vb[j], t.x, su);
+                                sl = fmaf(vb[j], t.y, sl);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int off = LPR / 2; off >= 1; off >>= 1) {
+                        su += __shfl_xor_sync(0xffffffffu, su, off);
+                        sl += __shfl_xor_sync(0xffffffffu, sl, off);
                     }
                 } else if (!first && !skip_sums) {
                     for (int64_t p = p0 + gl; p < p1; p += LPR) {
@@ -869,6 +911,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         kl = ktab[dl2 < 0 ? 0 : dl2];
                     } else {
                         const int64_t gi = lo + r;
+                        const double nrr = RES ? NRM(r) : nr;
                         if (kc_hu) {
                             ku = (double)kc_ru[gi];
                         } else {
@@ -878,10 +921,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 else
                                     ku = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)su);
                             } else if constexpr (MODE == MODE_FP64) {
-                                const double d2u = up.nrm + NRM(r) - 2.0 * su;
+                                const double d2u = up.nrm + nrr - 2.0 * su;
                                 ku = exp(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
                             } else {
-                                const float d2u = (float)up.nrm + (float)NRM(r) - 2.0f * su;
+                                const float d2u = (float)up.nrm + (float)nrr - 2.0f * su;
                                 ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
                             }
                             if (kc_step) kc_ru[gi] = (KT)ku;
@@ -895,10 +938,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 else
                                     kl = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)sl);
                             } else if constexpr (MODE == MODE_FP64) {
-                                const double d2l = low.nrm + NRM(r) - 2.0 * sl;
+                                const double d2l = low.nrm + nrr - 2.0 * sl;
                                 kl = exp(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
                             } else {
-                                const float d2l = (float)low.nrm + (float)NRM(r) - 2.0f * sl;
+                                const float d2l = (float)low.nrm + (float)nrr - 2.0f * sl;
                                 kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
                             }
                             if (kc_step) kc_rl[gi] = (KT)kl;
