@@ -175,6 +175,13 @@ typedef struct svm_kernel {
  * extremes. Each step adds a sweep over the active rows and a second
  * candidate exchange. svm_train and svm_train_fixed_workspace only. */
 #define SVM_FLAG_WSS2 16
+/* With shrinking, a launch over a problem that is not already one on-chip
+ * cluster ends once fewer than half of its rows are active; the active rows
+ * are gathered (in index order) into a smaller problem whose launch shape is
+ * chosen again, and the state is scattered back when it ends. The steps are
+ * the same either way (same pairs, same arithmetic); this flag turns the
+ * re-layout off. */
+#define SVM_FLAG_NO_RELAYOUT 32
 
 typedef struct svm_shrink_policy {
     int32_t kind;            /* enum svm_shrink_kind */
@@ -214,6 +221,7 @@ typedef struct svm_stats {
     int32_t cache_slots;     /* kernel rows the cache holds (0: no cache) */
     int64_t cache_hits;      /* steps x sides whose kernel row came from the cache */
     int64_t cache_misses;    /* ... that were computed (and stored) */
+    int64_t relayouts;       /* active-set re-layouts (see SVM_FLAG_NO_RELAYOUT) */
 } svm_stats;
 
 /*

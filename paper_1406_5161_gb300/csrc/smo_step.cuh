@@ -577,6 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         if (!first) {
             if (!gap_open) { exit_reason = 0; break; }
             if (iter >= A.iter_limit) { exit_reason = 1; break; }
+            if (total < A.compact_below) { exit_reason = 2; break; }
             // ---- 0. kernel-row cache: this step's rows of x_up and x_low
             //         (the same decisions in every CTA; a row found here was
             //         stored by this CTA in an earlier step of this launch)
@@ -1452,8 +1453,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             }
         }
         if (cta == 0 && tid == 0 && iter < A.trace_len) {
-            A.trace[2 * iter] = up.i == INT_MAX ? -1 : up.i;
-            A.trace[2 * iter + 1] = low.i == INT_MAX ? -1 : low.i;
+            A.trace[2 * iter] = up.i == INT_MAX ? -1 : (A.gmap ? A.gmap[up.i] : up.i);
+            A.trace[2 * iter + 1] = low.i == INT_MAX ? -1 : (A.gmap ? A.gmap[low.i] : low.i);
         }
         if (timed && tid == 0) { uint64_t t = clock64(); ph[5] += t - tp; tp = t; }
     }
@@ -1476,8 +1477,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         c->b_low = low.f;
         c->a_up = up.a;
         c->a_low = low.a;
-        c->i_up = up.i == INT_MAX ? -1 : up.i;
-        c->i_low = low.i == INT_MAX ? -1 : low.i;
+        c->i_up = up.i == INT_MAX ? -1 : (A.gmap ? A.gmap[up.i] : up.i);
+        c->i_low = low.i == INT_MAX ? -1 : (A.gmap ? A.gmap[low.i] : low.i);
         c->iter = iter;
         c->counter = counter;
         c->active = total;

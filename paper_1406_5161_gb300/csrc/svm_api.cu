@@ -208,14 +208,176 @@ __global__ void k_seg_nnz(int64_t n, int G, const int64_t *indptr, int64_t *out)
     if (s < G) out[s] = indptr[seg_lo(n, G, s + 1)] - indptr[seg_lo(n, G, s)];
 }
 
+// ---- active-set re-layout: the active rows of a problem gathered into a
+//      smaller problem (rows kept in increasing index order, so the
+//      lowest-index tie-break is unchanged), and the solver state scattered
+//      back when the smaller problem's launch ends
+
+// stored entries of the selected rows, per chunk of kChunkRows rows
+constexpr int kChunkRows = 4096;
+__global__ void k_sub_len_sums(int64_t m, const int32_t *idx, const int64_t *indptr, int64_t *sums)
+{
+    __shared__ unsigned long long s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    const int64_t b0 = (int64_t)blockIdx.x * kChunkRows;
+    unsigned long long c = 0;
+    for (int64_t j = b0 + threadIdx.x; j < m && j < b0 + kChunkRows; j += blockDim.x)
+        c += (unsigned long long)(indptr[idx[j] + 1] - indptr[idx[j]]);
+    atomicAdd(&s, c);
+    __syncthreads();
+    if (threadIdx.x == 0) sums[blockIdx.x] = (int64_t)s;
+}
+
+__global__ void k_scan64(const int64_t *sums, int nb, int64_t *offs, int64_t *total)
+{
+    if (threadIdx.x != 0) return;
+    int64_t acc = 0;
+    for (int b = 0; b < nb; ++b) {
+        offs[b] = acc;
+        acc += sums[b];
+    }
+    *total = acc;
+}
+
+// row pointers of the selected rows: per chunk, an ordered block scan of
+// their lengths (256 threads)
+__global__ void k_sub_indptr(int64_t m, const int32_t *idx, const int64_t *indptr, const int64_t *offs,
+                             int64_t *sub_indptr)
+{
+    __shared__ int64_t wsum[8];
+    __shared__ int64_t base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) base = offs[blockIdx.x];
+    __syncthreads();
+    const int64_t b0 = (int64_t)blockIdx.x * kChunkRows;
+    for (int64_t s0 = b0; s0 < m && s0 < b0 + kChunkRows; s0 += 256) {
+        const int64_t j = s0 + threadIdx.x;
+        const int64_t len = (j < m && j < b0 + kChunkRows) ? indptr[idx[j] + 1] - indptr[idx[j]] : 0;
+        int64_t incl = len;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t o = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += o;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        int64_t pre = base + incl - len;
+        int64_t tot = 0;
+        for (int k = 0; k < 8; ++k) {
+            if (k < w) pre += wsum[k];
+            tot += wsum[k];
+        }
+        if (j < m && j < b0 + kChunkRows) sub_indptr[j] = pre;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) sub_indptr[m] = base;
+}
+
+// the selected rows' entries (one warp per row) and per-row data
+struct SubRowsArgs {
+    int64_t m;
+    const int32_t *idx;          // selected rows of the parent problem
+    const int32_t *pmap;         // parent index -> caller index (NULL: identity)
+    const int64_t *indptr;
+    const int32_t *indices;
+    const float *values, *vmix, *normf;
+    const double *norm, *alpha, *f;
+    const int8_t *y;
+    const uint8_t *status;
+    const uint32_t *bits;
+    int bit_words;
+    const int64_t *sub_indptr;
+    int32_t *sub_indices;
+    float *sub_values, *sub_vmix, *sub_normf;
+    double *sub_norm, *sub_alpha, *sub_f;
+    int8_t *sub_y;
+    uint8_t *sub_status;
+    uint32_t *sub_bits;
+    int32_t *sub_gmap;
+};
+
+__global__ void k_sub_rows(SubRowsArgs S)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < S.m; j += warps) {
+        const int64_t i = S.idx[j];
+        const int64_t p0 = S.indptr[i], len = S.indptr[i + 1] - p0, q0 = S.sub_indptr[j];
+        for (int64_t k = lane; k < len; k += 32) {
+            S.sub_indices[q0 + k] = S.indices[p0 + k];
+            if (S.sub_values) S.sub_values[q0 + k] = S.values[p0 + k];
+            if (S.sub_vmix) S.sub_vmix[q0 + k] = S.vmix[p0 + k];
+        }
+        for (int k = lane; k < S.bit_words; k += 32) S.sub_bits[j * S.bit_words + k] = S.bits[i * S.bit_words + k];
+        if (lane == 0) {
+            S.sub_y[j] = S.y[i];
+            if (S.sub_norm) S.sub_norm[j] = S.norm[i];
+            if (S.sub_normf) S.sub_normf[j] = S.normf[i];
+            S.sub_alpha[j] = S.alpha[i];
+            S.sub_f[j] = S.f[i];
+            S.sub_status[j] = S.status[i];
+            S.sub_gmap[j] = S.pmap ? S.pmap[i] : (int32_t)i;
+        }
+    }
+}
+
+// solver state of the smaller problem back into its parent; mark[i] = 1 for
+// the parent rows still active
+__global__ void k_sub_scatter(int64_t m, const int32_t *idx, const double *sub_alpha, const double *sub_f,
+                              const uint8_t *sub_status, const uint8_t *sub_mark, double *alpha, double *f,
+                              uint8_t *status, uint8_t *mark)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t i = idx[j];
+    alpha[i] = sub_alpha[j];
+    f[i] = sub_f[j];
+    status[i] = sub_status[j];
+    mark[i] = sub_mark[j];
+}
+
+// active lists from marks: segment s lists its marked rows in increasing
+// order (one block of 256 threads per segment)
+__global__ void k_active_from_mark(int64_t n, int G, const uint8_t *mark, int32_t *act, int32_t *seg_cnt)
+{
+    __shared__ int wsum[8];
+    __shared__ int base;
+    const int s = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t lo = seg_lo(n, G, s);
+    const int m = (int)(seg_lo(n, G, s + 1) - lo);
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int r0 = 0; r0 < m; r0 += 256) {
+        const int r = r0 + threadIdx.x;
+        const bool p = r < m && mark[lo + r] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, p);
+        if (lane == 0) wsum[w] = __popc(bal);
+        __syncthreads();
+        int pre = base + __popc(bal & ((1u << lane) - 1u));
+        int tot = 0;
+        for (int k = 0; k < 8; ++k) {
+            if (k < w) pre += wsum[k];
+            tot += wsum[k];
+        }
+        if (p) act[lo + pre] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) seg_cnt[s] = base;
+}
+
 // ---- deterministic, order-preserving compaction by predicate
-enum { PRED_UNMARKED = 0, PRED_ALPHA_POS = 1 };
+enum { PRED_UNMARKED = 0, PRED_ALPHA_POS = 1, PRED_MARKED = 2 };
 constexpr int kChunk = 4096;
 constexpr int kCT = 256;
 
 __device__ __forceinline__ bool pred_at(int pred, int64_t i, const uint8_t *mark, const double *alpha)
 {
-    return pred == PRED_UNMARKED ? mark[i] == 0 : alpha[i] > 0.0;
+    return pred == PRED_UNMARKED ? mark[i] == 0 : (pred == PRED_MARKED ? mark[i] != 0 : alpha[i] > 0.0);
 }
 
 __global__ void k_count(int pred, int64_t n, const uint8_t *mark, const double *alpha, int *counts)
@@ -565,9 +727,6 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         ++launches;
     }
     const int sms = device_sms();
-    int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 15) / 16));
-    if (P->ctas > 0) G = (int)std::min<int64_t>(std::min<int64_t>(P->ctas, sms), n);
-    if (G > 256) G = 256;
     const int kt = mode == MODE_BINARY ? ktab_len : 0;
     const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
     // kernel-row cache (FP64 and mixed inputs): every slot holds one kernel
@@ -600,67 +759,89 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         }
         if (kc_slots > 0) kdir = smo_kdir_bytes(n, kc_slots, kc_direct);
     }
-    // thread-block clusters for the hierarchical exchange: one cluster of 16
-    // when its segments stay in shared memory (no global exchange at all),
-    // else clusters of 8 with a leader exchange through global memory
-    int cs = 1;
-    {
-        const SmoLayout L0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0, kdir);
+    // launch shape of a problem of n_l rows and nnz_l entries (the caller's
+    // problem, or the active rows gathered after shrinking): thread-block
+    // clusters for the hierarchical exchange, one cluster of 16 when its
+    // segments stay in shared memory (no global exchange at all), else
+    // clusters of 8 with a leader exchange through global memory; segment
+    // sizes decide whether the rows stay in shared memory
+    struct Shape {
+        int G, cs, resident, seg_rows_max;
+        int64_t seg_nnz_max;
+        size_t smem;
+    };
+    int64_t *segnnz_d = ar.alloc<int64_t>(256);
+    auto pick_shape = [&](int64_t n_l, int64_t nnz_l, const int64_t *indptr_l, size_t kdir_l) -> Shape {
+        int G_l = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n_l + 15) / 16));
+        if (P->ctas > 0) G_l = (int)std::min<int64_t>(std::min<int64_t>(P->ctas, sms), n_l);
+        if (G_l > 256) G_l = 256;
+        int cs_l = 1;
+        const SmoLayout L0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0, kdir_l);
         const bool clusters_ok = (P->flags & SVM_FLAG_NO_CLUSTERS) == 0 && L0.total <= lim_dyn;
         bool single = false;
-        if (clusters_ok && (P->ctas == 0 || P->ctas == 16) && n >= 16 * 32 &&
+        if (clusters_ok && (P->ctas == 0 || P->ctas == 16) && n_l >= 16 * 32 &&
             (P->flags & SVM_FLAG_STREAM_ROWS) == 0) {
-            const int rows16 = (int)((n + 15) / 16);
-            const int64_t nnz16 = (int64_t)(1.25 * (double)D.nnz / 16.0) + D.maxnnz;   // segment estimate
-            const SmoLayout L16 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, rows16, nnz16, kdir);
+            const int rows16 = (int)((n_l + 15) / 16);
+            const int64_t nnz16 = (int64_t)(1.25 * (double)nnz_l / 16.0) + D.maxnnz;   // segment estimate
+            const SmoLayout L16 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, rows16, nnz16, kdir_l);
             if (L16.total <= lim_dyn && smo_max_clusters(kmode, lpr, 2, L16.total, 16) >= 1 &&
-                (P->ctas == 16 || n <= 200000)) {
+                (P->ctas == 16 || n_l <= 200000)) {
                 single = true;
-                cs = 16;
-                G = 16;
+                cs_l = 16;
+                G_l = 16;
             }
         }
-        if (!single && clusters_ok && G >= 16) {
+        if (!single && clusters_ok && G_l >= 16) {
             const int maxc = smo_max_clusters(kmode, lpr, 0, L0.total, 8);
             if (maxc >= 2) {
-                cs = 8;
-                G = 8 * std::min(maxc, G / 8);
+                cs_l = 8;
+                G_l = 8 * std::min(maxc, G_l / 8);
             }
         }
-    }
-    // segment sizes decide whether the rows stay in shared memory
-    int64_t *segnnz_d = ar.alloc<int64_t>(std::max(G, 256));
-    int64_t seg_nnz_max = 0;
-    int seg_rows_max = 0;
-    SmoLayout Ls{}, Lr{};
-    int resident = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        k_seg_nnz<<<grid1(G), 256, 0, st>>>(n, G, D.indptr, segnnz_d);
-        CK(cudaGetLastError());
-        ++launches;
-        std::vector<int64_t> segnnz(G);
-        CK(cudaMemcpyAsync(segnnz.data(), segnnz_d, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        seg_nnz_max = 0;
-        for (int64_t v : segnnz) seg_nnz_max = std::max(seg_nnz_max, v);
-        seg_rows_max = (int)((n + G - 1) / G);
-        Ls = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max, seg_nnz_max, kdir);
-        Lr = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max, seg_nnz_max, kdir);
-        resident = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 && seg_nnz_max < ((int64_t)1 << 31) &&
-                   Lr.total <= lim_dyn;
-        if (resident && cs > 1 && smo_max_clusters(kmode, lpr, G == cs ? 2 : 1, Lr.total, cs) * cs < G) resident = 0;
-        if (resident || cs != 16) break;
-        // the single cluster was chosen for on-chip segments that do not
-        // fit after all: clusters of 8 over the whole GPU instead
-        cs = 8;
-        const size_t s0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0, kdir).total;
-        G = 8 * std::max(1, std::min(smo_max_clusters(kmode, lpr, 0, s0, 8), std::min(sms, 256) / 8));
-    }
-    const size_t smem = resident ? Lr.total : Ls.total;
-    if (smem > lim_dyn) {
-        set_err("d = %lld exceeds the shared-memory target rows of this mode", (long long)D.d);
-        throw Fail{SVM_ERR_UNSUPPORTED};
-    }
+        int64_t seg_nnz_max_l = 0;
+        int seg_rows_max_l = 0;
+        SmoLayout Ls{}, Lr{};
+        int resident_l = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            k_seg_nnz<<<grid1(G_l), 256, 0, st>>>(n_l, G_l, indptr_l, segnnz_d);
+            CK(cudaGetLastError());
+            ++launches;
+            std::vector<int64_t> segnnz(G_l);
+            CK(cudaMemcpyAsync(segnnz.data(), segnnz_d, sizeof(int64_t) * G_l, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            seg_nnz_max_l = 0;
+            for (int64_t v : segnnz) seg_nnz_max_l = std::max(seg_nnz_max_l, v);
+            seg_rows_max_l = (int)((n_l + G_l - 1) / G_l);
+            Ls = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, seg_rows_max_l, seg_nnz_max_l, kdir_l);
+            Lr = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, seg_rows_max_l, seg_nnz_max_l, kdir_l);
+            resident_l = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 &&
+                         seg_nnz_max_l < ((int64_t)1 << 31) && Lr.total <= lim_dyn;
+            if (resident_l && cs_l > 1 &&
+                smo_max_clusters(kmode, lpr, G_l == cs_l ? 2 : 1, Lr.total, cs_l) * cs_l < G_l)
+                resident_l = 0;
+            if (resident_l || cs_l != 16) break;
+            // the single cluster was chosen for on-chip segments that do not
+            // fit after all: clusters of 8 over the whole GPU instead
+            cs_l = 8;
+            const size_t s0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0, kdir_l).total;
+            G_l = 8 * std::max(1, std::min(smo_max_clusters(kmode, lpr, 0, s0, 8), std::min(sms, 256) / 8));
+        }
+        Shape sh;
+        sh.G = G_l;
+        sh.cs = cs_l;
+        sh.resident = resident_l;
+        sh.seg_rows_max = seg_rows_max_l;
+        sh.seg_nnz_max = seg_nnz_max_l;
+        sh.smem = resident_l ? Lr.total : Ls.total;
+        if (sh.smem > lim_dyn) {
+            set_err("d = %lld exceeds the shared-memory target rows of this mode", (long long)D.d);
+            throw Fail{SVM_ERR_UNSUPPORTED};
+        }
+        return sh;
+    };
+    const Shape top = pick_shape(n, D.nnz, D.indptr, kdir);
+    const int G = top.G;
+    const int cs = top.cs, resident = top.resident;
     double *ktab = nullptr;
     if (mode == MODE_BINARY) {
         ktab = ar.alloc<double>(3 * (size_t)ktab_len);
@@ -675,9 +856,10 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     double *f = ar.alloc<double>(n);
     uint8_t *status = ar.alloc<uint8_t>(n);
     int32_t *act = ar.alloc<int32_t>(n);
-    int32_t *seg_cnt = ar.alloc<int32_t>(G);
-    void *cand = ar.alloc<unsigned char>(2 * (size_t)G * smo_cand_bytes());
-    unsigned *seq = ar.alloc<unsigned>(smo_seq_words(G));
+    int32_t *seg_cnt = ar.alloc<int32_t>(256);
+    // exchange slots and flags for the largest grid of any level (<= 256 CTAs)
+    void *cand = ar.alloc<unsigned char>(2 * (size_t)256 * smo_cand_bytes());
+    unsigned *seq = ar.alloc<unsigned>(smo_seq_words(256));
     SmoCtrl *ctrl = ar.alloc<SmoCtrl>(1);
     const int64_t trace_len = (P->trace && P->trace_len > 0) ? P->trace_len : 0;
     int32_t *trace = ar.alloc<int32_t>(2 * std::max<int64_t>(trace_len, 1));
@@ -728,8 +910,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.ktab_len = ktab_len;
     A.maxnnz = D.maxnnz;
     A.resident = resident;
-    A.seg_rows_max = seg_rows_max;
-    A.seg_nnz_max = seg_nnz_max;
+    A.seg_rows_max = top.seg_rows_max;
+    A.seg_nnz_max = top.seg_nnz_max;
     A.C = P->C;
     A.gamma = P->gamma;
     A.phase_times = (P->flags & SVM_FLAG_PHASE_TIMES) != 0;
@@ -745,8 +927,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     }
     int64_t *cta_cycles = nullptr;
     if (A.phase_times) {
-        cta_cycles = ar.alloc<int64_t>(G);
-        CK(cudaMemsetAsync(cta_cycles, 0, sizeof(int64_t) * G, st));
+        cta_cycles = ar.alloc<int64_t>(256);
+        CK(cudaMemsetAsync(cta_cycles, 0, sizeof(int64_t) * 256, st));
     }
     A.cta_cycles = cta_cycles;
     A.timeout_ns = 10ll * 1000 * 1000 * 1000;
@@ -755,15 +937,65 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double ms_smo = 0.0, ms_recon = 0.0;
-    auto run = [&](int select_only, double thr, int64_t hh, int64_t limit) {
+    // Active-set re-layout (with shrinking): a launch over a problem that is
+    // not already one on-chip cluster ends once fewer than half of its rows
+    // are active; the active rows are gathered, in index order, into a
+    // smaller problem whose launch shape is chosen again (segments on chip,
+    // a single cluster), and its state is scattered back when its launch
+    // ends. Rows keep their order, so every step is the one the parent
+    // problem would have taken (the same pairs, the same arithmetic).
+    struct Level {
+        int64_t n, nnz;
+        const int64_t *indptr;
+        const int32_t *indices;
+        const float *values, *vmix, *normf;
+        const double *norm;
+        const int8_t *y;
+        const uint32_t *bits;
+        double *alpha, *f;
+        uint8_t *status;
+        int32_t *act, *seg_cnt;
+        const int32_t *idx;    // this level's rows in its parent (NULL at the top)
+        const int32_t *gmap;   // ... and in the caller's problem
+        Shape shape;
+    };
+    const bool relayout_on = (P->flags & SVM_FLAG_NO_RELAYOUT) == 0;
+    bool relayout_ok = relayout_on;
+    const int bit_words = mode_bits(kmode) ? mode_words(kmode) : 0;
+    std::vector<Level> lv;
+    lv.push_back(Level{n, D.nnz, D.indptr, D.indices, vals_fp32, D.vmix, D.normf, D.norm, D.y, bits,
+                       alpha, f, status, act, seg_cnt, nullptr, nullptr, top});
+    int64_t relayouts = 0;
+    auto launch_level = [&](const Level &L, int select_only, double thr, int64_t hh, int64_t limit) {
+        A.n = L.n;
+        A.G = L.shape.G;
+        A.indptr = L.indptr;
+        A.indices = L.indices;
+        A.values = L.values;
+        A.vmix = L.vmix;
+        A.y = L.y;
+        A.norm = L.norm;
+        A.normf = L.normf;
+        A.bits = L.bits;
+        A.alpha = L.alpha;
+        A.f = L.f;
+        A.status = L.status;
+        A.act = L.act;
+        A.seg_cnt = L.seg_cnt;
+        A.resident = L.shape.resident;
+        A.seg_rows_max = L.shape.seg_rows_max;
+        A.seg_nnz_max = L.shape.seg_nnz_max;
+        A.gmap = L.gmap;
+        const bool one_cluster_on_chip = L.shape.resident && L.shape.cs == L.shape.G;
+        A.compact_below = (relayout_ok && hh > 0 && !one_cluster_on_chip && L.n >= 2048) ? L.n / 2 : 0;
         CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
-        CK(cudaMemsetAsync(seq, 0, sizeof(unsigned) * smo_seq_words(G), st));
+        CK(cudaMemsetAsync(seq, 0, sizeof(unsigned) * smo_seq_words(L.shape.G), st));
         A.thr = thr;
         A.h = hh;
         A.iter_limit = limit;
         A.select_only = select_only;
         CK(cudaEventRecord(e0, st));
-        CK(launch_smo_persistent(kmode, lpr, A, smem, st, cs));
+        CK(launch_smo_persistent(kmode, lpr, A, L.shape.smem, st, L.shape.cs));
         CK(cudaEventRecord(e1, st));
         ++launches;
         CK(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));
@@ -775,6 +1007,119 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             set_err("a grid-wide wait in the SMO kernel exceeded its time limit");
             throw Fail{SVM_ERR_TIMEOUT};
         }
+    };
+    // the active rows of the deepest level into a new level; false when
+    // there are too few of them to be worth it
+    auto push_level = [&]() -> bool {
+        const Level Pa = lv.back();
+        uint8_t *mk = ar.alloc<uint8_t>(Pa.n);
+        CK(cudaMemsetAsync(mk, 0, Pa.n, st));
+        k_mark_active<<<Pa.shape.G, 256, 0, st>>>(Pa.n, Pa.shape.G, Pa.act, Pa.seg_cnt, mk);
+        CK(cudaGetLastError());
+        ++launches;
+        int32_t *idx = ar.alloc<int32_t>(Pa.n);
+        const int64_t m = compact(ar, PRED_MARKED, Pa.n, mk, nullptr, nullptr, idx, nullptr, st, &launches);
+        if (m < 2 * 32) return false;
+        const int nb = (int)((m + kChunkRows - 1) / kChunkRows);
+        int64_t *sums = ar.alloc<int64_t>(nb);
+        int64_t *offs = ar.alloc<int64_t>(nb);
+        int64_t *tot = ar.alloc<int64_t>(1);
+        int64_t *sub_indptr = ar.alloc<int64_t>(m + 1);
+        k_sub_len_sums<<<nb, 256, 0, st>>>(m, idx, Pa.indptr, sums);
+        k_scan64<<<1, 32, 0, st>>>(sums, nb, offs, tot);
+        k_sub_indptr<<<nb, 256, 0, st>>>(m, idx, Pa.indptr, offs, sub_indptr);
+        CK(cudaGetLastError());
+        launches += 3;
+        int64_t nnz_m = 0;
+        CK(cudaMemcpyAsync(&nnz_m, tot, sizeof nnz_m, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        SubRowsArgs S;
+        std::memset(&S, 0, sizeof S);
+        S.m = m;
+        S.idx = idx;
+        S.pmap = Pa.gmap;
+        S.indptr = Pa.indptr;
+        S.indices = Pa.indices;
+        S.values = Pa.values;
+        S.vmix = Pa.vmix;
+        S.normf = Pa.normf;
+        S.norm = Pa.norm;
+        S.alpha = Pa.alpha;
+        S.f = Pa.f;
+        S.y = Pa.y;
+        S.status = Pa.status;
+        S.bits = Pa.bits;
+        S.bit_words = Pa.bits ? bit_words : 0;
+        S.sub_indptr = sub_indptr;
+        S.sub_indices = ar.alloc<int32_t>(nnz_m);
+        // only the values the row pass reads: FP32 (FP64 mode) or BF16-rounded (mixed)
+        S.sub_values = (Pa.values && kmode == MODE_FP64) ? ar.alloc<float>(nnz_m) : nullptr;
+        S.sub_vmix = (Pa.vmix && kmode == MODE_MIXED) ? ar.alloc<float>(nnz_m) : nullptr;
+        S.sub_normf = Pa.normf ? ar.alloc<float>(m) : nullptr;
+        S.sub_norm = Pa.norm ? ar.alloc<double>(m) : nullptr;
+        S.sub_alpha = ar.alloc<double>(m);
+        S.sub_f = ar.alloc<double>(m);
+        S.sub_y = ar.alloc<int8_t>(m);
+        S.sub_status = ar.alloc<uint8_t>(m);
+        S.sub_bits = S.bit_words ? ar.alloc<uint32_t>((size_t)m * S.bit_words) : nullptr;
+        S.sub_gmap = ar.alloc<int32_t>(m);
+        k_sub_rows<<<(int)std::min<int64_t>((m + 7) / 8, 4096), 256, 0, st>>>(S);
+        CK(cudaGetLastError());
+        ++launches;
+        Level C;
+        C.n = m;
+        C.nnz = nnz_m;
+        C.indptr = sub_indptr;
+        C.indices = S.sub_indices;
+        C.values = S.sub_values;
+        C.vmix = S.sub_vmix;
+        C.normf = S.sub_normf;
+        C.norm = S.sub_norm;
+        C.y = S.sub_y;
+        C.bits = S.sub_bits;
+        C.alpha = S.sub_alpha;
+        C.f = S.sub_f;
+        C.status = S.sub_status;
+        C.act = ar.alloc<int32_t>(m);
+        C.seg_cnt = ar.alloc<int32_t>(256);
+        C.idx = idx;
+        C.gmap = S.sub_gmap;
+        C.shape = pick_shape(m, nnz_m, sub_indptr, kc_slots > 0 ? smo_kdir_bytes(m, kc_slots, kc_direct) : 0);
+        k_reset_active<<<C.shape.G, 256, 0, st>>>(m, C.shape.G, C.act, C.seg_cnt);
+        CK(cudaGetLastError());
+        ++launches;
+        lv.push_back(C);
+        ++relayouts;
+        return true;
+    };
+    // the deepest level's state back into its parent
+    auto pop_level = [&]() {
+        const Level C = lv.back();
+        lv.pop_back();
+        const Level &Pa = lv.back();
+        uint8_t *cm = ar.alloc<uint8_t>(C.n);
+        uint8_t *pm = ar.alloc<uint8_t>(Pa.n);
+        CK(cudaMemsetAsync(cm, 0, C.n, st));
+        CK(cudaMemsetAsync(pm, 0, Pa.n, st));
+        k_mark_active<<<C.shape.G, 256, 0, st>>>(C.n, C.shape.G, C.act, C.seg_cnt, cm);
+        k_sub_scatter<<<grid1(C.n), 256, 0, st>>>(C.n, C.idx, C.alpha, C.f, C.status, cm, Pa.alpha, Pa.f,
+                                                  Pa.status, pm);
+        k_active_from_mark<<<Pa.shape.G, 256, 0, st>>>(Pa.n, Pa.shape.G, pm, Pa.act, Pa.seg_cnt);
+        CK(cudaGetLastError());
+        launches += 3;
+    };
+    auto run = [&](int select_only, double thr, int64_t hh, int64_t limit) {
+        int sel = select_only;
+        for (;;) {
+            launch_level(lv.back(), sel, thr, hh, limit);
+            if (hc.exit_reason != 2) break;
+            // the same state continues on the gathered rows (a selection
+            // pass there finds the pair this launch had chosen)
+            if (!push_level()) relayout_ok = false;
+            sel = 1;
+        }
+        while (lv.size() > 1) pop_level();
+        relayout_ok = relayout_on;
     };
 
     bool shrinking = shrink_on;
@@ -920,6 +1265,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         stats->cache_slots = kc_slots;
         stats->cache_hits = hc.kc_hits;
         stats->cache_misses = hc.kc_misses;
+        stats->relayouts = relayouts;
         int dev = 0, khz = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);

@@ -67,7 +67,8 @@ struct SmoCtrl {
     int64_t active;            // active-set size
     int64_t row_visits;        // sum of active-set sizes over the steps
     int32_t i_up, i_low;
-    int32_t exit_reason;       // 0: gap <= thr, 1: iteration limit
+    int32_t exit_reason;       // 0: gap <= thr, 1: iteration limit, 2: active set
+                               // below SmoArgs::compact_below
     int32_t err;               // 0 ok, 1 timeout in a grid-wide wait
     int64_t shrink_events;
     // SM cycles spent by CTA 0 in each phase of a step (summed over steps,
@@ -128,6 +129,13 @@ struct SmoArgs {
     int32_t kernel, degree;    // kernel kind (KERNEL_*); polynomial degree
     double coef0;              // polynomial / sigmoid offset
     int32_t wss2;              // i_low by the second-order gain (its own kernel instantiation)
+    // active-set re-layout: the launch ends (exit_reason 2) once fewer than
+    // compact_below rows are active (0: never), so that the host can gather
+    // the active rows into a smaller problem; gmap (NULL at the top level)
+    // maps this problem's sample indices to the caller's for the trace and
+    // the reported pair
+    int64_t compact_below;
+    const int32_t *gmap;
 };
 
 // ---- batched and served solves: one job = one two-class problem
