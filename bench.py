@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--policy", default="Multi5pc")
+    ap.add_argument("--policy", default=None,
+                    help="shrinking policy (Table 3); default Multi5pc, and Multi500 for the "
+                         "covtype workload (fastest of the policies measured there)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=100)
     ap.add_argument("--serve-nmax", type=int, default=10000)
@@ -649,6 +651,8 @@ def run_serve(args):
 
 def main():
     args = parse()
+    if args.policy is None:
+        args.policy = "Multi500" if args.workload == "covtype" else "Multi5pc"
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank)
