@@ -464,7 +464,7 @@ def run_covtype(args):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 1)):
         pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream,
-                      flags=flags)
+                      flags=flags, max_iter=args.max_iter)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -476,7 +476,7 @@ def run_covtype(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream,
-                          flags=flags)
+                          flags=flags, max_iter=args.max_iter)
         e1.record(stream)
         ev.append((e0, e1))
         s = r["stats"]
@@ -509,6 +509,8 @@ def run_covtype(args):
                          "kernel_ms_per_step": ms_smo / args.steps}}
     if args.wss2:
         line["config"]["selection"] = "second-order i_low (SVM_FLAG_WSS2)"
+    if args.max_iter:
+        line["config"]["max_iter"] = args.max_iter
     print(json.dumps(line), flush=True)
     return 0
 
