@@ -182,6 +182,15 @@ typedef struct svm_kernel {
  * the same either way (same pairs, same arithmetic); this flag turns the
  * re-layout off. */
 #define SVM_FLAG_NO_RELAYOUT 32
+/* Kernel rows on the tensor cores (SVM_MIXED_BF16, RBF, d <= 256, no
+ * kernel-row cache): tiles of 16 active rows against the two target rows
+ * (BF16 inputs, FP32 accumulation) from a dense BF16 copy of the rows. Used
+ * automatically when the rows are dense enough (mean stored entries per row
+ * >= 32 and >= half of d rounded up to 32, d <= 128); SVM_FLAG_TENSOR_ROWS
+ * asks for it wherever it applies, SVM_FLAG_CUDA_CORE_ROWS keeps the CSR row
+ * pass on the CUDA cores (same arithmetic type, another summation order). */
+#define SVM_FLAG_CUDA_CORE_ROWS 64
+#define SVM_FLAG_TENSOR_ROWS 128
 
 typedef struct svm_shrink_policy {
     int32_t kind;            /* enum svm_shrink_kind */
@@ -222,6 +231,8 @@ typedef struct svm_stats {
     int64_t cache_hits;      /* steps x sides whose kernel row came from the cache */
     int64_t cache_misses;    /* ... that were computed (and stored) */
     int64_t relayouts;       /* active-set re-layouts (see SVM_FLAG_NO_RELAYOUT) */
+    int32_t row_tiles;       /* 1 when the kernel rows ran on the tensor cores */
+    int32_t reserved;
 } svm_stats;
 
 /*

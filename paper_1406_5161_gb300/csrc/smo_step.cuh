@@ -33,6 +33,7 @@
 #include <cstddef>
 #include <type_traits>
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "svm_internal.cuh"
@@ -67,6 +68,21 @@ __device__ __forceinline__ void step_bar_sync(int n) { asm volatile("bar.sync 1,
 __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// named barrier 2 among the row warps only (warps 1..; the pair-step warp
+// does not take part)
+__device__ __forceinline__ void rows_bar_sync() { asm volatile("bar.sync 2, %0;" ::"r"(kThreads - 32) : "memory"); }
+
+// D += A B on the tensor cores: A 16x16 BF16 (rows), B 16x8 BF16 (targets),
+// D 16x8 FP32 (m16n8k16, register fragments)
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // distributed shared memory and mbarriers (32-bit shared-window addresses)
@@ -799,6 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             KT *kc_ru = kc_step ? static_cast<KT *>(A.kc) + (size_t)sh.kc_su * A.kc_ld : nullptr;
             KT *kc_rl = kc_step ? static_cast<KT *>(A.kc) + (size_t)sh.kc_sl * A.kc_ld : nullptr;
             const bool skip_sums = kc_hu && kc_hl;
+            const float up_nrmf = (float)up.nrm, low_nrmf = (float)low.nrm;
             // streamed segment with no row shrunk: its active list is the
             // identity (lists are reset to it and compacted in order), so the
             // row index needs no load
@@ -806,6 +823,144 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             double du = 0.0, dl = 0.0, au_new = 0.0, al_new = 0.0;
             unsigned char st_u = 0, st_l = 0;
             bool have_step = first;
+            bool tiles_done = false;
+            if constexpr (MODE == MODE_MIXED && LPR == 16) {
+                if (A.dmat != nullptr && !kc_on) {
+                    // Kernel rows on the tensor cores (mixed mode, RBF): tiles
+                    // of 16 active rows x the two target rows (mma m16n8k16,
+                    // BF16 inputs, FP32 accumulation; B columns 2..7 zero),
+                    // rows read as dense BF16 from the d_pad-wide copy. Inside
+                    // each 32-column block the K order is permuted so that a
+                    // lane reads 8 consecutive values of a row with one
+                    // 16-byte load: in k-step h of block b, logical k = 2t + i
+                    // is column 32b + 8t + 4h + i and k = 2t + 8 + i column
+                    // 32b + 8t + 4h + 2 + i; the targets use the same map, so
+                    // the dot products are those of the rows. Each warp takes
+                    // 32 active rows (two tiles) at a time and hands each
+                    // row's two sums to one lane, which finishes the row as
+                    // the CUDA-core pass does.
+                    tiles_done = true;
+                    const int g = lane >> 2, t4 = lane & 3;
+                    const int nblk = A.d_pad >> 5;
+                    uint2 *frag = reinterpret_cast<uint2 *>(dsm + L.frag);   // [2 nblk k-steps][32 lanes]
+                    if (warp == 1) {
+                        for (int ks = 0; ks < 2 * nblk; ++ks) {
+                            const int b = ks >> 1, h = ks & 1;
+                            uint32_t w0 = 0, w1 = 0;
+                            if (!first && g < 2) {
+                                const int c = 32 * b + 8 * t4 + 4 * h;
+                                float e[4];
+#pragma unroll
+                                for (int x = 0; x < 4; ++x) {
+                                    const int cx = c + x;
+                                    e[x] = cx < d ? (g == 0 ? T[cx].x : T[cx].y) : 0.f;
+                                }
+                                const __nv_bfloat162 p0 = __floats2bfloat162_rn(e[0], e[1]);
+                                const __nv_bfloat162 p1 = __floats2bfloat162_rn(e[2], e[3]);
+                                w0 = *reinterpret_cast<const uint32_t *>(&p0);
+                                w1 = *reinterpret_cast<const uint32_t *>(&p1);
+                            }
+                            frag[ks * 32 + lane] = make_uint2(w0, w1);
+                        }
+                    }
+                    rows_bar_sync();
+                    for (int base = (warp - 1) * 32;; base += kRowWarps * 32) {   // warp-uniform
+                        const bool round0 = base == (warp - 1) * 32;
+                        if (!round0 && base >= cnt) break;
+                        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                        if (!first) {
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const int ka = base + 16 * q + g, kb2 = ka + 8;
+                                const __nv_bfloat16 *pa = nullptr, *pb = nullptr;
+                                if (ka < cnt) pa = A.dmat + (size_t)(lo + (ident ? ka : ACT(ka))) * A.d_pad + 8 * t4;
+                                if (kb2 < cnt) pb = A.dmat + (size_t)(lo + (ident ? kb2 : ACT(kb2))) * A.d_pad + 8 * t4;
+                                for (int b = 0; b < nblk; ++b) {
+                                    const uint4 u = pa ? __ldg(reinterpret_cast<const uint4 *>(pa + 32 * b)) : make_uint4(0, 0, 0, 0);
+                                    const uint4 v = pb ? __ldg(reinterpret_cast<const uint4 *>(pb + 32 * b)) : make_uint4(0, 0, 0, 0);
+                                    const uint2 f0 = frag[(2 * b) * 32 + lane], f1 = frag[(2 * b + 1) * 32 + lane];
+                                    mma_bf16_16816(acc[q], u.x, v.x, u.y, v.y, f0.x, f0.y);
+                                    mma_bf16_16816(acc[q], u.z, v.z, u.w, v.w, f1.x, f1.y);
+                                }
+                            }
+                        }
+                        // the sums of active-list position base + lane: tile
+                        // lane >> 4, row (lane & 15), held by lane 4 (lane & 7)
+                        // as (acc[2 s], acc[2 s + 1]), s = (lane >> 3) & 1
+                        const int src = 4 * (lane & 7);
+                        const int qq = lane >> 4, ss = (lane >> 3) & 1;
+                        float su = 0.f, sl = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                            for (int s2 = 0; s2 < 2; ++s2) {
+                                const float a = __shfl_sync(0xffffffffu, acc[q][2 * s2], src);
+                                const float b = __shfl_sync(0xffffffffu, acc[q][2 * s2 + 1], src);
+                                if (q == qq && s2 == ss) { su = a; sl = b; }
+                            }
+                        }
+                        const int k = base + lane;
+                        const bool valid = k < cnt;
+                        int r = 0;
+                        double fi = 0.0;
+                        uint8_t sb = 0;
+                        double ku = 0.0, kl = 0.0;
+                        if (valid) {
+                            r = ident ? k : ACT(k);
+                            fi = GETF(r);
+                            sb = GETST(r);
+                            if (!first) {
+                                // K(x, x) = 1 exactly for the pair's own rows (the
+                                // tile sums and the stored norms are summed in
+                                // different orders, so their difference is not 0)
+                                const int i = (int)(lo + r);
+                                const float nrr = (float)NRM(r);
+                                ku = i == up.i ? 1.0 : (double)__expf(-gammaf * fmaxf(up_nrmf + nrr - 2.0f * su, 0.f));
+                                kl = i == low.i ? 1.0 : (double)__expf(-gammaf * fmaxf(low_nrmf + nrr - 2.0f * sl, 0.f));
+                            }
+                        }
+                        if (!have_step) {
+                            step_bar_sync(kThreads);
+                            du = sh.du; dl = sh.dl;
+                            st_u = sh.st_u; st_l = sh.st_l;
+                            au_new = sh.au_new; al_new = sh.al_new;
+                            have_step = true;
+                        }
+                        if (valid) {
+                            const int i = (int)(lo + r);
+                            if (!first) {
+                                // Eq. (fup), FP64 accumulation
+                                fi = fma(dl, kl, fma(du, ku, fi));
+                                PUTF(r, fi);
+                                if (i == up.i) {
+                                    sb = st_u;
+                                    PUTST(r, sb);
+                                    PUTA(r, au_new);
+                                } else if (i == low.i) {
+                                    sb = st_l;
+                                    PUTST(r, sb);
+                                    PUTA(r, al_new);
+                                }
+                            }
+                            const uint8_t set = set_bits(sb);
+                            bool keep = true;
+                            if (shrink_now) {
+                                // Eq. (shrink), with the thresholds that chose this pair
+                                keep = !(((set == ST_I3 || set == ST_I4) && dless(fi, bup_sel)) ||
+                                         ((set == ST_I1 || set == ST_I2) && dless(blow_sel, fi)));
+                                if (!keep) SET_ACT(k, ~r);
+                            }
+                            if (keep) {
+                                const unsigned long long kup = key_up(fi), klo = key_low(fi);
+                                // a lane meets its rows in increasing index order
+                                if (st_up(set) && kup < bku) { bku = kup; biu = i; bru = r; }
+                                if (st_low(set) && klo < bkl) { bkl = klo; bil = i; brl = r; }
+                            }
+                        }
+                    }
+                }
+            }
+            if (!tiles_done)
             for (int kb = (warp - 1) * RPW;; kb += kRowWarps * RPW) {
                 const bool round0 = kb == (warp - 1) * RPW;
                 if (!round0 && kb >= cnt) break;

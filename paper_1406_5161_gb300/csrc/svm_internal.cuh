@@ -136,6 +136,11 @@ struct SmoArgs {
     // the reported pair
     int64_t compact_below;
     const int32_t *gmap;
+    // mixed mode, RBF: the rows as dense BF16 [n][d_pad] (d_pad a multiple of
+    // 32, <= 256, zero padded) for the tensor-core row tiles; NULL = the CSR
+    // row pass on the CUDA cores
+    const __nv_bfloat16 *dmat;
+    int32_t d_pad;
 };
 
 // ---- batched and served solves: one job = one two-class problem
@@ -195,7 +200,7 @@ cudaError_t launch_smo_batch(int mode, int lpr, int dense, const BatchArgs &a, s
 
 // Dynamic shared-memory layout of the step kernel (byte offsets).
 struct SmoLayout {
-    size_t tgt, tcol, ktab, f, alpha, nrm, rowptr, act, st, col, val, bits, dist, kdir, total;
+    size_t tgt, tcol, ktab, f, alpha, nrm, rowptr, act, st, col, val, bits, dist, kdir, frag, total;
 };
 
 __host__ __device__ inline size_t smo_align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -223,6 +228,8 @@ __host__ __device__ inline SmoLayout smo_layout(int mode, int d, int ktab_len, i
     L.bits = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 * mode_words(mode) : 0));
     L.dist = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 : 0));   // two 16-bit distances per row
     L.kdir = o;   o = smo_align16(o + kdir_bytes);                     // kernel-row cache directory
+    // mixed mode: B fragments of the tensor-core row tiles (16 k-steps x 32 lanes x 8 B)
+    L.frag = o;   o = smo_align16(o + (mode == 2 ? (size_t)16 * 32 * 8 : 0));
     L.total = o;
     return L;
 }

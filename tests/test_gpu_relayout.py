@@ -62,13 +62,16 @@ def _problem(name):
         return synth.gaussian_mixture(n=5000, n_test=0, seed=21), {}
     if name == "dense-mixed":
         return synth.gaussian_mixture(n=5000, n_test=0, seed=21), {"precision": pkg.SVM_MIXED_BF16}
+    if name == "dense-mixed-tiles":
+        return synth.gaussian_mixture(n=5000, n_test=0, d=64, seed=22, gamma=0.01), {
+            "precision": pkg.SVM_MIXED_BF16, "flags": pkg.SVM_FLAG_TENSOR_ROWS}
     if name == "ragged":
         return synth.random_sparse(6001, 300, 0.02, seed=5, binary=False, C=10.0, gamma=0.05), {}
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("policy", ["Multi5pc", "Multi2", "Single5pc"])
-@pytest.mark.parametrize("name", ["bits", "csr-binary", "dense-fp64", "dense-mixed", "ragged"])
+@pytest.mark.parametrize("name", ["bits", "csr-binary", "dense-fp64", "dense-mixed", "dense-mixed-tiles", "ragged"])
 def test_relayout_is_the_same_solve(name, policy):
     """Clusters of 8 over the GPU (ctas=152), so that the re-layout engages."""
     p, kw = _problem(name)
