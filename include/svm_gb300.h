@@ -223,7 +223,7 @@ typedef struct svm_stats {
                                 phase, summed over steps: target rows, pair step
                                 (FP64 part), row pass + CTA reduction, publish,
                                 grid exchange, other, pair step (K(up,low) part),
-                                unused */
+                                second-order gain sweep and exchange */
     double cta_busy_ms_min;  /* with SVM_FLAG_PHASE_TIMES: least and most time a */
     double cta_busy_ms_max;  /* CTA spent from step start to publishing its candidate */
     int32_t bit_rows;        /* 1 when the row pass read binary rows as bit masks */
@@ -423,6 +423,18 @@ int svm_train_fixed_workspace(const svm_csr *X, const int8_t *y, const svm_param
 /* Number of CUDA kernels this library has launched in this process (all
  * threads, all calls), for accounting of device work. */
 int64_t svm_kernel_launches(void);
+
+/* Failure-handling check (the paper has no counterpart: its outer-loop flag
+ * is never set, and this library bounds every device-side wait instead).
+ * Runs, on the device, the bounded wait that the fused step uses for its
+ * candidate exchange, on an mbarrier that nothing completes, with the given
+ * limit:
+ *   limit_ns  1e6 .. 5e9 (1 ms .. 5 s)
+ *   stream    cudaStream_t (NULL = legacy default stream)
+ * Returns SVM_ERR_TIMEOUT when the wait gave up (the expected outcome; the
+ * CUDA context stays usable), SVM_OK if it did not, SVM_ERR_ARG for a limit
+ * out of range. Synchronous. */
+int svm_diag_wait_timeout(int64_t limit_ns, void *stream);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char *svm_last_error(void);

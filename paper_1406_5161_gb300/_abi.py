@@ -121,12 +121,20 @@ def load(build_if_missing: bool = True):
             lib.svm_kernel_launches.argtypes = []
             lib.svm_train_fixed_workspace.restype = ct.c_int
             lib.svm_train_fixed_workspace.argtypes = [P, P, P, P, P, P]
+            lib.svm_diag_wait_timeout.restype = ct.c_int
+            lib.svm_diag_wait_timeout.argtypes = [ct.c_int64, P]
             _lib = lib
     return _lib
 
 
 def svm_kernel_launches() -> int:
     return int(load().svm_kernel_launches())
+
+
+def svm_diag_wait_timeout(limit_ns: int, stream=None) -> int:
+    """Runs the library's bounded device-side wait on a barrier that nothing
+    completes; returns the status (SVM_ERR_TIMEOUT expected)."""
+    return int(load().svm_diag_wait_timeout(int(limit_ns), _stream_ptr(stream)))
 
 
 def svm_last_error() -> str:

@@ -138,6 +138,26 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// Waits for the phase of the given parity of a CTA-local mbarrier, giving up
+// after timeout_ns of %globaltimer, or at once when another CTA has flagged
+// an error; returns 1 when it gave up (the caller records the error and
+// leaves its loop, so that no wait of the library can outlast its limit).
+__device__ __forceinline__ int mbar_wait_bounded(uint32_t bar, uint32_t parity, int64_t timeout_ns, const int *err)
+{
+    int spins = 0;
+    uint64_t t0 = 0;
+    while (!mbar_try_wait_cluster(bar, parity)) {
+        if (++spins >= 64) {
+            spins = 0;
+            const uint64_t now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > (uint64_t)timeout_ns) return 1;
+            if (*(volatile const int *)err) return 1;
+        }
+    }
+    return 0;
+}
+
 // status byte: bits 0-2 = index set (Eq. setinfo), bit 7 = label is +1
 __device__ __forceinline__ uint8_t set_bits(uint8_t b) { return b & 7; }
 __device__ __forceinline__ int8_t y_of(uint8_t b) { return (b & 0x80) ? 1 : -1; }
@@ -1316,17 +1336,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     // completes its phase of parity k & 1
                     const uint32_t bar = smem_u32(&sh.xbar[par]);
                     const uint32_t parity = (uint32_t)((epoch - 1) >> 1) & 1u;
-                    int timed_out = 0, spins = 0;
-                    uint64_t t0 = 0;
-                    while (!mbar_try_wait_cluster(bar, parity)) {
-                        if (++spins >= 64) {
-                            spins = 0;
-                            const uint64_t now = global_ns();
-                            if (t0 == 0) t0 = now;
-                            else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
-                            if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
-                        }
-                    }
+                    int timed_out = mbar_wait_bounded(bar, parity, A.timeout_ns, &A.ctrl->err);
                     timed_out = __any_sync(0xffffffffu, timed_out);
                     if (timed_out && lane == 0) atomicExch(&A.ctrl->err, 1);
                     unsigned long long k1 = kNoKey, k2 = kNoKey;

@@ -2302,6 +2302,33 @@ const char *svm_last_error(void) { return g_err.c_str(); }
 
 int64_t svm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+int svm_diag_wait_timeout(int64_t limit_ns, void *stream)
+{
+    g_err.clear();
+    try {
+        if (limit_ns < 1000000 || limit_ns > 5000000000ll) ARG_FAIL("limit_ns must be in [1e6, 5e9]");
+        cudaStream_t st = as_stream(stream);
+        Arena ar(st);
+        int *dev = ar.alloc<int>(2);   // [0] error flag of other CTAs (0), [1] gave up
+        CK(cudaMemsetAsync(dev, 0, 2 * sizeof(int), st));
+        CK(launch_diag_wait(limit_ns, dev, dev + 1, st));
+        g_launches += 1;
+        int gave_up = 0;
+        CK(cudaMemcpyAsync(&gave_up, dev + 1, sizeof gave_up, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (gave_up) {
+            set_err("a device-side wait exceeded its limit of %lld ns", (long long)limit_ns);
+            return SVM_ERR_TIMEOUT;
+        }
+        return SVM_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
 int svm_train_batch(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_batch_config *config,
                     svm_result *results)
 {

@@ -74,7 +74,8 @@ struct SmoCtrl {
     // SM cycles spent by CTA 0 in each phase of a step (summed over steps,
     // recorded only when SmoArgs::phase_times is set):
     // 0 target rows, 1 pair step (FP64 part), 2 row pass + CTA reduction,
-    // 3 publish, 4 grid exchange, 5 other, 6 pair step (K(up,low) part)
+    // 3 publish, 4 grid exchange, 5 other, 6 pair step (K(up,low) part),
+    // 7 second-order gain sweep and exchange
     int64_t phase_cycles[8];
     int64_t kc_hits, kc_misses;   // kernel-row cache lookups (CTA 0)
 };
@@ -249,6 +250,8 @@ cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t sm
 // one cluster (the kernel that launch_smo_persistent picks when G == cs)
 int smo_max_clusters(int mode, int lpr, int resident, size_t smem, int cs);
 size_t smo_cand_bytes();   // bytes of one global candidate slot
+// one bounded wait on an mbarrier that nothing completes (failure-handling check)
+cudaError_t launch_diag_wait(int64_t timeout_ns, const int *err, int *gave_up, cudaStream_t st);
 // shared-memory bytes of a kernel-row cache directory
 __host__ __device__ inline size_t smo_kdir_bytes(int64_t n, int slots, int direct)
 {
