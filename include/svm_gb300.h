@@ -275,6 +275,44 @@ int svm_decision_kernel(const svm_csr *X, const int8_t *y, const double *alpha, 
                         const svm_kernel *kernel, const svm_csr *Z, int32_t precision,
                         void *stream, double *out);
 
+/* ------------------------------------------------------ resident model */
+
+/* A trained model held on the device: the support vectors (the rows of X
+ * with alpha > 0, Section III-A's zeta), their coefficients alpha_i y_i, the
+ * threshold b and the kernel, so that the classifier of Eq. (classi) can be
+ * evaluated on new queries without re-reading the training rows or alpha.
+ * The handle owns its device memory, on the device current at creation. */
+typedef struct svm_model svm_model;
+
+/*
+ * svm_model_create -- gather the support vectors of a trained problem.
+ *   X, y, alpha   the training rows, labels and multipliers of svm_train
+ *                 (one memory space, as in svm_decision; read, not kept)
+ *   b, kernel     threshold and kernel of the training
+ *   precision     arithmetic of later decisions (enum svm_precision)
+ *   out           receives the handle (NULL on error)
+ * Errors: SVM_ERR_ARG (NULL pointers, bad kernel, inputs as for svm_decision),
+ * SVM_ERR_OOM, SVM_ERR_CUDA. Synchronous.
+ */
+int svm_model_create(const svm_csr *X, const int8_t *y, const double *alpha, double b,
+                     const svm_kernel *kernel, int32_t precision, void *stream, svm_model **out);
+
+/*
+ * svm_model_decision -- Eq. (classi) before the sign for the m rows of Z:
+ * out[q] = sum over support vectors k of alpha_k y_k K(x_k, z_q) - b; the
+ * same values as svm_decision_kernel on the model's training inputs.
+ * Z->d must equal the model's d; the current device must be the model's.
+ * out (m doubles) is in Z's memory space. Synchronous; calls on one model
+ * may overlap (the model is only read).
+ */
+int svm_model_decision(const svm_model *model, const svm_csr *Z, void *stream, double *out);
+
+/* Support vectors, columns and threshold of a model (each output nullable). */
+int svm_model_info(const svm_model *model, int64_t *n_sv, int64_t *d, double *b);
+
+/* Releases the model and its device memory (NULL is accepted). */
+int svm_model_free(svm_model *model);
+
 /* ------------------------------------------------------------ batching */
 
 /* One training job of a batch: a two-class subproblem over rows of the shared

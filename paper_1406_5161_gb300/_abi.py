@@ -123,6 +123,14 @@ def load(build_if_missing: bool = True):
             lib.svm_train_fixed_workspace.argtypes = [P, P, P, P, P, P]
             lib.svm_diag_wait_timeout.restype = ct.c_int
             lib.svm_diag_wait_timeout.argtypes = [ct.c_int64, P]
+            lib.svm_model_create.restype = ct.c_int
+            lib.svm_model_create.argtypes = [P, P, P, ct.c_double, P, ct.c_int32, P, P]
+            lib.svm_model_decision.restype = ct.c_int
+            lib.svm_model_decision.argtypes = [P, P, P, P]
+            lib.svm_model_info.restype = ct.c_int
+            lib.svm_model_info.argtypes = [P, P, P, P]
+            lib.svm_model_free.restype = ct.c_int
+            lib.svm_model_free.argtypes = [P]
             _lib = lib
     return _lib
 
@@ -291,6 +299,73 @@ def svm_decision(X, y, alpha, b: float, gamma: float, Z, *, precision: int = SVM
     if check and rc < 0:
         raise SvmError(rc, svm_last_error())
     return out
+
+
+class Model:
+    """A trained model resident on the device (svm_model_* of the C ABI): the
+    support vectors, alpha y, b and the kernel, for repeated decisions."""
+
+    def __init__(self, X, y, alpha, b: float, gamma: float, *, precision: int = SVM_FP64,
+                 kernel: int = SVM_KERNEL_RBF, degree: int = 3, coef0: float = 0.0, stream=None):
+        lib = load()
+        h = _Hold()
+        cx, devx = _csr(h, X)
+        if devx:
+            yp = h.tensor(y, "int8")
+            ap = h.tensor(alpha, "float64")
+        else:
+            yp = h.np(y, np.int8)
+            ap = h.np(alpha, np.float64)
+        k = svm_kernel(int(kernel), int(degree), float(gamma), float(coef0))
+        handle = ct.c_void_p(None)
+        rc = lib.svm_model_create(ct.byref(cx), yp, ap, float(b), ct.byref(k), int(precision),
+                                  _stream_ptr(stream), ct.byref(handle))
+        if rc < 0:
+            raise SvmError(rc, svm_last_error())
+        self._h = handle
+        self._lib = lib
+
+    def decision(self, Z, *, stream=None, out=None):
+        h = _Hold()
+        cz, devz = _csr(h, Z)
+        m = int(Z.n)
+        if devz:
+            import torch
+            if out is None:
+                out = torch.empty(m, dtype=torch.float64, device=Z.indptr.device)
+            op = out.data_ptr()
+        else:
+            if out is None:
+                out = np.zeros(m)
+            op = out.ctypes.data
+        rc = self._lib.svm_model_decision(self._h, ct.byref(cz), _stream_ptr(stream), op)
+        if rc < 0:
+            raise SvmError(rc, svm_last_error())
+        return out
+
+    def info(self) -> dict:
+        n_sv, d, b = ct.c_int64(0), ct.c_int64(0), ct.c_double(0.0)
+        rc = self._lib.svm_model_info(self._h, ct.byref(n_sv), ct.byref(d), ct.byref(b))
+        if rc < 0:
+            raise SvmError(rc, svm_last_error())
+        return {"n_sv": n_sv.value, "d": d.value, "b": b.value}
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value is not None:
+            self._lib.svm_model_free(self._h)
+            self._h = ct.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
 
 
 def svm_train_fixed_workspace(X, y, C: float, gamma: float, tau: float = 1e-3, *,

@@ -14,6 +14,7 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <new>
 #include <mutex>
 #include <thread>
 #include <cmath>
@@ -210,6 +211,7 @@ __global__ void k_seg_nnz(int64_t n, int G, const int64_t *indptr, int64_t *out)
 
 __global__ void k_dense_bf16(int64_t n, int d, int d_pad, const int64_t *indptr, const int32_t *indices,
                              const float *vmix, __nv_bfloat16 *out);
+__global__ void k_iota(int64_t n, int32_t *out);
 
 // ---- active-set re-layout: the active rows of a problem gathered into a
 //      smaller problem (rows kept in increasing index order, so the
@@ -1325,33 +1327,27 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     return status_code;
 }
 
-int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double b, const svm_kernel &K,
-                  const svm_csr *Z, int32_t precision, void *stream, double *out)
+void check_kernel(const svm_kernel &K)
 {
-    if (!X || !Z || !y || !alpha || !out) ARG_FAIL("NULL argument");
-    const double gamma = K.gamma;
-    if (!(gamma > 0)) ARG_FAIL("gamma must be > 0");
+    if (!(K.gamma > 0)) ARG_FAIL("gamma must be > 0");
     if (K.kind < SVM_KERNEL_RBF || K.kind > SVM_KERNEL_SIGMOID) ARG_FAIL("unknown kernel %d", K.kind);
     if (K.kind == SVM_KERNEL_POLY && (K.degree < 1 || K.degree > 64)) ARG_FAIL("polynomial degree must be 1..64");
     if (!std::isfinite(K.coef0)) ARG_FAIL("coef0 must be finite");
-    const bool rbf = K.kind == SVM_KERNEL_RBF;
-    if (Z->d != X->d) ARG_FAIL("Z->d (%lld) must equal X->d (%lld)", (long long)Z->d, (long long)X->d);
-    if (precision < SVM_FP64 || precision > SVM_MIXED_BF16_SIMT) ARG_FAIL("unknown precision %d", precision);
-    if (Z->n == 0) return SVM_OK;
-    cudaStream_t st = as_stream(stream);
+}
+
+// Eq. (classi) before the sign for the queries Z against support vectors:
+// rows list_sv[0 .. nsv) of DX with coefficients coef (alpha y). DX was
+// ingested for this precision; it is taken by value because norms it lacks
+// are derived into the call's arena.
+void decision_eval(Arena &ar, DevCSR DX, const int32_t *list_sv, const double *coef, int64_t nsv, double b,
+                   const svm_kernel &K, const svm_csr *Z, int32_t precision, cudaStream_t st, double *out,
+                   int *launches_out)
+{
     int launches = 0;
-    Arena ar(st);
+    const bool rbf = K.kind == SVM_KERNEL_RBF;
     const bool mixed = precision != SVM_FP64;
-    DevCSR DX, DZ;
-    ingest(ar, X, y, !mixed, mixed, st, DX, &launches, rbf);
+    DevCSR DZ;
     ingest(ar, Z, nullptr, !mixed, mixed, st, DZ, &launches, rbf);
-    const int64_t n = DX.n;
-    const double *alpha_d = alpha;
-    if (!X->on_device) {
-        double *a = ar.alloc<double>(n);
-        CK(cudaMemcpyAsync(a, alpha, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-        alpha_d = a;
-    }
     int mode = (DX.binary && DZ.binary) ? MODE_BINARY : (mixed ? MODE_MIXED : MODE_FP64);
     if (mode != MODE_BINARY && (DX.binary || DZ.binary)) {
         // one side binary, the other not: derive the missing norms
@@ -1370,7 +1366,7 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     double *ktab = nullptr;
     if (mode == MODE_BINARY) {
         ktab = ar.alloc<double>(3 * (size_t)ktab_len);
-        k_ktab<<<grid1(ktab_len), 256, 0, st>>>(gamma, ktab_len, ktab);
+        k_ktab<<<grid1(ktab_len), 256, 0, st>>>(K.gamma, ktab_len, ktab);
         CK(cudaGetLastError());
         ++launches;
     }
@@ -1379,9 +1375,6 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
         set_err("d = %lld exceeds the shared-memory query tile of this mode", (long long)DX.d);
         throw Fail{SVM_ERR_UNSUPPORTED};
     }
-    int32_t *list_sv = ar.alloc<int32_t>(n);
-    double *coef = ar.alloc<double>(n);
-    int64_t nsv = compact(ar, PRED_ALPHA_POS, n, nullptr, alpha_d, DX.y, list_sv, coef, st, &launches);
     double *out_d = out;
     if (!Z->on_device) out_d = ar.alloc<double>(DZ.n);
     RbfContract c;
@@ -1403,7 +1396,7 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
     c.nq = DZ.n;
     c.d = (int32_t)DX.d;
     c.mode = mode;
-    c.gamma = gamma;
+    c.gamma = K.gamma;
     c.kernel = K.kind;
     c.degree = K.degree;
     c.coef0 = K.coef0;
@@ -1427,13 +1420,199 @@ int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double
         CK(launch_rbf_contract(c, st));
         ++launches;
     }
-    g_launches += launches;
     if (!Z->on_device) CK(cudaMemcpyAsync(out, out_d, sizeof(double) * DZ.n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    *launches_out += launches;
+}
+
+int decision_impl(const svm_csr *X, const int8_t *y, const double *alpha, double b, const svm_kernel &K,
+                  const svm_csr *Z, int32_t precision, void *stream, double *out)
+{
+    if (!X || !Z || !y || !alpha || !out) ARG_FAIL("NULL argument");
+    check_kernel(K);
+    const bool rbf = K.kind == SVM_KERNEL_RBF;
+    if (Z->d != X->d) ARG_FAIL("Z->d (%lld) must equal X->d (%lld)", (long long)Z->d, (long long)X->d);
+    if (precision < SVM_FP64 || precision > SVM_MIXED_BF16_SIMT) ARG_FAIL("unknown precision %d", precision);
+    if (Z->n == 0) return SVM_OK;
+    cudaStream_t st = as_stream(stream);
+    int launches = 0;
+    Arena ar(st);
+    const bool mixed = precision != SVM_FP64;
+    DevCSR DX;
+    ingest(ar, X, y, !mixed, mixed, st, DX, &launches, rbf);
+    const int64_t n = DX.n;
+    const double *alpha_d = alpha;
+    if (!X->on_device) {
+        double *a = ar.alloc<double>(n);
+        CK(cudaMemcpyAsync(a, alpha, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        alpha_d = a;
+    }
+    int32_t *list_sv = ar.alloc<int32_t>(n);
+    double *coef = ar.alloc<double>(n);
+    int64_t nsv = compact(ar, PRED_ALPHA_POS, n, nullptr, alpha_d, DX.y, list_sv, coef, st, &launches);
+    decision_eval(ar, DX, list_sv, coef, nsv, b, K, Z, precision, st, out, &launches);
+    g_launches += launches;
     return SVM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Trained model held on the device: the support vectors (rows with alpha > 0,
+// gathered in index order into their own CSR), alpha y and b, so that
+// decisions on new queries re-read neither the training rows nor alpha.
+// ---------------------------------------------------------------------------
 
+// rows idx[0 .. m) of a CSR (entries, values, norms) into a compact CSR
+struct GatherArgs {
+    int64_t m;
+    const int32_t *idx;
+    const int64_t *indptr;
+    const int32_t *indices;
+    const float *values, *vmix, *normf;
+    const double *norm;
+    const int64_t *sub_indptr;
+    int32_t *sub_indices;
+    float *sub_values, *sub_vmix, *sub_normf;
+    double *sub_norm;
+};
+
+__global__ void k_gather_rows(GatherArgs S)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < S.m; j += warps) {
+        const int64_t i = S.idx[j];
+        const int64_t p0 = S.indptr[i], len = S.indptr[i + 1] - p0, q0 = S.sub_indptr[j];
+        for (int64_t k = lane; k < len; k += 32) {
+            S.sub_indices[q0 + k] = S.indices[p0 + k];
+            if (S.sub_values) S.sub_values[q0 + k] = S.values[p0 + k];
+            if (S.sub_vmix) S.sub_vmix[q0 + k] = S.vmix[p0 + k];
+        }
+        if (lane == 0) {
+            if (S.sub_norm) S.sub_norm[j] = S.norm[i];
+            if (S.sub_normf) S.sub_normf[j] = S.normf[i];
+        }
+    }
+}
+
+struct ModelState {
+    int device = 0;
+    DevCSR sv;                      // support-vector rows (model-owned memory)
+    int32_t *list = nullptr;        // 0 .. nsv-1
+    double *coef = nullptr;         // alpha y of each support vector
+    int64_t nsv = 0;
+    double b = 0.0;
+    svm_kernel K{};
+    int32_t precision = SVM_FP64;
+    std::vector<void *> mem;        // device allocations freed with the model
+};
+
+ModelState *model_create_impl(const svm_csr *X, const int8_t *y, const double *alpha, double b,
+                              const svm_kernel &K, int32_t precision, void *stream)
+{
+    if (!X || !y || !alpha) ARG_FAIL("NULL argument");
+    check_kernel(K);
+    if (precision < SVM_FP64 || precision > SVM_MIXED_BF16_SIMT) ARG_FAIL("unknown precision %d", precision);
+    if (!std::isfinite(b)) ARG_FAIL("b must be finite");
+    cudaStream_t st = as_stream(stream);
+    int launches = 0;
+    const bool rbf = K.kind == SVM_KERNEL_RBF;
+    const bool mixed = precision != SVM_FP64;
+    Arena ar(st);     // scratch of this call
+    Arena keep(st);   // what the model keeps (handed over below)
+    DevCSR DX;
+    ingest(ar, X, y, !mixed, mixed, st, DX, &launches, rbf);
+    const int64_t n = DX.n;
+    const double *alpha_d = alpha;
+    if (!X->on_device) {
+        double *a = ar.alloc<double>(n);
+        CK(cudaMemcpyAsync(a, alpha, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        alpha_d = a;
+    }
+    int32_t *list = ar.alloc<int32_t>(n);
+    double *coef_all = ar.alloc<double>(n);
+    const int64_t m = compact(ar, PRED_ALPHA_POS, n, nullptr, alpha_d, DX.y, list, coef_all, st, &launches);
+    std::unique_ptr<ModelState> M(new ModelState());
+    CK(cudaGetDevice(&M->device));
+    M->nsv = m;
+    M->b = b;
+    M->K = K;
+    M->precision = precision;
+    DevCSR S;
+    S.n = m;
+    S.d = DX.d;
+    S.binary = DX.binary;
+    S.maxnnz = DX.maxnnz;
+    int64_t *sub_indptr = keep.alloc<int64_t>(m + 1);
+    int64_t nnz_m = 0;
+    if (m > 0) {
+        const int nb = (int)((m + kChunkRows - 1) / kChunkRows);
+        int64_t *sums = ar.alloc<int64_t>(nb);
+        int64_t *offs = ar.alloc<int64_t>(nb);
+        int64_t *tot = ar.alloc<int64_t>(1);
+        k_sub_len_sums<<<nb, 256, 0, st>>>(m, list, DX.indptr, sums);
+        k_scan64<<<1, 32, 0, st>>>(sums, nb, offs, tot);
+        k_sub_indptr<<<nb, 256, 0, st>>>(m, list, DX.indptr, offs, sub_indptr);
+        CK(cudaGetLastError());
+        launches += 3;
+        CK(cudaMemcpyAsync(&nnz_m, tot, sizeof nnz_m, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        CK(cudaMemsetAsync(sub_indptr, 0, sizeof(int64_t), st));
+    }
+    S.nnz = nnz_m;
+    GatherArgs G;
+    std::memset(&G, 0, sizeof G);
+    G.m = m;
+    G.idx = list;
+    G.indptr = DX.indptr;
+    G.indices = DX.indices;
+    G.values = DX.values;
+    G.vmix = DX.vmix;
+    G.normf = DX.normf;
+    G.norm = DX.norm;
+    G.sub_indptr = sub_indptr;
+    G.sub_indices = keep.alloc<int32_t>(nnz_m);
+    G.sub_values = DX.values ? keep.alloc<float>(nnz_m) : nullptr;
+    G.sub_vmix = DX.vmix ? keep.alloc<float>(nnz_m) : nullptr;
+    G.sub_normf = DX.normf ? keep.alloc<float>(m) : nullptr;
+    G.sub_norm = DX.norm ? keep.alloc<double>(m) : nullptr;
+    if (m > 0) {
+        k_gather_rows<<<(int)std::min<int64_t>((m + 7) / 8, 4096), 256, 0, st>>>(G);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    S.indptr = sub_indptr;
+    S.indices = G.sub_indices;
+    S.values = G.sub_values;
+    S.vmix = G.sub_vmix;
+    S.normf = G.sub_normf;
+    S.norm = G.sub_norm;
+    M->sv = S;
+    M->coef = keep.alloc<double>(std::max<int64_t>(m, 1));
+    M->list = keep.alloc<int32_t>(std::max<int64_t>(m, 1));
+    if (m > 0) {
+        CK(cudaMemcpyAsync(M->coef, coef_all, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+        k_iota<<<grid1(m), 256, 0, st>>>(m, M->list);
+        CK(cudaGetLastError());
+        ++launches;
+    }
+    CK(cudaStreamSynchronize(st));
+    M->mem = std::move(keep.ptrs);
+    keep.ptrs.clear();
+    g_launches += launches;
+    return M.release();
+}
+
+void model_free_impl(ModelState *M)
+{
+    if (!M) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != M->device) cudaSetDevice(M->device);
+    for (void *p : M->mem) cudaFree(p);
+    if (cur != M->device) cudaSetDevice(cur);
+    delete M;
+}
 
 // ---------------------------------------------------------------------------
 // Batched training (many subproblems over one matrix in one launch)
@@ -2296,6 +2475,83 @@ int svm_decision_kernel(const svm_csr *X, const int8_t *y, const double *alpha, 
         set_err("unexpected host exception");
         return SVM_ERR_CUDA;
     }
+}
+
+struct svm_model {
+    ModelState *impl;
+};
+
+int svm_model_create(const svm_csr *X, const int8_t *y, const double *alpha, double b, const svm_kernel *kernel,
+                     int32_t precision, void *stream, svm_model **out)
+{
+    g_err.clear();
+    try {
+        if (!out) ARG_FAIL("out is NULL");
+        *out = nullptr;
+        if (!kernel) ARG_FAIL("kernel is NULL");
+        ModelState *M = model_create_impl(X, y, alpha, b, *kernel, precision, stream);
+        svm_model *h = new (std::nothrow) svm_model;
+        if (!h) {
+            model_free_impl(M);
+            set_err("host allocation failed");
+            return SVM_ERR_OOM;
+        }
+        h->impl = M;
+        *out = h;
+        return SVM_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_model_decision(const svm_model *model, const svm_csr *Z, void *stream, double *out)
+{
+    g_err.clear();
+    try {
+        if (!model || !model->impl || !Z || !out) ARG_FAIL("NULL argument");
+        const ModelState &M = *model->impl;
+        if (Z->d != M.sv.d) ARG_FAIL("Z->d (%lld) must equal the model's d (%lld)", (long long)Z->d, (long long)M.sv.d);
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if (dev != M.device) ARG_FAIL("the model lives on device %d, the current device is %d", M.device, dev);
+        if (Z->n == 0) return SVM_OK;
+        cudaStream_t st = as_stream(stream);
+        int launches = 0;
+        Arena ar(st);
+        decision_eval(ar, M.sv, M.list, M.coef, M.nsv, M.b, M.K, Z, M.precision, st, out, &launches);
+        g_launches += launches;
+        return SVM_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
+int svm_model_info(const svm_model *model, int64_t *n_sv, int64_t *d, double *b)
+{
+    g_err.clear();
+    if (!model || !model->impl) {
+        set_err("model is NULL");
+        return SVM_ERR_ARG;
+    }
+    if (n_sv) *n_sv = model->impl->nsv;
+    if (d) *d = model->impl->sv.d;
+    if (b) *b = model->impl->b;
+    return SVM_OK;
+}
+
+int svm_model_free(svm_model *model)
+{
+    g_err.clear();
+    if (!model) return SVM_OK;
+    model_free_impl(model->impl);
+    delete model;
+    return SVM_OK;
 }
 
 const char *svm_last_error(void) { return g_err.c_str(); }
