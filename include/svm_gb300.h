@@ -200,6 +200,14 @@ typedef struct svm_shrink_policy {
                                 first_factor * tau; <= 0 means 20 (Algorithm 5) */
 } svm_shrink_policy;
 
+/* The paper's three classes of shrinking heuristics (Section IV, Table 3),
+ * with multiple reconstructions: aggressive (counter 5% of N), average (10%)
+ * and lazy (50%). Usable as initialisers:
+ *   svm_shrink_policy p = SVM_SHRINK_AGGRESSIVE; */
+#define SVM_SHRINK_AGGRESSIVE {SVM_SHRINK_FRACTION, SVM_RECON_MULTI, 0.05, 20.0}
+#define SVM_SHRINK_AVERAGE {SVM_SHRINK_FRACTION, SVM_RECON_MULTI, 0.10, 20.0}
+#define SVM_SHRINK_LAZY {SVM_SHRINK_FRACTION, SVM_RECON_MULTI, 0.50, 20.0}
+
 typedef struct svm_stats {
     int64_t iters;           /* SMO steps */
     int64_t shrink_events;

@@ -87,3 +87,22 @@ def test_ctypes_struct_sizes_match_header(tmp_path):
     import ctypes
     for n, s in zip(names, sizes):
         assert ctypes.sizeof(getattr(_abi, n)) == s, n
+
+
+def test_shrink_presets_match_the_python_ones(tmp_path):
+    """SVM_SHRINK_AGGRESSIVE / _AVERAGE / _LAZY initialise the C struct with
+    the Table 3 classes the Python presets name."""
+    prog = ("#include <stdio.h>\n#include \"svm_gb300.h\"\nint main(void){\n"
+            "svm_shrink_policy p[3] = {SVM_SHRINK_AGGRESSIVE, SVM_SHRINK_AVERAGE, SVM_SHRINK_LAZY};\n"
+            "for (int i = 0; i < 3; ++i) printf(\"%d %d %.17g %.17g\\n\", p[i].kind, p[i].recon, p[i].value,"
+            " p[i].first_factor);\nreturn 0;}\n")
+    (tmp_path / "pre.c").write_text(prog)
+    exe = str(tmp_path / "pre")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(tmp_path / "pre.c"),
+                    "-o", exe], check=True)
+    rows = [line.split() for line in subprocess.run([exe], capture_output=True, text=True,
+                                                     check=True).stdout.splitlines()]
+    for row, py in zip(rows, (pkg.AGGRESSIVE, pkg.AVERAGE, pkg.LAZY)):
+        kind, value, recon = py
+        assert int(row[0]) == kind and int(row[1]) == recon and float(row[2]) == value
+        assert float(row[3]) == 20.0
