@@ -127,6 +127,10 @@ typedef struct svm_params {
     int32_t kernel;          /* enum svm_kernel_kind; 0 = RBF (Section V-A) */
     int32_t degree;          /* SVM_KERNEL_POLY: degree >= 1 */
     double coef0;            /* SVM_KERNEL_POLY / SVM_KERNEL_SIGMOID: offset */
+    int64_t *active_trace;   /* optional HOST buffer: (step, active rows) after each of the
+                                first active_trace_len shrink events (Eq. shrink), 2 int64
+                                per event; -1 where no event happened */
+    int64_t active_trace_len;
 } svm_params;
 
 /* Kernels. RBF exp(-gamma ||x - z||^2) is the paper's (Section V-A); the

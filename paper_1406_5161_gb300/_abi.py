@@ -49,7 +49,8 @@ class svm_params(ct.Structure):
                 ("stream", ct.c_void_p), ("trace", ct.c_void_p), ("trace_len", ct.c_int64),
                 ("flags", ct.c_int32), ("ctas", ct.c_int32),
                 ("lanes_per_row", ct.c_int32), ("cache_mb", ct.c_int32),
-                ("kernel", ct.c_int32), ("degree", ct.c_int32), ("coef0", ct.c_double)]
+                ("kernel", ct.c_int32), ("degree", ct.c_int32), ("coef0", ct.c_double),
+                ("active_trace", ct.c_void_p), ("active_trace_len", ct.c_int64)]
 
 
 class svm_kernel(ct.Structure):
@@ -220,8 +221,11 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
               precision: int = SVM_FP64, shrink: tuple | None = None, stream=None,
               trace_len: int = 0, alpha_out=None, flags: int = 0, ctas: int = 0,
               lanes_per_row: int = 0, cache_mb: int = 0, kernel: int = SVM_KERNEL_RBF,
-              degree: int = 3, coef0: float = 0.0, check: bool = True) -> dict:
+              degree: int = 3, coef0: float = 0.0, active_trace_len: int = 0,
+              check: bool = True) -> dict:
     """Train by SMO. ``shrink`` = (kind, value, recon[, first_factor]) or None.
+    ``active_trace_len``: record (step, active rows) after each of the first
+    so many shrink events (returned as ``active_trace``, one row per event).
     ``cache_mb``: kernel-row cache budget in MiB (0 automatic, < 0 off).
     ``kernel``: SVM_KERNEL_* (RBF default; polynomial uses degree, coef0;
     sigmoid uses coef0).
@@ -247,6 +251,10 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
                    _stream_ptr(stream), trace.ctypes.data if trace_len else None, int(trace_len),
                    int(flags), int(ctas), int(lanes_per_row), int(cache_mb), int(kernel), int(degree),
                    float(coef0))
+    atrace = np.full((max(active_trace_len, 0), 2), -1, dtype=np.int64)
+    if active_trace_len:
+        p.active_trace = atrace.ctypes.data
+        p.active_trace_len = int(active_trace_len)
     pol = None
     if shrink is not None:
         kind, value, recon = shrink[:3]
@@ -262,6 +270,8 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
     out = {"status": rc, "alpha": alpha_out, "b": b.value, "iters": it.value, "stats": st.as_dict()}
     if trace_len:
         out["trace"] = trace[: min(trace_len, it.value)]
+    if active_trace_len:
+        out["active_trace"] = atrace[atrace[:, 0] >= 0]
     return out
 
 

@@ -1494,6 +1494,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 counter = A.h < total ? A.h : total;
                 if (counter < 1) counter = 1;
                 ++shrink_events;
+                if (cta == 0 && tid == 0 && shrink_events <= A.atrace_len) {
+                    A.atrace[2 * (shrink_events - 1)] = iter;
+                    A.atrace[2 * (shrink_events - 1) + 1] = total;
+                }
             }
         }
         first = false;

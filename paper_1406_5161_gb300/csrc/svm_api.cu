@@ -897,6 +897,9 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     const int64_t trace_len = (P->trace && P->trace_len > 0) ? P->trace_len : 0;
     int32_t *trace = ar.alloc<int32_t>(2 * std::max<int64_t>(trace_len, 1));
     if (trace_len) CK(cudaMemsetAsync(trace, 0xff, sizeof(int32_t) * 2 * trace_len, st));
+    const int64_t atrace_len = (P->active_trace && P->active_trace_len > 0) ? P->active_trace_len : 0;
+    int64_t *atrace = ar.alloc<int64_t>(2 * std::max<int64_t>(atrace_len, 1));
+    if (atrace_len) CK(cudaMemsetAsync(atrace, 0xff, sizeof(int64_t) * 2 * atrace_len, st));
     k_init<<<grid1(n), 256, 0, st>>>(n, D.y, alpha, f, status);
     k_reset_active<<<G, 256, 0, st>>>(n, G, act, seg_cnt);
     CK(cudaGetLastError());
@@ -939,6 +942,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.ctrl = ctrl;
     A.trace = trace;
     A.trace_len = trace_len;
+    A.atrace = atrace;
+    A.atrace_len = atrace_len;
     A.ktab = ktab;
     A.ktab_len = ktab_len;
     A.maxnnz = D.maxnnz;
@@ -1270,6 +1275,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         tr.resize(2 * trace_len);
         CK(cudaMemcpyAsync(tr.data(), trace, sizeof(int32_t) * 2 * trace_len, cudaMemcpyDeviceToHost, st));
     }
+    if (atrace_len)
+        CK(cudaMemcpyAsync(P->active_trace, atrace, sizeof(int64_t) * 2 * atrace_len, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (trace_len) {
         for (int64_t t = 0; t < trace_len; ++t) {

@@ -142,6 +142,9 @@ struct SmoArgs {
     // row pass on the CUDA cores
     const __nv_bfloat16 *dmat;
     int32_t d_pad;
+    // optional: (step, active rows) after each shrink event, 2 per event
+    int64_t *atrace;
+    int64_t atrace_len;
 };
 
 // ---- batched and served solves: one job = one two-class problem

@@ -31,8 +31,9 @@ def _pair(p, trace_len, **kw):
     Xd = pkg.to_device(p.X)
     yd = torch.as_tensor(p.y, device="cuda")
     flags = kw.pop("flags", 0)
-    a = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, trace_len=trace_len, flags=flags, **kw)
-    b = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, trace_len=trace_len, flags=flags | NO_RELAYOUT, **kw)
+    a = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, trace_len=trace_len, flags=flags, active_trace_len=4096, **kw)
+    b = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, trace_len=trace_len, flags=flags | NO_RELAYOUT,
+                      active_trace_len=4096, **kw)
     return a, b
 
 
@@ -46,6 +47,9 @@ def _same(a, b):
     assert a["stats"]["reconstructions"] == b["stats"]["reconstructions"]
     assert a["stats"]["row_visits"] == b["stats"]["row_visits"]
     assert b["stats"]["relayouts"] == 0
+    # the active-set trajectory (|pi| after each shrink event) is the same too
+    assert np.array_equal(a["active_trace"], b["active_trace"])
+    assert len(a["active_trace"]) == min(4096, a["stats"]["shrink_events"])
 
 
 def _kkt(p, r):

@@ -387,3 +387,24 @@ def test_kernel_arguments_are_checked():
     assert r["status"] == pkg.SVM_ERR_ARG and "kernel" in pkg.svm_last_error()
     r = pkg.svm_train(p.X, p.y, 1.0, 0.1, 1e-3, kernel=pkg.SVM_KERNEL_POLY, degree=0, check=False)
     assert r["status"] == pkg.SVM_ERR_ARG and "degree" in pkg.svm_last_error()
+
+
+def test_active_set_trajectory():
+    """svm_params.active_trace: (step, active rows) after each shrink event of
+    Eq. (shrink): one row per event, steps increasing, sizes within [2, n],
+    shrinking between reconstructions, and the counts the kernel reports."""
+    p = synth.onehot_sparse(n=6000, n_test=0, seed=12)
+    kind, value, recon = pkg.POLICIES["Multi5pc"]
+    r, _, _ = gpu_train(p, shrink=(kind, value, recon), active_trace_len=1000)
+    at = r["active_trace"]
+    s = r["stats"]
+    assert len(at) == s["shrink_events"] >= 2
+    assert (np.diff(at[:, 0]) > 0).all() and at[-1, 0] <= r["iters"]
+    assert (at[:, 1] >= 2).all() and (at[:, 1] <= p.X.n).all()
+    # between two reconstructions the active set only shrinks
+    rises = int((np.diff(at[:, 1]) > 0).sum())
+    assert rises <= s["reconstructions"]
+    # the same solve without a trajectory buffer
+    r2, _, _ = gpu_train(p, shrink=(kind, value, recon))
+    assert r2["iters"] == r["iters"]
+    assert np.array_equal(r2["alpha"].cpu().numpy(), r["alpha"].cpu().numpy())
