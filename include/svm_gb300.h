@@ -131,6 +131,10 @@ typedef struct svm_params {
                                 first active_trace_len shrink events (Eq. shrink), 2 int64
                                 per event; -1 where no event happened */
     int64_t active_trace_len;
+    const double *alpha0;    /* optional warm start (resume): n multipliers in X's memory
+                                space, 0 <= alpha0 <= C and sum y alpha0 = 0 (within
+                                1e-9 max(1, C n)); f is recomputed from them (Eq. fcache)
+                                on the device; NULL = the usual start alpha = 0 */
 } svm_params;
 
 /* Kernels. RBF exp(-gamma ||x - z||^2) is the paper's (Section V-A); the

@@ -50,7 +50,8 @@ class svm_params(ct.Structure):
                 ("flags", ct.c_int32), ("ctas", ct.c_int32),
                 ("lanes_per_row", ct.c_int32), ("cache_mb", ct.c_int32),
                 ("kernel", ct.c_int32), ("degree", ct.c_int32), ("coef0", ct.c_double),
-                ("active_trace", ct.c_void_p), ("active_trace_len", ct.c_int64)]
+                ("active_trace", ct.c_void_p), ("active_trace_len", ct.c_int64),
+                ("alpha0", ct.c_void_p)]
 
 
 class svm_kernel(ct.Structure):
@@ -222,7 +223,7 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
               trace_len: int = 0, alpha_out=None, flags: int = 0, ctas: int = 0,
               lanes_per_row: int = 0, cache_mb: int = 0, kernel: int = SVM_KERNEL_RBF,
               degree: int = 3, coef0: float = 0.0, active_trace_len: int = 0,
-              check: bool = True) -> dict:
+              alpha0=None, check: bool = True) -> dict:
     """Train by SMO. ``shrink`` = (kind, value, recon[, first_factor]) or None.
     ``active_trace_len``: record (step, active rows) after each of the first
     so many shrink events (returned as ``active_trace``, one row per event).
@@ -251,6 +252,8 @@ def svm_train(X, y, C: float, gamma: float, tau: float = 1e-3, *, max_iter: int 
                    _stream_ptr(stream), trace.ctypes.data if trace_len else None, int(trace_len),
                    int(flags), int(ctas), int(lanes_per_row), int(cache_mb), int(kernel), int(degree),
                    float(coef0))
+    if alpha0 is not None:   # warm start, in X's memory space
+        p.alpha0 = h.tensor(alpha0, "float64") if dev else h.np(alpha0, np.float64)
     atrace = np.full((max(active_trace_len, 0), 2), -1, dtype=np.int64)
     if active_trace_len:
         p.active_trace = atrace.ctypes.data

@@ -183,6 +183,18 @@ __global__ void k_init(int64_t n, const int8_t *y, double *alpha, double *f, uin
     status[i] = (uint8_t)(st_of(yi, 0.0, 1.0) | (yi > 0 ? 0x80 : 0));
 }
 
+// Warm start: the given multipliers and their index sets (Eq. setinfo).
+__global__ void k_init_warm(int64_t n, double C, const int8_t *y, const double *alpha0, double *alpha,
+                            uint8_t *status)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int8_t yi = y[i];
+    const double a = alpha0[i];
+    alpha[i] = a;
+    status[i] = (uint8_t)(st_of(yi, a, C) | (yi > 0 ? 0x80 : 0));
+}
+
 // Active lists back to all samples: segment s holds local indices 0..size-1.
 __global__ void k_reset_active(int64_t n, int G, int32_t *act, int32_t *seg_cnt)
 {
@@ -904,6 +916,82 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     k_reset_active<<<G, 256, 0, st>>>(n, G, act, seg_cnt);
     CK(cudaGetLastError());
     launches += 2;
+
+    // warm start (resume): alpha0 checked on the host, index sets from it, and
+    // f = sum_j alpha_j y_j K(x_i, x_j) - y_i (Eq. fcache) by the contraction
+    // that reconstruction uses (support vectors = alpha0 > 0, queries = all)
+    if (P->alpha0) {
+        std::vector<double> a0(n);
+        std::vector<int8_t> yh(n);
+        CK(cudaMemcpyAsync(a0.data(), P->alpha0, sizeof(double) * n,
+                           X->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, st));
+        CK(cudaMemcpyAsync(yh.data(), D.y, n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double ysum = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(a0[i] >= 0.0 && a0[i] <= P->C)) ARG_FAIL("alpha0[%lld] is outside [0, C]", (long long)i);
+            ysum += yh[i] > 0 ? a0[i] : -a0[i];
+        }
+        if (!(std::fabs(ysum) <= 1e-9 * std::max(1.0, P->C * (double)n)))
+            ARG_FAIL("alpha0 violates sum y alpha = 0 (%.3g)", ysum);
+        double *a0d = ar.alloc<double>(n);
+        CK(cudaMemcpyAsync(a0d, a0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+        k_init_warm<<<grid1(n), 256, 0, st>>>(n, P->C, D.y, a0d, alpha, status);
+        CK(cudaGetLastError());
+        ++launches;
+        int32_t *w_sv = ar.alloc<int32_t>(n);
+        double *w_coef = ar.alloc<double>(n);
+        const int64_t w_nsv = compact(ar, PRED_ALPHA_POS, n, nullptr, alpha, D.y, w_sv, w_coef, st, &launches);
+        if (w_nsv > 0) {
+            int32_t *w_q = ar.alloc<int32_t>(n);
+            k_iota<<<grid1(n), 256, 0, st>>>(n, w_q);
+            CK(cudaGetLastError());
+            ++launches;
+            RbfContract c;
+            std::memset(&c, 0, sizeof c);
+            c.x_indptr = D.indptr;
+            c.x_indices = D.indices;
+            c.x_values = mode == MODE_MIXED ? D.vmix : D.values;
+            c.x_norm = D.norm;
+            c.x_normf = D.normf;
+            c.sv = w_sv;
+            c.coef = w_coef;
+            c.nsv = w_nsv;
+            c.z_indptr = D.indptr;
+            c.z_indices = D.indices;
+            c.z_values = c.x_values;
+            c.z_norm = D.norm;
+            c.z_normf = D.normf;
+            c.q = w_q;
+            c.nq = n;
+            c.d = (int32_t)D.d;
+            c.mode = mode;
+            c.gamma = P->gamma;
+            c.kernel = P->kernel;
+            c.degree = P->degree;
+            c.coef0 = P->coef0;
+            c.ktab = ktab;
+            c.ktab_len = ktab_len;
+            c.out_by_row = 1;
+            c.out = f;
+            c.yq = D.y;
+            c.add_scalar = 0.0;
+            if (use_tc && mode == MODE_MIXED && tc_rbf_supported((int)D.d)) {
+                void *ws = ar.alloc<unsigned char>(tc_rbf_workspace_bytes(n, w_nsv, (int)D.d));
+                int tc_err = 0;
+                CK(launch_rbf_contract_tc(c, ws, &tc_err, st));
+                launches += 3;
+                CK(cudaStreamSynchronize(st));
+                if (tc_err) {
+                    set_err("a wait in the tensor-core contraction exceeded its limit");
+                    throw Fail{SVM_ERR_TIMEOUT};
+                }
+            } else {
+                CK(launch_rbf_contract(c, st));
+                ++launches;
+            }
+        }
+    }
 
     const bool shrink_on = sp.kind != SVM_SHRINK_NONE;
     int64_t h = 0;
@@ -2280,6 +2368,7 @@ struct FixedCarve {
 int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, double *alpha_out,
                      double *b_out, int64_t *iters_out)
 {
+    if (P && P->alpha0) ARG_FAIL("alpha0 (warm start) is not taken by the fixed-workspace solve");
     if (!X || !P || !y || !alpha_out || !b_out) ARG_FAIL("NULL argument");
     if (!X->on_device) ARG_FAIL("the fixed-workspace call takes device buffers only (on_device = 1)");
     if (!(P->C > 0) || !std::isfinite(P->C)) ARG_FAIL("C must be > 0");
