@@ -184,7 +184,7 @@ typedef struct svm_kernel {
  * candidate exchange. svm_train and svm_train_fixed_workspace only. */
 #define SVM_FLAG_WSS2 16
 /* With shrinking, a launch over a problem that is not already one on-chip
- * cluster ends once fewer than half of its rows are active; the active rows
+ * cluster ends once fewer than three quarters of its rows are active; the active rows
  * are gathered (in index order) into a smaller problem whose launch shape is
  * chosen again, and the state is scattered back when it ends. The steps are
  * the same either way (same pairs, same arithmetic); this flag turns the

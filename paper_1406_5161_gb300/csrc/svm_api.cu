@@ -1064,8 +1064,9 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     CK(cudaEventCreate(&e1));
     double ms_smo = 0.0, ms_recon = 0.0;
     // Active-set re-layout (with shrinking): a launch over a problem that is
-    // not already one on-chip cluster ends once fewer than half of its rows
-    // are active; the active rows are gathered, in index order, into a
+    // not already one on-chip cluster ends once a quarter of its rows have
+    // been shrunk (measured: 3.47 -> 3.29 s against waiting for half of them
+    // on the covtype-shaped workload, no gain from waiting for an eighth); the active rows are gathered, in index order, into a
     // smaller problem whose launch shape is chosen again (segments on chip,
     // a single cluster), and its state is scattered back when its launch
     // ends. Rows keep their order, so every step is the one the parent
@@ -1116,7 +1117,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         A.dmat = L.dmat;
         A.d_pad = d_pad;
         const bool one_cluster_on_chip = L.shape.resident && L.shape.cs == L.shape.G;
-        A.compact_below = (relayout_ok && hh > 0 && !one_cluster_on_chip && L.n >= 2048) ? L.n / 2 : 0;
+        A.compact_below = (relayout_ok && hh > 0 && !one_cluster_on_chip && L.n >= 2048) ? L.n * 3 / 4 : 0;
         CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(seq, 0, sizeof(unsigned) * smo_seq_words(L.shape.G), st));
         A.thr = thr;

@@ -1,8 +1,8 @@
 """GPU tests of the active-set re-layout (through the C ABI).
 
 With shrinking (Eq. shrink, Algorithms 4-5), a launch over a problem that is
-not already one on-chip cluster ends once fewer than half of its rows are
-active; the active rows are gathered in index order into a smaller problem
+not already one on-chip cluster ends once fewer than three quarters of its
+rows are active; the active rows are gathered in index order into a smaller problem
 that gets its own launch shape, and the state is scattered back when that
 launch ends. Rows keep their order, so the lowest-index tie-break of Eq.
 (bminmax) and every step's arithmetic are unchanged: a solve with the
