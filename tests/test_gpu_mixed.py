@@ -147,7 +147,7 @@ def test_covtype_581012_fp64_and_mixed():
     d64 = pkg.svm_decision(Xd, yd, r64["alpha"], r64["b"], p.gamma, Zsd).cpu().numpy()
     dor = oracle.decision(p.X, p.y, a64, r64["b"], p.gamma, Zs)
     assert np.abs(d64 - dor).max() <= 1e-9 * max(1.0, np.abs(dor).max())
-    # mixed against FP64 (errors reported in the design doc)
+    # mixed against FP64 (the errors are printed with -s)
     Zd = pkg.to_device(p.Z)
     dz64 = pkg.svm_decision(Xd, yd, r64["alpha"], r64["b"], p.gamma, Zd).cpu().numpy()
     dzmx = pkg.svm_decision(Xd, yd, rmx["alpha"], rmx["b"], p.gamma, Zd,
