@@ -128,3 +128,25 @@ def test_no_relayout_without_shrinking_or_for_one_cluster():
     assert a["stats"]["cluster_size"] == 16
     _same(a, b)
     assert a["stats"]["relayouts"] == 0
+
+
+@pytest.mark.timeout(600)
+def test_automatic_shape_with_relayout_against_the_oracle():
+    """FP64, 40,000 covtype-shaped rows: the automatic shape starts on
+    clusters of 8 with on-chip segments and, as shrinking proceeds, moves
+    through re-laid-out levels to one cluster. Against the oracle (plain
+    Algorithm 1): the first 200 pairs (the first shrink test comes later),
+    and the end state under the oracle's KKT check and objective."""
+    from test_gpu_smo import check_end_state, first_mismatch
+    p = synth.covtype_like(n=40000, n_test=0, seed=9)
+    oracle.set_threads(oracle.max_threads())
+    ref = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, trace_len=300)
+    assert ref["status"] == 0
+    Xd = pkg.to_device(p.X)
+    yd = torch.as_tensor(p.y, device="cuda")
+    r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=pkg.POLICIES["Multi5pc"], trace_len=300)
+    assert r["status"] == pkg.SVM_OK
+    assert r["stats"]["cluster_size"] == 8 and r["stats"]["relayouts"] >= 1
+    t = first_mismatch(r["trace"], ref["trace"], ref.get("margin"), 300)
+    assert t >= 200
+    check_end_state(p, r, ref)
