@@ -490,6 +490,13 @@ int64_t svm_kernel_launches(void);
  * out of range. Synchronous. */
 int svm_diag_wait_timeout(int64_t limit_ns, void *stream);
 
+/* Measurement aid (the paper has no counterpart): the rate of the SFU's
+ * exp2 instruction over the whole device, from a kernel of independent
+ * ex2.approx chains (the instruction of the RBF contraction's epilogue), so
+ * that the contraction can be reported against the exp rate it is bound by.
+ * ex2_per_s receives instructions per second. Synchronous. */
+int svm_diag_sfu_rate(double *ex2_per_s, void *stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char *svm_last_error(void);
 

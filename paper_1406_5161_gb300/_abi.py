@@ -125,6 +125,8 @@ def load(build_if_missing: bool = True):
             lib.svm_train_fixed_workspace.argtypes = [P, P, P, P, P, P]
             lib.svm_diag_wait_timeout.restype = ct.c_int
             lib.svm_diag_wait_timeout.argtypes = [ct.c_int64, P]
+            lib.svm_diag_sfu_rate.restype = ct.c_int
+            lib.svm_diag_sfu_rate.argtypes = [P, P]
             lib.svm_model_create.restype = ct.c_int
             lib.svm_model_create.argtypes = [P, P, P, ct.c_double, P, ct.c_int32, P, P]
             lib.svm_model_decision.restype = ct.c_int
@@ -139,6 +141,15 @@ def load(build_if_missing: bool = True):
 
 def svm_kernel_launches() -> int:
     return int(load().svm_kernel_launches())
+
+
+def svm_diag_sfu_rate(stream=None) -> float:
+    """SFU exp2 instructions per second over the whole device (measured)."""
+    v = ct.c_double(0.0)
+    rc = load().svm_diag_sfu_rate(ct.byref(v), _stream_ptr(stream))
+    if rc != SVM_OK:
+        raise SvmError(rc, svm_last_error())
+    return v.value
 
 
 def svm_diag_wait_timeout(limit_ns: int, stream=None) -> int:

@@ -2655,6 +2655,22 @@ const char *svm_last_error(void) { return g_err.c_str(); }
 
 int64_t svm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
+int svm_diag_sfu_rate(double *ex2_per_s, void *stream)
+{
+    g_err.clear();
+    try {
+        if (!ex2_per_s) ARG_FAIL("NULL argument");
+        CK(measure_sfu_ex2(ex2_per_s, as_stream(stream)));
+        g_launches += 2;
+        return SVM_OK;
+    } catch (const Fail &f) {
+        return f.code;
+    } catch (...) {
+        set_err("unexpected host exception");
+        return SVM_ERR_CUDA;
+    }
+}
+
 int svm_diag_wait_timeout(int64_t limit_ns, void *stream)
 {
     g_err.clear();

@@ -253,6 +253,8 @@ cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t sm
 // one cluster (the kernel that launch_smo_persistent picks when G == cs)
 int smo_max_clusters(int mode, int lpr, int resident, size_t smem, int cs);
 size_t smo_cand_bytes();   // bytes of one global candidate slot
+// SFU exp2 instructions per second over the whole GPU (microbenchmark)
+cudaError_t measure_sfu_ex2(double *ops_per_s, cudaStream_t st);
 // one bounded wait on an mbarrier that nothing completes (failure-handling check)
 cudaError_t launch_diag_wait(int64_t timeout_ns, const int *err, int *gave_up, cudaStream_t st);
 // shared-memory bytes of a kernel-row cache directory

@@ -479,4 +479,53 @@ cudaError_t launch_rbf_contract_tc(const RbfContract &c, void *ws, int *err_host
     return e;
 }
 
+
+// SFU exp2 rate (microbenchmark for the contraction's roofline): every thread
+// runs 8 independent chains of ex2.approx, the instruction of the epilogue.
+__global__ void k_sfu_ex2(int iters, float seed, float *sink)
+{
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed * (float)(j + 1) * 1e-3f - (float)(threadIdx.x & 7) * 1e-4f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float r;
+            asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[j]));
+            a[j] = r * -0.5f;   // stays in (-1, 1): no overflow, no denormals
+        }
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc += a[j];
+    if (acc == 12345.f) sink[blockIdx.x] = acc;   // keeps the loop alive
+}
+
+cudaError_t measure_sfu_ex2(double *ops_per_s, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    float *sink = nullptr;
+    if ((e = cudaMallocAsync(&sink, sizeof(float) * blocks, st)) != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_sfu_ex2<<<blocks, threads, 0, st>>>(iters / 8, 0.5f, sink);   // warm-up
+    cudaEventRecord(e0, st);
+    k_sfu_ex2<<<blocks, threads, 0, st>>>(iters, 0.5f, sink);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(sink, st);
+    if (e == cudaSuccess) *ops_per_s = (double)blocks * threads * iters * 8 / (ms * 1e-3);
+    return e;
+}
+
 }  // namespace svmgb

@@ -43,3 +43,12 @@ def test_wait_that_runs_out_returns_timeout_and_context_stays_usable(limit_ms):
 def test_wait_limits_are_checked():
     assert pkg.svm_diag_wait_timeout(10) == pkg.SVM_ERR_ARG
     assert pkg.svm_diag_wait_timeout(10**10) == pkg.SVM_ERR_ARG
+
+
+def test_sfu_rate_microbenchmark_is_plausible():
+    """svm_diag_sfu_rate: ex2.approx instructions per second over the device,
+    within a factor of the nominal 16 per clock per SM."""
+    r = pkg.svm_diag_sfu_rate()
+    props = torch.cuda.get_device_properties(0)
+    nominal = 16.0 * props.multi_processor_count * 2.1e9
+    assert 0.2 * nominal <= r <= 2.0 * nominal, (r, nominal)
