@@ -126,6 +126,31 @@ struct TcArgs {
 };
 
 // 2^x on the special-function unit (flush to zero below 2^-126)
+// packed pairs of FP32 values (f32x2 arithmetic, sm_100 and later)
+__device__ __forceinline__ unsigned long long pack_f32x2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack_f32x2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, unsigned long long b,
+                                                       unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -255,7 +280,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
             // slot (t+1) % 3, last read by the epilogue of tile t-2)
             if (t + 1 < ntiles) load_tile(t + 1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float part0 = 0.f, part1 = 0.f;
+            unsigned long long part = pack_f32x2(0.f, 0.f);   // (columns j, j + 1) partial sums
+            const unsigned long long zc2 = pack_f32x2(zc, zc), g2v = pack_f32x2(a.g2, a.g2);
 #pragma unroll 1
             for (int c0 = half * (kTile / 2); c0 < (half + 1) * (kTile / 2); c0 += 32) {
                 uint32_t r[32];
@@ -271,25 +297,34 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
                       "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                     : "r"(addr)
                     : "memory");
-                // the tile's constants for these 32 columns, as vectors
-                float xc[32], cf[32];
+                // the tile's constants for these 32 columns as column pairs:
+                // zc + xc (the row's and the column's scaled norms) and coef.
+                // The FP32 arithmetic runs on packed pairs (f32x2), half the
+                // instructions of the scalar form and the same IEEE result
+                // in each lane.
+                unsigned long long xz[16], cf[16];
 #pragma unroll
                 for (int v = 0; v < 8; ++v) {
                     const float4 x4 = reinterpret_cast<const float4 *>(&s_xc[pc][c0])[v];
                     const float4 c4 = reinterpret_cast<const float4 *>(&s_coef[pc][c0])[v];
-                    xc[4 * v] = x4.x; xc[4 * v + 1] = x4.y; xc[4 * v + 2] = x4.z; xc[4 * v + 3] = x4.w;
-                    cf[4 * v] = c4.x; cf[4 * v + 1] = c4.y; cf[4 * v + 2] = c4.z; cf[4 * v + 3] = c4.w;
+                    xz[2 * v] = add_f32x2(pack_f32x2(x4.x, x4.y), zc2);
+                    xz[2 * v + 1] = add_f32x2(pack_f32x2(x4.z, x4.w), zc2);
+                    cf[2 * v] = pack_f32x2(c4.x, c4.y);
+                    cf[2 * v + 1] = pack_f32x2(c4.z, c4.w);
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 32; j += 2) {
                     // log2 K = -gamma log2(e) (||z||^2 + ||x||^2 - 2 <z, x>), clamped at 0
-                    const float e0 = fminf(fmaf(__uint_as_float(r[j]), a.g2, zc + xc[j]), 0.f);
-                    const float e1 = fminf(fmaf(__uint_as_float(r[j + 1]), a.g2, zc + xc[j + 1]), 0.f);
-                    part0 = fmaf(cf[j], ex2_approx(e0), part0);
-                    part1 = fmaf(cf[j + 1], ex2_approx(e1), part1);
+                    float e0, e1;
+                    unpack_f32x2(fma_f32x2(pack_f32x2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])), g2v,
+                                           xz[j >> 1]), e0, e1);
+                    const unsigned long long k2 = pack_f32x2(ex2_approx(fminf(e0, 0.f)), ex2_approx(fminf(e1, 0.f)));
+                    part = fma_f32x2(cf[j >> 1], k2, part);
                 }
             }
+            float part0, part1;
+            unpack_f32x2(part, part0, part1);
             acc += (double)(part0 + part1);
             // accumulator pb is rewritten by the MMA of tile t+1 only after
             // the next iteration's barrier
