@@ -42,14 +42,13 @@ def test_onehot_sparse_recipe():
     assert (p.X.n, p.X.d, p.Z.n) == (32561, 123, 10000)
     assert (_rows_nnz(p.X) == 14).all()
     assert p.X.values is None or (p.X.values == 1.0).all()
-    sizes = np.asarray(p.meta["group_sizes"]) if "group_sizes" in p.meta else None
+    sizes = np.asarray(p.meta["group_sizes"])
     cols = p.X.indices.reshape(-1, 14)
     assert (np.diff(cols, axis=1) > 0).all()           # sorted, distinct
-    if sizes is not None:
-        assert sizes.sum() == 123 and len(sizes) == 14 and (sizes >= 2).all()
-        edges = np.r_[0, np.cumsum(sizes)]
-        for g in range(14):
-            assert ((cols[:, g] >= edges[g]) & (cols[:, g] < edges[g + 1])).all()
+    assert sizes.sum() == 123 and len(sizes) == 14 and (sizes >= 2).all()
+    edges = np.r_[0, np.cumsum(sizes)]
+    for g in range(14):
+        assert ((cols[:, g] >= edges[g]) & (cols[:, g] < edges[g + 1])).all()
     pos = (np.concatenate([p.y, p.yz]) > 0).mean()
     # 24% positive, then 5% of all labels flipped: 0.24 (0.95) + 0.76 (0.05)
     assert abs(pos - (0.24 * 0.95 + 0.76 * 0.05)) < 0.01
