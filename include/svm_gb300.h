@@ -451,18 +451,28 @@ int svm_server_destroy(svm_server *srv);
  * process that reserved the whole device before it started.
  *
  * All scratch (gradient, index sets, active lists, exchange slots, tables,
- * reductions) lives in one 4 MiB array that the library reserves in every
- * GPU's memory when it is loaded and keeps until the process exits. The
+ * reductions) lives in one 4 MiB file-scope device array. CUDA places it in
+ * a GPU's memory when the library's code is first loaded on that GPU: under
+ * lazy module loading (CUDA's default) that is the first call of this
+ * library that runs device work there, not the moment the shared object is
+ * opened. It then stays until the process exits. A caller that caps or
+ * reserves device memory should therefore make one call first (a small
+ * warm-up problem through this entry point) on each GPU it will use. The
  * caller passes the inputs and the output buffer in device memory:
  *   X         device CSR (X->on_device must be 1), 2 <= n <= 131072 rows,
- *             at most 4096 entries in a row
+ *             d < 2^31, at most 4096 entries in a row
  *   y         n device labels (+1 / -1)
  *   params    C, gamma, tau, max_iter, stream; precision must be SVM_FP64;
- *             trace, flags, ctas and lanes_per_row are ignored
+ *             flags other than SVM_FLAG_WSS2 are ignored, as are trace,
+ *             ctas and lanes_per_row
  *   alpha_out n doubles of device memory, written with the multipliers
  *   b_out     host double; iters_out host int64 (may be NULL)
  * Larger problems return SVM_ERR_UNSUPPORTED with a message naming the
- * limit; other results are those of svm_train.
+ * limit; d >= 2^31 returns SVM_ERR_ARG before any device work. Binary input
+ * (every stored value 1.0) whose distance tables do not fit in shared
+ * memory takes the FP64 row pass, as in svm_train; it then needs explicit
+ * values (values == NULL there gives SVM_ERR_UNSUPPORTED). Other results are
+ * those of svm_train.
  *
  * The first call on each device looks up the device address of the array
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -2313,8 +2313,10 @@ double ms_between(std::chrono::steady_clock::time_point a, std::chrono::steady_c
 // a call: code running inside a memory-capped or externally managed pool, a
 // real-time loop that must not block on the allocator, or a host that
 // reserved the whole device up front. For them every piece of scratch the
-// solve needs lives in one file-scope device array that the library reserves
-// when it is loaded; inputs and outputs are the caller's device buffers.
+// solve needs lives in one file-scope device array, placed in a GPU's memory
+// when this file's code is first loaded there (with lazy module loading, the
+// first call that runs device work on that GPU); inputs and outputs are the
+// caller's device buffers.
 // ---------------------------------------------------------------------------
 constexpr int64_t kFixedMaxRows = 131072;            // largest n accepted
 constexpr int kFixedMaxRowNnz = 4096;                // longest row accepted
@@ -2379,6 +2381,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     if (P->kernel != SVM_KERNEL_RBF) ARG_FAIL("the fixed-workspace call supports the RBF kernel only");
     if (P->tie_break != 0) ARG_FAIL("only the lowest-index tie-break (0) is implemented");
     if (X->n < 2 || X->d < 1) ARG_FAIL("need n >= 2 and d >= 1");
+    if (X->d >= (int64_t)INT32_MAX) ARG_FAIL("d must be < 2^31");
     if (X->n > kFixedMaxRows) {
         set_err("n = %lld exceeds the fixed workspace limit of %lld rows", (long long)X->n,
                 (long long)kFixedMaxRows);
@@ -2410,9 +2413,20 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
         set_err("a row has %d entries; the fixed workspace accepts at most %d", h.maxnnz, kFixedMaxRowNnz);
         throw Fail{SVM_ERR_UNSUPPORTED};
     }
-    const bool binary = !h.not_binary;
-    const int mode = binary ? MODE_BINARY : MODE_FP64;
+    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
+    // binary input whose distance tables do not fit in shared memory takes
+    // the generic FP64 row pass with norms, as svm_train does
+    bool binary = !h.not_binary;
     const int ktab_len = 2 * h.maxnnz + 1;
+    if (binary && smo_layout(MODE_BINARY, (int)X->d, ktab_len, h.maxnnz, 0, 0, 0).total > lim_dyn) {
+        if (!X->values) {
+            set_err("d = %lld is too large for the binary tables and values is NULL (the FP64 row "
+                    "pass of the fixed-workspace call needs explicit values)", (long long)X->d);
+            throw Fail{SVM_ERR_UNSUPPORTED};
+        }
+        binary = false;
+    }
+    const int mode = binary ? MODE_BINARY : MODE_FP64;
     double *norm = nullptr, *ktab = nullptr;
     if (binary) {
         ktab = W.take<double>(3 * (size_t)ktab_len);
@@ -2431,7 +2445,6 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     const int sms = device_sms();
     int G = (int)std::min<int64_t>(sms, std::max<int64_t>(1, (n + 15) / 16));
     if (G > 256) G = 256;
-    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
     const SmoLayout L0 = smo_layout(mode, (int)X->d, binary ? ktab_len : 0, h.maxnnz, 0, 0, 0);
     if (L0.total > lim_dyn) {
         set_err("d = %lld exceeds the shared-memory target rows of this mode", (long long)X->d);

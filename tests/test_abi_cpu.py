@@ -106,3 +106,24 @@ def test_shrink_presets_match_the_python_ones(tmp_path):
         kind, value, recon = py
         assert int(row[0]) == kind and int(row[1]) == recon and float(row[2]) == value
         assert float(row[3]) == 20.0
+
+
+def test_fixed_workspace_rejects_huge_d_before_any_device_work():
+    """d >= 2^31 cannot be carried by the row pass's 32-bit column layout; the
+    fixed-workspace call must refuse it from its argument checks alone (the
+    pointers below are never read, and no CUDA call is made on this host)."""
+    import ctypes as ct
+    from paper_1406_5161_gb300 import _abi
+    lib = pkg.load()
+    dummy = (ct.c_double * 16)()
+    addr = ct.addressof(dummy)
+    for d in (2 ** 31, 2 ** 32 + 5):
+        X = _abi.svm_csr(10, d, addr, addr, addr, 1, 0)
+        p = _abi.svm_params()
+        p.C, p.gamma, p.tau, p.precision = 1.0, 0.1, 1e-3, pkg.SVM_FP64
+        b = ct.c_double(0.0)
+        it = ct.c_int64(0)
+        rc = lib.svm_train_fixed_workspace(ct.byref(X), addr, ct.byref(p), addr, ct.byref(b),
+                                           ct.byref(it))
+        assert rc == pkg.SVM_ERR_ARG, d
+        assert "d must be < 2^31" in pkg.svm_last_error()
