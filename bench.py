@@ -1,19 +1,24 @@
 #!/usr/bin/env python3
-"""Benchmark of the GB300 SVM trainer on the a9a-shaped one-hot workload.
+"""Benchmark of the GB300 SVM trainer.
 
-Workload: n = 32,561 training rows, d = 123 binary columns (14 one-hot
-groups, exactly 14 ones per row), labels from an RBF teacher (24% positive,
-5% flipped), RBF gamma = 0.05, C = 1, tau = 1e-3, plus 10,000 held-out rows.
-All inputs are seeded synthetic data (paper_1406_5161_gb300.synth); the
-paper's own datasets are not used.
+Default workload (the benchmark line): the covtype-shaped problem,
+n = 581,012 training rows, d = 54 (10 dense N(0,1) columns and one-hot blocks
+of 4 and 40 columns, 12 stored entries per row), labels from a random tanh
+MLP (49% positive), RBF gamma = 0.1, C = 4, tau = 1e-3, plus 10,000 held-out
+rows, trained in FP64 (the paper's arithmetic). All inputs are seeded
+synthetic data (paper_1406_5161_gb300.synth); the paper's own datasets are
+not used.
 
 One step = one full training to the KKT tolerance through the C ABI
 (svm_train: ingest, fused SMO steps with adaptive shrinking, gradient
 reconstruction, threshold b) followed by the decision function on the 10,000
 held-out rows (svm_decision). The metric is SMO iterations per second over
-the timed steps; time-to-KKT is reported beside it.
+the timed steps; time-to-KKT is reported beside it, and, for the default
+workload, the same solve in the mixed-precision pattern and the a9a-shaped
+one-hot workload as extra fields.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload covtype|onehot|batch|serve|recon] [--precision fp64|mixed]
 
 With N > 1 (launched by torch.distributed.run) every rank trains its own
 replica (the solve does not shard); the value is the sum of all ranks'
@@ -40,36 +45,52 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SMO iter/s"
 UNIT = "iter/s"
-WORKLOAD = ("onehot_sparse (a9a-shaped): n=32561, d=123, 14 ones/row, C=1, gamma=0.05, "
-            "tau=1e-3; train to KKT + decision on 10000 held-out rows")
+WORKLOADS = {
+    "covtype": ("covtype-shaped: n=581012, d=54 (10 dense + one-hot 4 + one-hot 40, 12 entries/row), "
+                "C=4, gamma=0.1, tau=1e-3; train to KKT + decision on 10000 held-out rows"),
+    "onehot": ("onehot_sparse (a9a-shaped): n=32561, d=123, 14 ones/row, C=1, gamma=0.05, "
+               "tau=1e-3; train to KKT + decision on 10000 held-out rows"),
+}
+# fastest measured Table-3 policy per workload and precision
+DEFAULT_POLICY = {("covtype", "fp64"): "Multi500", ("covtype", "mixed"): "Multi500",
+                  ("onehot", "fp64"): "Multi5pc", ("onehot", "mixed"): "Multi5pc"}
+DTYPE = {"fp64": "f64", "mixed": "mixed (bf16 values, f32 dots/exp, f64 f/step/b)"}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="covtype", choices=["covtype", "onehot", "batch", "serve", "recon"],
+                    help="covtype: the benchmark line (581,012 rows); onehot: the a9a-shaped "
+                         "workload; batch: the one-vs-one x C x gamma grid (405 jobs) batched vs "
+                         "one job at a time; serve: the served Poisson stream; recon: the "
+                         "tensor-core contraction")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="covtype / onehot: FP64 throughout, or the mixed-precision pattern")
     ap.add_argument("--policy", default=None,
-                    help="shrinking policy (Table 3); default Multi5pc, and Multi500 for the "
-                         "covtype workload (fastest of the policies measured there)")
+                    help="shrinking policy (Table 3); default: the fastest measured for the "
+                         "workload and precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="reference arm: about how long its warm-up and timed steps take together")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra fields (other precision, the a9a-shaped workload)")
     ap.add_argument("--serve-jobs", type=int, default=100)
     ap.add_argument("--serve-nmax", type=int, default=10000)
     ap.add_argument("--serve-cluster", type=int, default=0, help="CTAs per served job (0 = server default)")
     ap.add_argument("--serve-burst", action="store_true",
                     help="submit every job at time 0 (saturated server) instead of the Poisson times")
-    ap.add_argument("--workload", default="onehot", choices=["onehot", "batch", "serve", "recon", "covtype"],
-                    help="onehot: the benchmark line; batch: the one-vs-one x C x gamma grid "
-                         "(405 jobs) batched vs one job at a time")
     ap.add_argument("--plain-sample", type=int, default=27,
                     help="batch workload: jobs trained one at a time for the comparison")
     ap.add_argument("--wss2", action="store_true",
-                    help="onehot / covtype: choose i_low by the second-order gain "
+                    help="covtype / onehot: choose i_low by the second-order gain "
                          "(SVM_FLAG_WSS2) instead of the first-order rule")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap SMO steps per solve (profiling of small cases; not a bench value)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -159,10 +180,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
+def measured_traffic(workload: str, precision: str):
     """DRAM bytes per launch of the fused step kernel from the committed ncu
-    summary, or None when the kernel source changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "smo_step_c2_traffic.json")
+    summary of this workload, or None when there is none or the kernel source
+    changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"smo_step_{workload}_{precision}_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
@@ -170,7 +192,7 @@ def measured_traffic():
         return None
     if rec.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
 
 
 def peaks():
@@ -182,9 +204,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload():
+def workload(name: str):
     from paper_1406_5161_gb300 import synth
-    return synth.onehot_sparse()
+    return synth.covtype_like() if name == "covtype" else synth.onehot_sparse()
+
+
+def row_bytes(p, precision: str, binary: bool) -> tuple[float, float]:
+    """Algorithmic bytes of the fused step: per active row visited, and per
+    step for the two target rows. Per row: the CSR entries (column index, plus
+    the value unless every value is 1.0), the row pointer, f read and write,
+    the index set, and for non-binary rows the norm (FP64: 8 B per entry + 29,
+    125 B at 12 entries; mixed precision with BF16 values: 6 B per entry + 29,
+    101 B; binary: 4 B per entry + 25, 81 B at 14 entries)."""
+    nnz_row = p.X.nnz / p.X.n
+    if binary:
+        per_entry, fixed = 4.0, 8 + 16 + 1
+    elif precision == "fp64":
+        per_entry, fixed = 8.0, 29
+    else:
+        per_entry, fixed = 6.0, 29
+    return per_entry * nnz_row + fixed, 2 * per_entry * nnz_row
 
 
 # ---------------------------------------------------------------- reference arm
@@ -192,10 +231,16 @@ def run_reference(args, rank):
     if rank != 0:
         return 0
     import oracle
-    p = workload()
+    name = args.workload if args.workload in WORKLOADS else "covtype"
+    p = workload(name)
     cores = len(os.sched_getaffinity(0))
     oracle.set_threads(cores)
-    m = 400  # SMO steps per timed step: a bounded prefix of the solve
+    # SMO steps per timed step: a bounded prefix of the solve, sized so that
+    # warm-up and timed steps together take about two minutes
+    t0 = time.perf_counter()
+    oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=50)
+    per = (time.perf_counter() - t0) / 50
+    m = int(max(50, min(15000, args.ref_seconds / max(1, args.steps + args.warmup) / max(per, 1e-6))))
     for _ in range(args.warmup):
         oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=m)
     t0 = time.perf_counter()
@@ -208,9 +253,11 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "policy": "Original (oracle has no shrinking)"},
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[name], "policy": "Original (oracle has no shrinking)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {m} SMO steps of the workload per step (FP64 oracle, Algorithm 1)"},
+                             "sample": f"first {m} SMO steps of the workload per step (FP64 oracle, "
+                                       "Algorithm 1, no shrinking)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -232,9 +279,9 @@ def cpu_baseline(p):
     # shorter prefix
     oracle.set_threads(1)
     t0 = time.perf_counter()
-    oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=20)
-    per1 = (time.perf_counter() - t0) / 20
-    m1 = int(max(20, min(m, 4.0 / max(per1, 1e-6))))
+    oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=10)
+    per1 = (time.perf_counter() - t0) / 10
+    m1 = int(max(10, min(m, 4.0 / max(per1, 1e-6))))
     t0 = time.perf_counter()
     r1 = oracle.smo(p.X, p.y, p.C, p.gamma, p.tau, max_iter=m1)
     dt1 = time.perf_counter() - t0
@@ -247,6 +294,37 @@ def cpu_baseline(p):
 
 
 # ---------------------------------------------------------------- GPU arm
+def solve_once(pkg, p, precision: str, policy_name: str, steps: int, warmup: int, flush, stream,
+               with_decision: bool = True):
+    """Untimed-by-contract extra: `steps` solves (after `warmup`) of another
+    precision or workload, timed with CUDA events like the main line."""
+    import torch
+    Xd = pkg.to_device(p.X)
+    yd = torch.as_tensor(p.y, device="cuda")
+    Zd = pkg.to_device(p.Z)
+    prec = pkg.SVM_FP64 if precision == "fp64" else pkg.SVM_MIXED_BF16
+    policy = pkg.POLICIES[policy_name]
+    for _ in range(warmup):
+        pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream)
+    torch.cuda.synchronize()
+    ms, iters, objs = [], 0, []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream)
+        if with_decision:
+            pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, precision=prec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters += r["iters"]
+        objs.append(r["stats"]["objective"])
+    return {"value": iters / (sum(ms) / 1e3), "unit": UNIT, "time_to_kkt_ms": statistics.mean(ms),
+            "iters_per_solve": iters / steps, "objective": objs[-1], "policy": policy_name,
+            "steps": steps, "dtype": DTYPE[precision]}
+
+
 def run_gb300(args, rank, world, local):
     import numpy as np
     import torch
@@ -260,8 +338,9 @@ def run_gb300(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     pkg.load()
-    p = workload()
+    p = workload(args.workload)
     policy = pkg.POLICIES[args.policy]
+    prec = pkg.SVM_FP64 if args.precision == "fp64" else pkg.SVM_MIXED_BF16
     flags = pkg.SVM_FLAG_WSS2 if args.wss2 else 0
     Xd = pkg.to_device(p.X)
     yd = torch.as_tensor(p.y, device="cuda")
@@ -269,14 +348,13 @@ def run_gb300(args, rank, world, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    def step():
-        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream,
-                          max_iter=args.max_iter, flags=flags)
-        dz = pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
-        return r, dz
+    def train(X, y, **kw):
+        return pkg.svm_train(X, y, p.C, p.gamma, p.tau, shrink=policy, precision=prec,
+                             max_iter=args.max_iter, flags=flags, **kw)
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        r = train(Xd, yd, stream=stream)
+        pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, precision=prec, stream=stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -289,15 +367,13 @@ def run_gb300(args, rank, world, local):
     e2 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     iters = row_visits = 0
     ms_smo = ms_recon = 0.0
-    smo_launch_count = 0
     stats = None
     for k in range(args.steps):
         flush.zero_()                    # L2 flushed between timed steps
         e0[k].record(stream)
-        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, stream=stream,
-                          max_iter=args.max_iter, flags=flags)
+        r = train(Xd, yd, stream=stream)
         e1[k].record(stream)
-        pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, stream=stream)
+        pkg.svm_decision(Xd, yd, r["alpha"], r["b"], p.gamma, Zd, precision=prec, stream=stream)
         e2[k].record(stream)
         stats = r["stats"]
         iters += r["iters"]
@@ -333,11 +409,10 @@ def run_gb300(args, rank, world, local):
             dist.barrier()
         t0 = time.perf_counter()
         e2e_iters = 0
-        n_e2e = max(1, min(3, args.steps))
+        n_e2e = 1 if args.workload == "covtype" else max(1, min(3, args.steps))
         for _ in range(n_e2e):
-            r = pkg.svm_train(Xh, yh, p.C, p.gamma, p.tau, shrink=policy, alpha_out=alpha_h,
-                              max_iter=args.max_iter, flags=flags)
-            pkg.svm_decision(Xh, yh, alpha_h, r["b"], p.gamma, Zh, out=out_h)
+            r = train(Xh, yh, alpha_out=alpha_h)
+            pkg.svm_decision(Xh, yh, alpha_h, r["b"], p.gamma, Zh, precision=prec, out=out_h)
             e2e_iters += r["iters"]
         dt, e2e_all = job_totals(dist, time.perf_counter() - t0, float(e2e_iters), "cuda")
         nbytes = lambda X: X.indptr.nbytes + X.indices.nbytes + X.values.nbytes  # noqa: E731
@@ -352,35 +427,46 @@ def run_gb300(args, rank, world, local):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the fused step kernel
-    nnz_row = p.X.nnz / p.X.n
-    b_row = 4 * nnz_row + 8 + 16 + 1
-    alg_bytes = row_visits * b_row + iters * 2 * 4 * nnz_row
+    # ---- roofline of the fused step kernel (algorithmic bytes / kernel time)
+    b_row, b_targets = row_bytes(p, args.precision, bool(stats["binary_input"]))
+    alg_bytes = row_visits * b_row + iters * b_targets
     achieved = alg_bytes / (ms_smo / 1e3) / 1e9
     peak, peak_kind = peaks()
-    traffic = measured_traffic()
+    trec = measured_traffic(args.workload, args.precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "smo_persistent_kernel",
+                "frac": achieved / peak, "traffic": trec["dram_bytes_per_launch"] if trec else None,
+                "kernel": "smo_persistent_kernel",
                 "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                 "bytes_per_row_visit": b_row, "row_visits_per_step": row_visits / args.steps,
                 "kernel_ms_per_step": ms_smo / args.steps}
+    if trec:
+        roofline["traffic_launch"] = trec.get("launch")
+        roofline["traffic_alg_bytes"] = trec.get("alg_bytes_per_launch")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "policy": args.policy,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "policy": args.policy,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "n": int(p.X.n), "d": int(p.X.d), "held_out": int(p.Z.n)},
             "time_to_kkt_ms": statistics.mean(kkt_ms),
             "iters_per_solve": iters / args.steps,
             "recon_ms_per_step": ms_recon / args.steps,
+            "objective": stats["objective"],
             "gpu_launches": int(launches),
             "clocks": clk, "roofline": roofline, "e2e": e2e}
     if args.max_iter:
         line["config"]["max_iter"] = args.max_iter
     if args.wss2:
         line["config"]["selection"] = "second-order i_low (SVM_FLAG_WSS2)"
+    if world == 1 and not args.no_extras and args.workload == "covtype" and not args.max_iter:
+        other = "mixed" if args.precision == "fp64" else "fp64"
+        line["extra_" + other] = solve_once(pkg, p, other, DEFAULT_POLICY[("covtype", other)], 1, 1,
+                                            flush, stream)
+        line["extra_onehot"] = dict(solve_once(pkg, workload("onehot"), "fp64",
+                                               DEFAULT_POLICY[("onehot", "fp64")], 5, 3, flush, stream),
+                                    workload=WORKLOADS["onehot"])
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p)
     print(json.dumps(line), flush=True)
@@ -452,78 +538,6 @@ def run_batch(args):
                               "job_iters_per_s": sum(r["iters"] for r in plain) / plain_s},
             "speedup_trains_per_s": batch_tps / plain_tps,
             "objective_rel_diff_max": max(rel)}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_covtype(args):
-    """The precision pattern at full size: covtype-shaped 581,012 rows, d = 54,
-    trained to KKT in mixed precision (BF16 values, FP32 dots and exp, FP64 f,
-    pair step and b) with Multi5pc shrinking. The fused step streams its
-    segments from HBM here (they do not fit in shared memory), so its roofline
-    is the HBM copy bandwidth."""
-    import torch
-    import paper_1406_5161_gb300 as pkg
-    from paper_1406_5161_gb300 import synth
-
-    torch.cuda.set_device(0)
-    p = synth.covtype_like()
-    Xd = pkg.to_device(p.X)
-    yd = torch.as_tensor(p.y, device="cuda")
-    policy = pkg.POLICIES[args.policy]
-    prec = pkg.SVM_MIXED_BF16
-    flags = pkg.SVM_FLAG_WSS2 if args.wss2 else 0
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    for _ in range(max(args.warmup, 1)):
-        pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream,
-                      flags=flags, max_iter=args.max_iter)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
-    iters = visits = 0
-    ms_smo = ms_recon = 0.0
-    ev = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, shrink=policy, precision=prec, stream=stream,
-                          flags=flags, max_iter=args.max_iter)
-        e1.record(stream)
-        ev.append((e0, e1))
-        s = r["stats"]
-        iters += r["iters"]
-        visits += s["row_visits"]
-        ms_smo += s["ms_smo"]
-        ms_recon += s["ms_recon"]
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    nnz_row = p.X.nnz / p.X.n
-    # per active row: column index and value (4 + 4 B per entry), row pointer,
-    # f read + write, index set, FP32 norm, active-list entry
-    b_row = 8 * nnz_row + 8 + 16 + 1 + 4 + 4
-    alg = visits * b_row + iters * 2 * 8 * nnz_row
-    achieved = alg / (ms_smo / 1e3) / 1e9
-    peak, kind = peaks()
-    line = {"metric": METRIC, "value": iters / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "dtype": "mixed (bf16 values, f32 dots/exp, f64 f/step/b)", "data": "synthetic",
-            "config": {"workload": "covtype-shaped: n=581012, d=54, 12 entries/row, C=4, gamma=0.1, "
-                                   "tau=1e-3, train to KKT", "policy": args.policy,
-                       "l2": "flushed between timed solves (256 MiB write)"},
-            "time_to_kkt_ms": 1e3 * t / args.steps, "iters_per_solve": iters / args.steps,
-            "recon_ms_per_step": ms_recon / args.steps, "clocks": clk,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "smo_persistent_kernel",
-                         "peak_source": f"{kind} hbm_gbs (burst copy)", "bytes_per_row_visit": b_row,
-                         "row_visits_per_step": visits / args.steps,
-                         "kernel_ms_per_step": ms_smo / args.steps}}
-    if args.wss2:
-        line["config"]["selection"] = "second-order i_low (SVM_FLAG_WSS2)"
-    if args.max_iter:
-        line["config"]["max_iter"] = args.max_iter
     print(json.dumps(line), flush=True)
     return 0
 
@@ -670,7 +684,7 @@ def run_serve(args):
 def main():
     args = parse()
     if args.policy is None:
-        args.policy = "Multi500" if args.workload == "covtype" else "Multi5pc"
+        args.policy = DEFAULT_POLICY.get((args.workload, args.precision), "Multi5pc")
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank)
@@ -680,8 +694,6 @@ def main():
         return run_serve(args)
     if args.workload == "recon":
         return run_recon(args)
-    if args.workload == "covtype":
-        return run_covtype(args)
     return run_gb300(args, rank, world, local)
 
 

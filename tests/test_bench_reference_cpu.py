@@ -17,7 +17,8 @@ def _lines(out):
 
 
 def test_reference_arm_prints_one_contract_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1",
+                        "--ref-seconds", "4"],
                        cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = _lines(r.stdout)
@@ -35,7 +36,8 @@ def test_reference_arm_under_two_ranks_prints_once():
         port = s.getsockname()[1]
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
                         "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py",
-                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1",
+                        "--ref-seconds", "4"],
                        cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _lines(r.stdout)
