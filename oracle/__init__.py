@@ -16,7 +16,12 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                  to f recomputed from scratch); KKT gap at exit.
   smo_shrink     reaches the no-shrink optimum (structural fact of the paper:
                  shrinking changes the path, never the optimum); equals smo
-                 with shrinking off; hand-checked Eq. (shrink) cases.
+                 with shrinking off; keeps the plain run's pairs until late;
+                 its schedule (the step of every shrink test and
+                 reconstruction, the counter h = k or ceil(p N), the reset to
+                 min(h, |active|), the 20 tau / 2 tau phase thresholds, the
+                 Multi restart and the Single stop) equals the one derived
+                 from Algorithms 4 and 5 and Table 3 in the tests.
   dot / kernel   dense numpy inner product; closed forms.
   gradient,
   reconstruct    recomputation from the definition (Eq. fcache) with numpy.
@@ -86,7 +91,8 @@ def _bind(path: str):
     lib.or_smo_shrink.restype = ct.c_int
     lib.or_smo_shrink.argtypes = [P, P, ct.c_double, ct.c_double, ct.c_double,
                                   ct.c_int64, ct.c_int, ct.c_double, ct.c_int,
-                                  ct.c_double, P, P, P, P, ct.c_int64, P, ct.c_int]
+                                  ct.c_double, P, P, P, P, ct.c_int64, P, ct.c_int,
+                                  P, P, P, ct.c_int64, P]
     lib.or_gradient.restype = None
     lib.or_gradient.argtypes = [P, P, P, ct.c_double, P]
     lib.or_reconstruct.restype = None
@@ -253,9 +259,14 @@ def smo_wss2(X, y, C: float, gamma: float, tau: float, max_iter: int = 10**9,
 
 def smo_shrink(X, y, C: float, gamma: float, tau: float, kind: int, value: float,
                recon: int, first_factor: float = 20.0, max_iter: int = 10**9,
-               trace_len: int = 0, wss: int = 1, lib=None) -> dict:
+               trace_len: int = 0, wss: int = 1, events: int = 0, lib=None) -> dict:
     """Algorithms 4/5 (+ the multiple-reconstruction variant) with Algorithm 6.
-    ``wss=2`` chooses i_low by the second-order gain over the active rows."""
+    ``wss=2`` chooses i_low by the second-order gain over the active rows.
+    ``trace_len`` > 0 records per step the pair, the active-set size and the
+    active-set gap (``trace``, ``active``, ``gap``); ``events`` > 0 records up
+    to that many schedule events as rows (steps completed, kind 1 = shrink /
+    2 = reconstruction, active rows after, triggering gap, gap over all rows
+    after a reconstruction) in ``events`` (``n_events`` counts all)."""
     k = _Keep()
     n = int(X.n)
     alpha = np.zeros(n)
@@ -263,17 +274,30 @@ def smo_shrink(X, y, C: float, gamma: float, tau: float, kind: int, value: float
     res = _Result()
     trace = np.full((max(trace_len, 0), 2), -1, dtype=np.int64)
     act = np.zeros(max(trace_len, 0), dtype=np.int64)
+    gap = np.full(max(trace_len, 0), np.nan)
+    ev = np.full((max(events, 0), 3), -1, dtype=np.int64)
+    evg = np.full((max(events, 0), 2), np.nan)
+    nev = ct.c_int64(0)
     (lib or _load()).or_smo_shrink(k.csr(X), _ptr(k.arr(y, np.int8)), C, gamma, tau, int(max_iter),
                           int(kind), float(value), int(recon), float(first_factor),
                           _ptr(alpha), _ptr(f), ct.byref(res),
                           _ptr(trace) if trace_len else None, int(trace_len),
-                          _ptr(act) if trace_len else None, int(wss))
+                          _ptr(act) if trace_len else None, int(wss),
+                          _ptr(gap) if trace_len else None,
+                          _ptr(ev) if events else None, _ptr(evg) if events else None,
+                          int(events), ct.byref(nev))
     out = _result(res)
     out.update(alpha=alpha, f=f)
     if trace_len:
         m = min(trace_len, res.iters)
         out["trace"] = trace[:m]
         out["active"] = act[:m]
+        out["gap"] = gap[:m]
+    if events:
+        m = min(events, nev.value)
+        out["events"] = [{"step": int(ev[e, 0]), "kind": int(ev[e, 1]), "active": int(ev[e, 2]),
+                          "gap": float(evg[e, 0]), "gap_all": float(evg[e, 1])} for e in range(m)]
+        out["n_events"] = int(nev.value)
     return out
 
 

@@ -633,10 +633,24 @@ int or_smo_wss2(const or_csr *X, const int8_t *y, double C, double gamma, double
     return status;
 }
 
+/*
+ * Algorithms 4 and 5 with Algorithm 6. Optional records (each may be NULL):
+ *   trace / active_trace (trace_len): pair and active-set size of each step;
+ *   gap_trace (trace_len): b_low - b_up of the selection that chose each
+ *     step's pair, over the active rows (the quantity the phase threshold of
+ *     Algorithm 5 is tested on);
+ *   ev (3 * ev_cap) and ev_gap (2 * ev_cap): the events of the schedule in
+ *     order, (steps completed, kind, active rows after) with kind 1 = shrink
+ *     (Algorithm 4) and 2 = reconstruction (Algorithm 6); ev_gap holds the
+ *     active-set gap that triggered the event and, for a reconstruction, the
+ *     gap over all rows after it (Algorithm 5's stopping test). *n_ev receives
+ *     the number of events (it may exceed ev_cap; only ev_cap are stored).
+ */
 int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, double tau,
                   int64_t max_iter, int kind, double value, int recon, double first_factor,
                   double *alpha, double *f, or_result *res,
-                  int64_t *trace, int64_t trace_len, int64_t *active_trace, int wss)
+                  int64_t *trace, int64_t trace_len, int64_t *active_trace, int wss,
+                  double *gap_trace, int64_t *ev, double *ev_gap, int64_t ev_cap, int64_t *n_ev)
 {
     int64_t n = X->n;
     double *nrm = row_norms(X);
@@ -659,7 +673,7 @@ int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, doub
     int shrinking = kind != OR_SHRINK_NONE;
     int64_t counter = h;
     double thr = shrinking ? first_factor * tau : 2.0 * tau;
-    int64_t it = 0, n_shrink = 0, n_recon = 0;
+    int64_t it = 0, n_shrink = 0, n_recon = 0, ne = 0;
     int status = 0;
     or_sel s = select_pair(m, act, f, set);
     for (;;) {
@@ -672,6 +686,7 @@ int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, doub
             }
             if (trace && it < trace_len) { trace[2 * it] = u; trace[2 * it + 1] = l; }
             if (active_trace && it < trace_len) active_trace[it] = m;
+            if (gap_trace && it < trace_len) gap_trace[it] = s.b_low - s.b_up;
             double kuu = kern(X, nrm, gamma, u, u), kll = kern(X, nrm, gamma, l, l);
             double kul = kern(X, nrm, gamma, u, l);
             or_step st = alpha_step(C, y[u], y[l], alpha[u], alpha[l], f[u], f[l], kuu, kll, kul);
@@ -699,6 +714,11 @@ int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, doub
                 counter = h < m ? h : m;
                 if (counter < 1) counter = 1;
                 ++n_shrink;
+                if (ev && ne < ev_cap) {
+                    ev[3 * ne] = it + 1; ev[3 * ne + 1] = 1; ev[3 * ne + 2] = m;
+                    if (ev_gap) { ev_gap[2 * ne] = s.b_low - s.b_up; ev_gap[2 * ne + 1] = NAN; }
+                }
+                ++ne;
             }
             ++it;
             s = select_pair(m, act, f, set);
@@ -720,9 +740,15 @@ int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, doub
             }
         }
         ++n_recon;
+        const double gap_active = s.b_low - s.b_up;
         for (int64_t i = 0; i < n; ++i) { act[i] = i; live[i] = 1; }
         m = n;
         s = select_pair(m, act, f, set);
+        if (ev && ne < ev_cap) {
+            ev[3 * ne] = it; ev[3 * ne + 1] = 2; ev[3 * ne + 2] = m;
+            if (ev_gap) { ev_gap[2 * ne] = gap_active; ev_gap[2 * ne + 1] = s.b_low - s.b_up; }
+        }
+        ++ne;
         if (s.b_low - s.b_up <= 2.0 * tau) break;
         if (recon == OR_RECON_SINGLE) {
             shrinking = 0;
@@ -740,6 +766,7 @@ int or_smo_shrink(const or_csr *X, const int8_t *y, double C, double gamma, doub
     res->n_recon = n_recon;
     res->final_active = m;
     res->status = status;
+    if (n_ev) *n_ev = ne;
     free(shr);
     free(live);
     free(act);

@@ -232,6 +232,109 @@ def check_shrink_keeps_path(lib=None):
     assert first >= 0.5 * plain["iters"], (first, plain["iters"])
 
 
+# ------------------------------------------------------------ shrink schedule
+# Table 3 / Section III-C: the counter h is a fixed k, or ceil(p N) for a
+# fraction p of the N samples. Algorithm 4: the shrink test runs when the
+# counter, decremented every step, reaches zero, and the counter is then set
+# to the smaller of h and the active-set size. Algorithm 5 (and its multiple
+# reconstruction variant): the first reconstruction happens at the first
+# selection whose active-set gap b_low - b_up is <= 20 tau, later ones at
+# <= 2 tau; after each, the gap over all rows decides: stop at <= 2 tau, else
+# continue from the full set, with shrinking restarted at counter h (Multi) or
+# switched off (Single). The expected schedule below is derived from these
+# definitions alone and compared with the events the oracle records.
+SCHEDULE_CASES = [
+    # (tau, kind, value, recon): each exercises a part of the definition
+    (2e-4, oracle.SHRINK_FIXED, 500, oracle.RECON_MULTI),      # reset to |pi| < h
+    (2e-4, oracle.SHRINK_FIXED, 300, oracle.RECON_SINGLE),     # reset; Single stop
+    (1e-3, oracle.SHRINK_FRACTION, 0.05, oracle.RECON_MULTI),  # ceil(0.05 * 1501) = 76; Multi restart
+    (1e-3, oracle.SHRINK_FRACTION, 0.10, oracle.RECON_SINGLE), # ceil(0.10 * 1501) = 151
+    (1e-3, oracle.SHRINK_FIXED, 2, oracle.RECON_MULTI),        # shrink test every other step
+]
+
+
+def _schedule_problem():
+    # N = 1501 makes p N non-integer for the fractions above
+    return synth.onehot_sparse(n=1501, n_test=0, seed=41)
+
+
+def _expected_h(kind, value, n):
+    # the cases keep p N away from an integer, so ceil is unambiguous
+    import math
+    if kind == oracle.SHRINK_FIXED:
+        return int(value)
+    assert abs(value * n - round(value * n)) > 1e-6
+    return math.ceil(value * n)
+
+
+def check_shrink_schedule(lib=None, cases=SCHEDULE_CASES):
+    p = _schedule_problem()
+    n = p.X.n
+    for tau, kind, value, recon in cases:
+        run = oracle.smo_shrink(p.X, p.y, p.C, p.gamma, tau, kind, value, recon, max_iter=MAXIT,
+                                trace_len=MAXIT, events=100000, lib=lib)
+        tag = (tau, kind, value, recon)
+        assert run["status"] == 0, tag
+        ev, gap, act = run["events"], run["gap"], run["active"]
+        assert run["n_events"] == len(ev), tag
+        assert len(gap) == run["iters"], tag
+        h = _expected_h(kind, value, n)
+        assert h >= 1
+        next_shrink, thr, phase, shrinking, m = h, 20.0 * tau, 0, True, n
+        n_shrink = n_recon = 0
+        for j, e in enumerate(ev):
+            t = e["step"]
+            if e["kind"] == 1:
+                # Algorithm 4: a shrink test exactly when the counter expires
+                assert shrinking, (tag, "shrink event after shrinking was switched off", e)
+                assert t == next_shrink, (tag, "shrink at", t, "expected", next_shrink)
+                assert e["active"] <= m, (tag, "Eq. (shrink) only removes rows", e)
+                assert e["gap"] == gap[t - 1], tag
+                m = e["active"]
+                next_shrink = t + max(1, min(h, m))
+                n_shrink += 1
+            else:
+                assert e["kind"] == 2, e
+                # Algorithm 5: the phase ends at its first selection with gap <= thr
+                assert np.all(gap[phase:t] > thr), (tag, "a selection at or below the threshold "
+                                                    "before the reconstruction", phase, t, thr)
+                assert e["gap"] <= thr, (tag, e, thr)
+                assert not shrinking or next_shrink > t, (tag, "a shrink test was due", next_shrink, t)
+                assert e["active"] == n, tag
+                n_recon += 1
+                phase, m = t, n
+                if e["gap_all"] <= 2.0 * tau:
+                    assert j == len(ev) - 1 and run["iters"] == t, (tag, "must stop here")
+                else:
+                    thr = 2.0 * tau
+                    if recon == oracle.RECON_MULTI:
+                        next_shrink = t + h
+                    else:
+                        shrinking = False
+        # the last phase: no selection reached its threshold before the end,
+        # and no shrink test was due
+        if not ev or ev[-1]["kind"] != 2:
+            assert np.all(gap[phase:] > thr), (tag, "the final phase ran past its threshold")
+            assert not shrinking or next_shrink > run["iters"], tag
+        assert n_recon >= 1, (tag, "shrinking runs end with a reconstruction")
+        assert n_shrink == run["n_shrink"] and n_recon == run["n_recon"], tag
+        # the per-step active-set size follows the events
+        cur, k = n, 0
+        for t in range(run["iters"]):
+            while k < len(ev) and ev[k]["step"] <= t:
+                cur = ev[k]["active"]
+                k += 1
+            assert act[t] == cur, (tag, t, act[t], cur)
+        # the recorded gaps are those of the state: at exit the gap over all
+        # rows recomputed from alpha (Eq. fcache) equals the last one recorded
+        kk = oracle.kkt(p.X, p.y, run["alpha"], p.C, p.gamma, lib=lib)
+        assert abs(kk["gap"] - (run["b_low"] - run["b_up"])) <= 1e-9, tag
+        assert kk["gap"] <= 2.0 * tau + 1e-9, tag
+        if ev[-1]["kind"] == 2 and ev[-1]["gap_all"] <= 2.0 * tau:
+            assert abs(ev[-1]["gap_all"] - kk["gap"]) <= 1e-9, tag
+    return True
+
+
 # ---------------------------------------------------------------- other kernels
 # Section V: other kernels are straightforward to use. Linear <x,z>,
 # polynomial (gamma <x,z> + coef0)^degree, sigmoid tanh(gamma <x,z> + coef0).
@@ -384,6 +487,7 @@ ALL_CHECKS = [
     check_shrink_same_optimum,
     check_shrink_none_is_plain,
     check_shrink_keeps_path,
+    check_shrink_schedule,
     check_linear_two_point_closed_form,
     check_kernels_bruteforce,
     check_linear_decision_is_primal,

@@ -261,9 +261,11 @@ def shrink_problem():
 def test_shrinking_policies_match_oracle(shrink_problem, name):
     p, plain = shrink_problem
     kind, value, recon = pkg.POLICIES[name]
-    ref = oracle.smo_shrink(p.X, p.y, p.C, p.gamma, p.tau, kind, value, recon, trace_len=100000)
+    ref = oracle.smo_shrink(p.X, p.y, p.C, p.gamma, p.tau, kind, value, recon, trace_len=100000,
+                            events=100000)
     flags = pkg.SVM_FLAG_STREAM_ROWS if name.startswith("Single") else 0
-    r, _, _ = gpu_train(p, shrink=(kind, value, recon), trace_len=100000, flags=flags)
+    r, _, _ = gpu_train(p, shrink=(kind, value, recon), trace_len=100000, flags=flags,
+                        active_trace_len=100000)
     assert r["status"] == pkg.SVM_OK
     # pairs: identical to the oracle's shrinking run (near ties excepted via
     # the plain run's margins over the common prefix)
@@ -275,6 +277,12 @@ def test_shrinking_policies_match_oracle(shrink_problem, name):
     if not len(diff) and r["iters"] == ref["iters"]:
         assert r["stats"]["shrink_events"] == ref["n_shrink"]
         assert r["stats"]["reconstructions"] == ref["n_recon"]
+        # the schedule itself (Algorithm 4, Table 3): the step of every shrink
+        # test and the active-set size after it equal the oracle's, whose
+        # schedule is pinned to the definitions on the CPU
+        want = np.array([(e["step"], e["active"]) for e in ref["events"] if e["kind"] == 1],
+                        dtype=np.int64).reshape(-1, 2)
+        assert np.array_equal(r["active_trace"], want)
     check_end_state(p, r, plain)
 
 

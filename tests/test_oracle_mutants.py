@@ -43,6 +43,12 @@ MUTANTS = {
     "wss2_shrink_first_order": ("l = select_low2(X, nrm, gamma, m, act, f, set, u, &gap2);",
                                 "l = s.i_low; (void)gap2;"),
     "wss2_shrink_ignores_active": ("const int64_t t = act ? act[k] : k;", "const int64_t t = k;"),
+    "shrink_counter_floor": ("h = (int64_t)ceil(value * (double)n);", "h = (int64_t)floor(value * (double)n);"),
+    "shrink_reset_to_h": ("counter = h < m ? h : m;", "counter = h;"),
+    "first_recon_at_2tau": ("double thr = shrinking ? first_factor * tau : 2.0 * tau;",
+                            "double thr = 2.0 * tau;"),
+    "multi_restart_stale_counter": ("        } else {\n            counter = h;\n        }\n        thr = 2.0 * tau;",
+                                    "        } else {\n        }\n        thr = 2.0 * tau;"),
     "recon_never_resets": ("for (int64_t i = 0; i < n; ++i) { act[i] = i; live[i] = 1; }\n        m = n;",
                            "for (int64_t i = 0; i < n; ++i) { live[i] = 1; }"),
 }
@@ -51,6 +57,7 @@ MUTANTS = {
 ORDER = [P.check_kernel_closed_form, P.check_dot_and_norm, P.check_two_point_closed_form,
          P.check_invariants, P.check_gradient_and_decision, P.check_bruteforce,
          P.check_shrink_none_is_plain, P.check_shrink_keeps_path, P.check_shrink_same_optimum,
+         P.check_shrink_schedule,
          P.check_linear_two_point_closed_form, P.check_kernels_bruteforce,
          P.check_linear_decision_is_primal, P.check_kernels_invariants, P.check_wss2,
          P.check_wss2_shrink]
