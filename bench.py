@@ -83,8 +83,10 @@ def parse(argv=None):
     ap.add_argument("--serve-cluster", type=int, default=0, help="CTAs per served job (0 = server default)")
     ap.add_argument("--serve-burst", action="store_true",
                     help="submit every job at time 0 (saturated server) instead of the Poisson times")
-    ap.add_argument("--plain-sample", type=int, default=27,
-                    help="batch workload: jobs trained one at a time for the comparison")
+    ap.add_argument("--plain-sample", type=int, default=0,
+                    help="batch workload: jobs trained one at a time for the comparison "
+                         "(0 = all 405; a smaller sample covers all 9 (C, gamma) cells of "
+                         "evenly spaced pairs)")
     ap.add_argument("--wss2", action="store_true",
                     help="covtype / onehot: choose i_low by the second-order gain "
                          "(SVM_FLAG_WSS2) instead of the first-order rule")
@@ -509,9 +511,12 @@ def run_batch(args):
     # one job at a time on a sample: all 9 (C, gamma) cells of evenly spaced pairs
     npairs = len(mc.ovo_pairs())
     cells = len(mc.Cs) * len(mc.gammas)
-    take = max(1, args.plain_sample // cells)
-    pairs = [round(k * (npairs - 1) / max(1, take - 1)) for k in range(take)] if take > 1 else [0]
-    idx = [pp * cells + c for pp in pairs for c in range(cells)]
+    if args.plain_sample <= 0 or args.plain_sample >= len(jobs):
+        idx = list(range(len(jobs)))
+    else:
+        take = max(1, args.plain_sample // cells)
+        pairs = [round(k * (npairs - 1) / max(1, take - 1)) for k in range(take)] if take > 1 else [0]
+        idx = [pp * cells + c for pp in pairs for c in range(cells)]
     subs = [(pkg.to_device(mc.X.take(jobs[i]["rows"])), torch.as_tensor(jobs[i]["y"], device="cuda")) for i in idx]
     pkg.svm_train(subs[0][0], subs[0][1], jobs[idx[0]]["C"], jobs[idx[0]]["gamma"], mc.tau, precision=prec)
     torch.cuda.synchronize()
@@ -537,7 +542,11 @@ def run_batch(args):
                               "iters": int(sum(r["iters"] for r in plain)),
                               "job_iters_per_s": sum(r["iters"] for r in plain) / plain_s},
             "speedup_trains_per_s": batch_tps / plain_tps,
-            "objective_rel_diff_max": max(rel)}
+            "objective_rel_diff_max": max(rel),
+            "objective_rel_diff_jobs": len(rel),
+            "objective_rel_diff_over_1e-5": int(sum(x > 1e-5 for x in rel)),
+            "pair_rows_min_max": [int(min(len(jobs[i]["rows"]) for i in idx)),
+                                  int(max(len(jobs[i]["rows"]) for i in idx))]}
     print(json.dumps(line), flush=True)
     return 0
 

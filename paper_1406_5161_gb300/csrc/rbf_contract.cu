@@ -11,6 +11,7 @@
 // reduced in a fixed order, so results are deterministic.
 #include <cuda_runtime.h>
 
+#include "fp64_math.cuh"
 #include "svm_internal.cuh"
 
 namespace svmgb {
@@ -24,6 +25,7 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ double red[kCWarps][TQ];
+    __shared__ double exp2_s[MODE == MODE_FP64 ? kExp2TabLen : 1];   // FP64: table-driven exp
     __shared__ double zn[TQ];
     __shared__ int zlen[TQ];
     __shared__ int zrow[TQ];
@@ -38,6 +40,9 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
     Elem *Zt = reinterpret_cast<Elem *>(dsm);
     const int tile_words = MODE == MODE_BINARY ? d : d * TQ;
     for (int w = tid; w < tile_words; w += kCThreads) Zt[w] = (Elem)0;
+    if constexpr (MODE == MODE_FP64) {
+        for (int w = tid; w < kExp2TabLen; w += kCThreads) exp2_s[w] = kExp2Tab[w];
+    }
     if (tid < TQ) {
         int r = -1;
         if (tid < nt) r = c.q ? c.q[qbase + tid] : (int)(qbase + tid);
@@ -57,6 +62,7 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
         for (int64_t p = p0 + tid; p < p1; p += kCThreads) {
             const int col = c.z_indices[p];
             if constexpr (MODE == MODE_BINARY) atomicOr(&Zt[col], 1u << q);
+            else if constexpr (MODE == MODE_FP64) Zt[(size_t)col * TQ + q] = widen_f32(c.z_values[p]);
             else Zt[(size_t)col * TQ + q] = (Elem)c.z_values[p];
         }
     }
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
 #pragma unroll
             for (int q = 0; q < TQ; ++q) acc[q] = 0.0;
             for (int64_t p = p0; p < p1; ++p) {
-                const double v = (double)c.x_values[p];
+                const double v = widen_f32(c.x_values[p]);
                 const double *zc = Zt + (size_t)c.x_indices[p] * TQ;
 #pragma unroll
                 for (int q = 0; q < TQ; ++q) acc[q] = fma(v, zc[q], acc[q]);
@@ -100,7 +106,7 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
 #pragma unroll
                 for (int q = 0; q < TQ; ++q) {
                     double d2 = zn[q] + xn - 2.0 * acc[q];
-                    part[q] = fma(coef, exp(-c.gamma * (d2 < 0.0 ? 0.0 : d2)), part[q]);
+                    part[q] = fma(coef, exp_tang(-c.gamma * (d2 < 0.0 ? 0.0 : d2), exp2_s), part[q]);
                 }
             } else {
 #pragma unroll

@@ -30,7 +30,10 @@ cudaError_t launch_diag_wait(int64_t timeout_ns, const int *err, int *gave_up, c
 
 int smo_threads() { return smo::kThreads; }
 size_t smo_cand_bytes() { return smo::kCandStride; }
-size_t smo_static_smem() { return sizeof(smo::Shared); }
+size_t smo_static_smem(int mode)
+{
+    return sizeof(smo::Shared) + sizeof(double) * (mode == MODE_FP64 ? kExp2TabLen : 1);
+}
 
 cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem, cudaStream_t st,
                                   int cs)

@@ -36,6 +36,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "fp64_math.cuh"
 #include "svm_internal.cuh"
 
 namespace svmgb {
@@ -387,6 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     constexpr int W4 = mode_words(MODE) / 4;   // uint4 words of a bit-mask row
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ Shared sh;
+    // FP64 rows: 2^(j/256) for the table-driven exp of the row pass
+    __shared__ double exp2_s[MODE == MODE_FP64 ? kExp2TabLen : 1];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = A.G, cta = blockIdx.x;
@@ -432,6 +435,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     }
     if constexpr (MODE == MODE_BINARY || BITS) {
         for (int c = tid; c < 3 * A.ktab_len; c += kThreads) ktab[c] = A.ktab[c];
+    }
+    if constexpr (MODE == MODE_FP64) {
+        for (int c = tid; c < kExp2TabLen; c += kThreads) exp2_s[c] = kExp2Tab[c];
     }
     const double *rtab = ktab + A.ktab_len;      // 1 / eta (0 when eta <= 1e-12)
     const double *etab = ktab + 2 * A.ktab_len;  // eta = 2 - 2 exp(-gamma k)
@@ -1036,8 +1042,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 sl += (int)(t >> 8);
                             } else if constexpr (MODE == MODE_FP64) {
                                 double2 t = T[cb[j]];
-                                su = fma((double)vb[j], t.x, su);
-                                sl = fma((double)vb[j], t.y, sl);
+                                const double v = widen_f32(vb[j]);
+                                su = fma(v, t.x, su);
+                                sl = fma(v, t.y, sl);
                             } else {
                                 float2 t = T[cb[j]];
                                 su = fmaf(vb[j], t.x, su);
@@ -1058,7 +1065,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             su += (int)(t & 0xff);
                             sl += (int)(t >> 8);
                         } else if constexpr (MODE == MODE_FP64) {
-                            double v = (double)VAL(p);
+                            const double v = widen_f32(VAL(p));
                             double2 t = T[c];
                             su = fma(v, t.x, su);
                             sl = fma(v, t.y, sl);
@@ -1098,7 +1105,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                     ku = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)su);
                             } else if constexpr (MODE == MODE_FP64) {
                                 const double d2u = up.nrm + nrr - 2.0 * su;
-                                ku = exp(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
+                                ku = exp_tang(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u), exp2_s);
                             } else {
                                 const float d2u = (float)up.nrm + (float)nrr - 2.0f * su;
                                 ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
@@ -1115,7 +1122,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                     kl = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)sl);
                             } else if constexpr (MODE == MODE_FP64) {
                                 const double d2l = low.nrm + nrr - 2.0 * sl;
-                                kl = exp(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
+                                kl = exp_tang(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l), exp2_s);
                             } else {
                                 const float d2l = (float)low.nrm + (float)nrr - 2.0f * sl;
                                 kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
@@ -1578,7 +1585,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         for (int64_t p = p0 + gl; p < p1; p += LPR) {
                             const int c = COL(p);
                             if constexpr (MODE == MODE_BINARY) su += (int)(Tn[c] & 0xff);
-                            else if constexpr (MODE == MODE_FP64) su = fma((double)VAL(p), Tn[c].x, su);
+                            else if constexpr (MODE == MODE_FP64) su = fma(widen_f32(VAL(p)), Tn[c].x, su);
                             else su = fmaf(VAL(p), Tn[c].x, su);
                         }
 #pragma unroll
@@ -1592,7 +1599,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 double kut;
                                 if constexpr (MODE == MODE_FP64) {
                                     const double d2 = up.nrm + NRM(r) - 2.0 * su;
-                                    kut = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                                    kut = exp_tang(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2), exp2_s);
                                 } else {
                                     const float d2 = (float)up.nrm + (float)NRM(r) - 2.0f * su;
                                     kut = (double)__expf(-gammaf * fmaxf(d2, 0.f));

@@ -232,6 +232,8 @@ __global__ void k_iota(int64_t n, int32_t *out);
 
 // stored entries of the selected rows, per chunk of kChunkRows rows
 constexpr int kChunkRows = 4096;
+// largest FP64-mode problem (rows, non-binary input) solved by one 16-CTA cluster
+constexpr int64_t kFp64OneClusterRows = 8192;
 __global__ void k_sub_len_sums(int64_t m, const int32_t *idx, const int64_t *indptr, int64_t *sums)
 {
     __shared__ unsigned long long s;
@@ -773,7 +775,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     }
     const int sms = device_sms();
     const int kt = mode == MODE_BINARY ? ktab_len : 0;
-    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
+    const size_t lim_dyn = smem_limit() - smo_static_smem(kmode) - 1024;
     // kernel-row cache (FP64 and mixed inputs): every slot holds one kernel
     // row over all n samples; all n rows when they fit (direct), else up to
     // 8192 rows in 4-way sets; the directory goes into each CTA's shared
@@ -829,8 +831,13 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             const int rows16 = (int)((n_l + 15) / 16);
             const int64_t nnz16 = (int64_t)(1.25 * (double)nnz_l / 16.0) + D.maxnnz;   // segment estimate
             const SmoLayout L16 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, rows16, nnz16, kdir_l);
+            // FP64 rows cost ~50 operations of the FP64 pipe each (about two
+            // issue per clock per SM here), so above a few thousand rows 16 SMs
+            // are slower than clusters of 8 over the whole GPU despite their
+            // cheaper exchange (measured crossover ~7,000 covtype-shaped rows)
+            const int64_t one_cluster_max = kmode == MODE_FP64 ? kFp64OneClusterRows : 200000;
             if (L16.total <= lim_dyn && smo_max_clusters(kmode, lpr, 2, L16.total, 16) >= 1 &&
-                (P->ctas == 16 || n_l <= 200000)) {
+                (P->ctas == 16 || n_l <= one_cluster_max)) {
                 single = true;
                 cs_l = 16;
                 G_l = 16;
@@ -2413,7 +2420,8 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
         set_err("a row has %d entries; the fixed workspace accepts at most %d", h.maxnnz, kFixedMaxRowNnz);
         throw Fail{SVM_ERR_UNSUPPORTED};
     }
-    const size_t lim_dyn = smem_limit() - smo_static_smem() - 1024;
+    // (the larger of the two modes' static shared memory: the mode is decided below)
+    const size_t lim_dyn = smem_limit() - std::max(smo_static_smem(MODE_BINARY), smo_static_smem(MODE_FP64)) - 1024;
     // binary input whose distance tables do not fit in shared memory takes
     // the generic FP64 row pass with norms, as svm_train does
     bool binary = !h.not_binary;

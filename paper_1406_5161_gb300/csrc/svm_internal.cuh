@@ -266,7 +266,7 @@ __host__ __device__ inline size_t smo_kdir_bytes(int64_t n, int slots, int direc
 // apart (a 128-byte line each); the array holds smo_seq_words(G) words
 constexpr int kSeqStride = 32;
 __host__ __device__ inline size_t smo_seq_words(int G) { return 2 * (size_t)G * kSeqStride; }
-size_t smo_static_smem();
+size_t smo_static_smem(int mode);   // static shared memory of the step kernel of this mode
 int smo_threads();
 
 // Contraction of query rows against support vectors with the RBF epilogue:

@@ -102,10 +102,14 @@ def test_mixed_errors_against_oracle(covtype_small, shrink):
            "decision_max": float(np.abs(dz - dref).max()),
            "sign_agree": float((np.sign(dz) == np.sign(dref)).mean())}
     print("mixed vs FP64 oracle", shrink, err)
-    assert err["objective_rel"] <= 2e-4
-    assert err["b"] <= 1e-2
-    assert err["decision_max"] <= 5e-2
-    assert err["sign_agree"] >= 0.99
+    # about twice the errors measured on GB300 (objective 2.9e-5 relative,
+    # alpha 0.11 of C = 4, b 1.1e-3, decision 0.020, every sign equal), so
+    # that a regression of the precision pattern by 2x or more fails
+    assert err["objective_rel"] <= 6e-5
+    assert err["alpha_max"] <= 0.25
+    assert err["b"] <= 2.5e-3
+    assert err["decision_max"] <= 0.04
+    assert err["sign_agree"] >= 0.9985
     assert (a >= 0).all() and (a <= p.C).all() and abs((a * p.y).sum()) <= 1e-9 * len(a)
 
 

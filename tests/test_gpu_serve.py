@@ -36,10 +36,19 @@ def test_same_alone_and_in_mix(jobs):
         for p in jobs:
             t = srv.submit(p.X, p.y, p.C, p.gamma, p.tau)
             alone.append(srv.wait(t))
-        tickets = [srv.submit(p.X, p.y, p.C, p.gamma, p.tau) for p in jobs]
+        t0, tickets, sub = time.perf_counter(), [], []
+        for p in jobs:
+            sub.append(1e3 * (time.perf_counter() - t0))
+            tickets.append(srv.submit(p.X, p.y, p.C, p.gamma, p.tau))
         mix = [srv.wait(t) for t in tickets]
         st = srv.stats()
     assert st["bytes_in_use"] == 0 and st["running"] == 0
+    # the jobs of the mix really ran at the same time: admission-to-done
+    # intervals (host clock) of at least two jobs overlap
+    spans = [(s + m["queue_ms"], s + m["time_to_model_ms"]) for s, m in zip(sub, mix)]
+    overlaps = sum(1 for i in range(len(spans)) for j in range(i + 1, len(spans))
+                   if spans[i][0] < spans[j][1] and spans[j][0] < spans[i][1])
+    assert overlaps >= 1, spans
     for p, a, m in zip(jobs, alone, mix):
         assert a["status"] == pkg.SVM_OK and m["status"] == pkg.SVM_OK
         # identical computation alone and in the mix
