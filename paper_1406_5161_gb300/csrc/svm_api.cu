@@ -234,6 +234,9 @@ __global__ void k_iota(int64_t n, int32_t *out);
 constexpr int kChunkRows = 4096;
 // largest FP64-mode problem (rows, non-binary input) solved by one 16-CTA cluster
 constexpr int64_t kFp64OneClusterRows = 8192;
+// smallest FP64-mode problem that takes one CTA per SM with the flat exchange
+// even when its segments fit in shared memory
+constexpr int64_t kFp64FlatRows = 49152;
 __global__ void k_sub_len_sums(int64_t m, const int32_t *idx, const int64_t *indptr, int64_t *sums)
 {
     __shared__ unsigned long long s;
@@ -877,6 +880,36 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             cs_l = 8;
             const size_t s0 = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, 0, 0, kdir_l).total;
             G_l = 8 * std::max(1, std::min(smo_max_clusters(kmode, lpr, 0, s0, 8), std::min(sms, 256) / 8));
+        }
+        // Rows that stream from global memory, and FP64 levels of many rows,
+        // are bound by the row pass, not by the exchange: there one CTA on
+        // every SM with the flat exchange beats clusters of 8, which leave the
+        // SMs that do not make up whole clusters idle (measured on GB300:
+        // covtype-shaped full set 87 -> 71 us/step FP64, 28 -> 25 mixed)
+        if (P->ctas == 0 && cs_l == 8 && (!resident_l || (kmode == MODE_FP64 && n_l >= kFp64FlatRows))) {
+            const int Gf = (int)std::min<int64_t>(std::min(sms, 256), std::max<int64_t>(1, (n_l + 15) / 16));
+            k_seg_nnz<<<grid1(Gf), 256, 0, st>>>(n_l, Gf, indptr_l, segnnz_d);
+            CK(cudaGetLastError());
+            ++launches;
+            std::vector<int64_t> segnnz(Gf);
+            CK(cudaMemcpyAsync(segnnz.data(), segnnz_d, sizeof(int64_t) * Gf, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            int64_t snm = 0;
+            for (int64_t v : segnnz) snm = std::max(snm, v);
+            const int srm = (int)((n_l + Gf - 1) / Gf);
+            const SmoLayout Lsf = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 0, srm, snm, kdir_l);
+            const SmoLayout Lrf = smo_layout(kmode, (int)D.d, kt, D.maxnnz, 1, srm, snm, kdir_l);
+            const int resf = (P->flags & SVM_FLAG_STREAM_ROWS) == 0 && D.d <= 65535 &&
+                             snm < ((int64_t)1 << 31) && Lrf.total <= lim_dyn;
+            if ((resf ? Lrf.total : Lsf.total) <= lim_dyn) {
+                G_l = Gf;
+                cs_l = 1;
+                resident_l = resf;
+                seg_rows_max_l = srm;
+                seg_nnz_max_l = snm;
+                Ls = Lsf;
+                Lr = Lrf;
+            }
         }
         Shape sh;
         sh.G = G_l;
