@@ -90,6 +90,9 @@ def parse(argv=None):
     ap.add_argument("--wss2", action="store_true",
                     help="covtype / onehot: choose i_low by the second-order gain "
                          "(SVM_FLAG_WSS2) instead of the first-order rule")
+    ap.add_argument("--cache-mb", type=int, default=0,
+                    help="covtype / onehot: kernel-row cache budget in MiB (0 automatic, -1 off; "
+                         "profiling of small cases)")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap SMO steps per solve (profiling of small cases; not a bench value)")
     return ap.parse_args(argv)
@@ -352,7 +355,7 @@ def run_gb300(args, rank, world, local):
 
     def train(X, y, **kw):
         return pkg.svm_train(X, y, p.C, p.gamma, p.tau, shrink=policy, precision=prec,
-                             max_iter=args.max_iter, flags=flags, **kw)
+                             max_iter=args.max_iter, flags=flags, cache_mb=args.cache_mb, **kw)
 
     for _ in range(max(args.warmup, 3)):
         r = train(Xd, yd, stream=stream)
@@ -444,6 +447,19 @@ def run_gb300(args, rank, world, local):
     if trec:
         roofline["traffic_launch"] = trec.get("launch")
         roofline["traffic_alg_bytes"] = trec.get("alg_bytes_per_launch")
+    fp64_pipe = None
+    if args.precision == "fp64" and not stats["binary_input"]:
+        # the FP64 row pass is bound by the FP64 pipe, not by memory: per
+        # active row, 2 nnz FMAs (the two inner products), 2 x 3 for the
+        # distances and scaling, 2 x 10 for the exponentials (the table-driven
+        # method) and 2 FMAs for Eq. (fup)
+        instr_row = 2 * p.X.nnz / p.X.n + 28
+        ach = row_visits * instr_row / (ms_smo / 1e3) / 1e9
+        fp64_pipe = {"bound": "alu", "achieved": ach, "peak": 625.0, "unit": "G FP64 instr/s",
+                     "frac": ach / 625.0, "instr_per_row_visit": instr_row,
+                     "peak_source": "nominal FP64 rate 1.25 TFLOP/s (FMA = 2 flops) = 625 G FP64 "
+                                    "instructions/s (152 SMs x 2 per clock x 2.07 GHz); a DFMA "
+                                    "microbenchmark measures 1.59 per clock per SM (500 G/s)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -458,8 +474,12 @@ def run_gb300(args, rank, world, local):
             "objective": stats["objective"],
             "gpu_launches": int(launches),
             "clocks": clk, "roofline": roofline, "e2e": e2e}
+    if fp64_pipe:
+        line["roofline_fp64_pipe"] = fp64_pipe
     if args.max_iter:
         line["config"]["max_iter"] = args.max_iter
+    if args.cache_mb:
+        line["config"]["cache_mb"] = args.cache_mb
     if args.wss2:
         line["config"]["selection"] = "second-order i_low (SVM_FLAG_WSS2)"
     if world == 1 and not args.no_extras and args.workload == "covtype" and not args.max_iter:

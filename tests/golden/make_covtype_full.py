@@ -20,8 +20,9 @@ Outputs, beside this file:
 * ``covtype_full_decision.txt``: the 10,000 held-out decision values;
 * ``covtype_full_alpha.npz``: alpha (compressed; zero for most rows).
 
-A full run takes about 30-40 minutes on 8 cores (about 340,000 steps over
-all 581,012 rows each). Usage: ``python tests/golden/make_covtype_full.py``.
+A full run takes about 45 minutes on 6 x86 cores (340,282 steps over all
+581,012 rows each; ORACLE_THREADS sets the thread count). Usage:
+``python tests/golden/make_covtype_full.py``.
 """
 import hashlib
 import json
@@ -81,7 +82,7 @@ def main():
         fh.write("# Eq. (classi) before the sign on the 10,000 held-out rows of "
                  "covtype_like(seed=3); FP64 oracle (make_covtype_full.py)\n")
         for v in dec:
-            fh.write(f"{v!r}\n")
+            fh.write(f"{float(v)!r}\n")
     np.savez_compressed(os.path.join(HERE, "covtype_full_alpha.npz"), alpha=a)
     print(json.dumps(meta, indent=1))
 

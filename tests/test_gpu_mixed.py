@@ -121,50 +121,3 @@ def test_mixed_tensor_and_cuda_cores_agree(covtype_small):
     r2 = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_MIXED_BF16_SIMT, shrink=pol)
     assert r1["stats"]["reconstructions"] >= 1
     assert abs(r1["stats"]["objective"] - r2["stats"]["objective"]) <= 1e-6 * abs(r2["stats"]["objective"])
-
-
-@pytest.mark.timeout(900)
-def test_covtype_581012_fp64_and_mixed():
-    """Full-size covtype-shaped workload: the FP64 GPU solve is checked by the
-    oracle on sampled outputs it can compute one by one; the mixed solve's
-    errors are measured against the FP64 solve."""
-    p = synth.covtype_like()
-    Xd, yd = dev(p)
-    pol = pkg.POLICIES["Multi5pc"]
-    r64 = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_FP64, shrink=pol)
-    rmx = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=pkg.SVM_MIXED_BF16, shrink=pol)
-    assert r64["status"] == pkg.SVM_OK and rmx["status"] == pkg.SVM_OK
-    a64 = r64["alpha"].cpu().numpy()
-    amx = rmx["alpha"].cpu().numpy()
-    rng = np.random.default_rng(0)
-    # oracle: f of 300 sampled training rows from the FP64 alpha (Algorithm 6
-    # definition) -> the KKT conditions hold on the sample
-    rows = np.sort(rng.choice(p.X.n, 300, replace=False))
-    f = oracle.reconstruct(p.X, p.y, a64, p.gamma, rows, np.zeros(p.X.n))[rows]
-    ys, as_ = p.y[rows].astype(float), a64[rows]
-    up = ((as_ > 0) & (as_ < p.C)) | ((ys > 0) & (as_ == 0)) | ((ys < 0) & (as_ == p.C))
-    low = ((as_ > 0) & (as_ < p.C)) | ((ys > 0) & (as_ == p.C)) | ((ys < 0) & (as_ == 0))
-    assert f[low].max() - f[up].min() <= 2 * p.tau + 1e-6
-    # oracle decision values of 200 held-out points from the FP64 model
-    Zs = p.Z.take(np.arange(0, p.Z.n, 50))
-    Zsd = pkg.to_device(Zs)
-    d64 = pkg.svm_decision(Xd, yd, r64["alpha"], r64["b"], p.gamma, Zsd).cpu().numpy()
-    dor = oracle.decision(p.X, p.y, a64, r64["b"], p.gamma, Zs)
-    assert np.abs(d64 - dor).max() <= 1e-9 * max(1.0, np.abs(dor).max())
-    # mixed against FP64 (the errors are printed with -s)
-    Zd = pkg.to_device(p.Z)
-    dz64 = pkg.svm_decision(Xd, yd, r64["alpha"], r64["b"], p.gamma, Zd).cpu().numpy()
-    dzmx = pkg.svm_decision(Xd, yd, rmx["alpha"], rmx["b"], p.gamma, Zd,
-                            precision=pkg.SVM_MIXED_BF16).cpu().numpy()
-    w64, wmx = r64["stats"]["objective"], rmx["stats"]["objective"]
-    err = {"objective_rel": abs(wmx - w64) / abs(w64), "alpha_max": float(np.abs(amx - a64).max()),
-           "alpha_mean": float(np.abs(amx - a64).mean()), "b": abs(rmx["b"] - r64["b"]),
-           "decision_max": float(np.abs(dzmx - dz64).max()),
-           "decision_mean": float(np.abs(dzmx - dz64).mean()),
-           "sign_agree": float((np.sign(dzmx) == np.sign(dz64)).mean()),
-           "iters": (r64["iters"], rmx["iters"]),
-           "ms": (r64["stats"]["ms_total"], rmx["stats"]["ms_total"]),
-           "recon_ms": (r64["stats"]["ms_recon"], rmx["stats"]["ms_recon"])}
-    print("covtype 581012 mixed vs FP64:", err)
-    assert err["objective_rel"] <= 1e-3
-    assert err["sign_agree"] >= 0.99
