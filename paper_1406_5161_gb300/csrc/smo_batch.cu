@@ -310,8 +310,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                             const float nf = normf[g];
                             float d2u = (float)up.nrm + nf - 2.0f * su;
                             float d2l = (float)low.nrm + nf - 2.0f * sl;
-                            ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
-                            kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
+                            // widened exactly by integer operations (a conversion
+                            // instruction would take a slot of the FP64 pipe)
+                            ku = widen_f32(__expf(-gammaf * fmaxf(d2u, 0.f)));
+                            kl = widen_f32(__expf(-gammaf * fmaxf(d2l, 0.f)));
                         }
                         fi = fma(dl, kl, fma(du, ku, fi));
                         fj[r] = fi;

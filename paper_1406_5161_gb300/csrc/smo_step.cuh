@@ -589,6 +589,13 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         else if constexpr (MODE == MODE_FP64) return A.norm[lo + r];
         else return (double)A.normf[lo + r];
     };
+    // mixed mode: the FP32 norm as it is stored (no round trip through the
+    // FP64 pipe, whose conversions cost as much as its arithmetic here)
+    auto NRMF = [&](int r) -> float {
+        if constexpr (MODE != MODE_MIXED) return 0.f;
+        else if constexpr (RES) return nrm_s[r];
+        else return A.normf[lo + r];
+    };
 
     const double C = A.C;
     const double snap = 1e-12 * C, c_snap = C - snap;
@@ -940,9 +947,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 // tile sums and the stored norms are summed in
                                 // different orders, so their difference is not 0)
                                 const int i = (int)(lo + r);
-                                const float nrr = (float)NRM(r);
-                                ku = i == up.i ? 1.0 : (double)__expf(-gammaf * fmaxf(up_nrmf + nrr - 2.0f * su, 0.f));
-                                kl = i == low.i ? 1.0 : (double)__expf(-gammaf * fmaxf(low_nrmf + nrr - 2.0f * sl, 0.f));
+                                const float nrr = NRMF(r);
+                                ku = i == up.i ? 1.0 : widen_f32(__expf(-gammaf * fmaxf(up_nrmf + nrr - 2.0f * su, 0.f)));
+                                kl = i == low.i ? 1.0 : widen_f32(__expf(-gammaf * fmaxf(low_nrmf + nrr - 2.0f * sl, 0.f)));
                             }
                         }
                         if (!have_step) {
@@ -997,13 +1004,16 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 double fi = 0.0;
                 uint8_t sb = 0;
                 double nr = 0.0;
+                float nrf = 0.f;
                 if (valid) {
                     r = ident ? k : ACT(k);
                     if constexpr (!BITS) ROWP(r, p0, p1);
                     if (gl == 0) {
                         fi = GETF(r);
                         sb = GETST(r);
-                        if constexpr (!RES) nr = NRM(r);   // issued with the row's other loads
+                        // issued with the row's other loads
+                        if constexpr (!RES && MODE == MODE_MIXED) nrf = NRMF(r);
+                        else if constexpr (!RES) nr = NRM(r);
                     }
                 }
                 Acc su = 0, sl = 0;
@@ -1094,40 +1104,55 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         kl = ktab[dl2 < 0 ? 0 : dl2];
                     } else {
                         const int64_t gi = lo + r;
-                        const double nrr = RES ? NRM(r) : nr;
-                        if (kc_hu) {
-                            ku = (double)kc_ru[gi];
-                        } else {
-                            if (A.kernel != KERNEL_RBF) {
-                                if constexpr (MODE == MODE_FP64)
+                        if constexpr (MODE == MODE_FP64) {
+                            const double nrr = RES ? NRM(r) : nr;
+                            if (kc_hu) {
+                                ku = kc_ru[gi];
+                            } else {
+                                if (A.kernel != KERNEL_RBF) {
                                     ku = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, (double)su);
-                                else
-                                    ku = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)su);
-                            } else if constexpr (MODE == MODE_FP64) {
-                                const double d2u = up.nrm + nrr - 2.0 * su;
-                                ku = exp_tang(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u), exp2_s);
-                            } else {
-                                const float d2u = (float)up.nrm + (float)nrr - 2.0f * su;
-                                ku = (double)__expf(-gammaf * fmaxf(d2u, 0.f));
+                                } else {
+                                    const double d2u = up.nrm + nrr - 2.0 * su;
+                                    ku = exp_tang(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u), exp2_s);
+                                }
+                                if (kc_step) kc_ru[gi] = ku;
                             }
-                            if (kc_step) kc_ru[gi] = (KT)ku;
-                        }
-                        if (kc_hl) {
-                            kl = (double)kc_rl[gi];
-                        } else {
-                            if (A.kernel != KERNEL_RBF) {
-                                if constexpr (MODE == MODE_FP64)
+                            if (kc_hl) {
+                                kl = kc_rl[gi];
+                            } else {
+                                if (A.kernel != KERNEL_RBF) {
                                     kl = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, (double)sl);
-                                else
-                                    kl = (double)kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)sl);
-                            } else if constexpr (MODE == MODE_FP64) {
-                                const double d2l = low.nrm + nrr - 2.0 * sl;
-                                kl = exp_tang(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l), exp2_s);
-                            } else {
-                                const float d2l = (float)low.nrm + (float)nrr - 2.0f * sl;
-                                kl = (double)__expf(-gammaf * fmaxf(d2l, 0.f));
+                                } else {
+                                    const double d2l = low.nrm + nrr - 2.0 * sl;
+                                    kl = exp_tang(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l), exp2_s);
+                                }
+                                if (kc_step) kc_rl[gi] = kl;
                             }
-                            if (kc_step) kc_rl[gi] = (KT)kl;
+                        } else {
+                            // mixed: FP32 kernel values, widened exactly for
+                            // the FP64 f update by integer operations
+                            const float nrr = RES ? NRMF(r) : nrf;
+                            float kuf, klf;
+                            if (kc_hu) {
+                                kuf = kc_ru[gi];
+                            } else {
+                                if (A.kernel != KERNEL_RBF)
+                                    kuf = kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)su);
+                                else
+                                    kuf = __expf(-gammaf * fmaxf(up_nrmf + nrr - 2.0f * su, 0.f));
+                                if (kc_step) kc_ru[gi] = kuf;
+                            }
+                            if (kc_hl) {
+                                klf = kc_rl[gi];
+                            } else {
+                                if (A.kernel != KERNEL_RBF)
+                                    klf = kernel_of_dot(A.kernel, gammaf, (float)A.coef0, A.degree, (float)sl);
+                                else
+                                    klf = __expf(-gammaf * fmaxf(low_nrmf + nrr - 2.0f * sl, 0.f));
+                                if (kc_step) kc_rl[gi] = klf;
+                            }
+                            ku = widen_f32(kuf);
+                            kl = widen_f32(klf);
                         }
                     }
                 }
@@ -1601,8 +1626,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                     const double d2 = up.nrm + NRM(r) - 2.0 * su;
                                     kut = exp_tang(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2), exp2_s);
                                 } else {
-                                    const float d2 = (float)up.nrm + (float)NRM(r) - 2.0f * su;
-                                    kut = (double)__expf(-gammaf * fmaxf(d2, 0.f));
+                                    const float d2 = (float)up.nrm + NRMF(r) - 2.0f * su;
+                                    kut = widen_f32(__expf(-gammaf * fmaxf(d2, 0.f)));
                                 }
                                 eta = 2.0 - 2.0 * kut;   // K(x,x) = 1
                             } else {

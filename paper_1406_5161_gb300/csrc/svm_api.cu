@@ -783,32 +783,50 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     // row over all n samples; all n rows when they fit (direct), else up to
     // 8192 rows in 4-way sets; the directory goes into each CTA's shared
     // memory, so its size is part of the layout
-    int kc_slots = 0, kc_direct = 0;
-    int64_t kc_ld = 0;
+    // The plan is made again for every level of the active-set re-layout
+    // (below) within the buffer sized at the top level: rows of a smaller
+    // level are shorter, so more of them fit, and the whole kernel matrix of
+    // the small late levels fits directly.
+    struct KcPlan {
+        int64_t ld = 0;
+        int slots = 0, direct = 0;
+    };
+    const size_t kc_esz = kmode == MODE_FP64 ? 8 : 4;
+    auto plan_kc = [&](int64_t n_l, size_t cap) {
+        KcPlan k;
+        k.ld = (n_l + 31) / 32 * 32;
+        const size_t row_bytes = (size_t)k.ld * kc_esz;
+        if ((size_t)n_l * row_bytes <= cap && smo_kdir_bytes(n_l, 0, 1) <= lim_dyn / 4) {
+            k.slots = (int)n_l;
+            k.direct = 1;
+        } else {
+            int64_t sl = std::min<int64_t>((int64_t)(cap / row_bytes), 8192);
+            while (sl >= 64 && smo_kdir_bytes(n_l, (int)sl, 0) > lim_dyn / 2) sl /= 2;
+            k.slots = sl >= 64 ? (int)(sl / 4 * 4) : 0;
+        }
+        return k;
+    };
+    KcPlan top_kc;
+    size_t kc_cap = 0;   // bytes of the cache buffer
     size_t kdir = 0;
     // automatic for FP64 rows (their exp costs ~20 FP64 instructions per
     // value); the mixed mode's FP32 exp is cheaper than the cache traffic, so
     // there the cache is used only when a budget is given
     if ((kmode == MODE_FP64 && P->cache_mb >= 0) || (kmode == MODE_MIXED && P->cache_mb > 0)) {
-        const size_t esz = kmode == MODE_FP64 ? 8 : 4;
-        kc_ld = (n + 31) / 32 * 32;
         size_t budget = (size_t)P->cache_mb << 20;
         if (P->cache_mb == 0) {
             size_t fr = 0, tot = 0;
             if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
             budget = std::min<size_t>(fr / 2, (size_t)32 << 30);
         }
-        const size_t row_bytes = (size_t)kc_ld * esz;
-        if ((size_t)n * row_bytes <= budget && smo_kdir_bytes(n, 0, 1) <= lim_dyn / 4) {
-            kc_slots = (int)n;
-            kc_direct = 1;
-        } else {
-            int64_t sl = std::min<int64_t>((int64_t)(budget / row_bytes), 8192);
-            while (sl >= 64 && smo_kdir_bytes(n, (int)sl, 0) > lim_dyn / 2) sl /= 2;
-            kc_slots = sl >= 64 ? (int)(sl / 4 * 4) : 0;
+        top_kc = plan_kc(n, budget);
+        if (top_kc.slots > 0) {
+            kc_cap = (size_t)top_kc.slots * (size_t)top_kc.ld * kc_esz;
+            kdir = smo_kdir_bytes(n, top_kc.slots, top_kc.direct);
         }
-        if (kc_slots > 0) kdir = smo_kdir_bytes(n, kc_slots, kc_direct);
     }
+    const int kc_slots = top_kc.slots, kc_direct = top_kc.direct;
+    const int64_t kc_ld = top_kc.ld;
     // launch shape of a problem of n_l rows and nnz_l entries (the caller's
     // problem, or the active rows gathered after shrinking): thread-block
     // clusters for the hierarchical exchange, one cluster of 16 when its
@@ -1085,8 +1103,9 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.kernel = P->kernel;
     A.degree = P->degree;
     A.coef0 = P->coef0;
+    void *kc_buf = kc_cap ? ar.alloc<unsigned char>(kc_cap) : nullptr;
     if (kc_slots > 0) {
-        A.kc = ar.alloc<unsigned char>((size_t)kc_slots * (size_t)kc_ld * (kmode == MODE_FP64 ? 8 : 4));
+        A.kc = kc_buf;
         A.kc_ld = kc_ld;
         A.kc_slots = kc_slots;
         A.kc_direct = kc_direct;
@@ -1126,13 +1145,14 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         const int32_t *gmap;   // ... and in the caller's problem
         Shape shape;
         const __nv_bfloat16 *dmat;   // dense BF16 rows for the row tiles, or NULL
+        KcPlan kc;                   // kernel-row cache plan of this level
     };
     const bool relayout_on = (P->flags & SVM_FLAG_NO_RELAYOUT) == 0;
     bool relayout_ok = relayout_on;
     const int bit_words = mode_bits(kmode) ? mode_words(kmode) : 0;
     std::vector<Level> lv;
     lv.push_back(Level{n, D.nnz, D.indptr, D.indices, vals_fp32, D.vmix, D.normf, D.norm, D.y, bits,
-                       alpha, f, status, act, seg_cnt, nullptr, nullptr, top, dmat});
+                       alpha, f, status, act, seg_cnt, nullptr, nullptr, top, dmat, top_kc});
     int64_t relayouts = 0;
     auto launch_level = [&](const Level &L, int select_only, double thr, int64_t hh, int64_t limit) {
         A.n = L.n;
@@ -1156,6 +1176,10 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         A.gmap = L.gmap;
         A.dmat = L.dmat;
         A.d_pad = d_pad;
+        A.kc = L.kc.slots > 0 ? kc_buf : nullptr;
+        A.kc_ld = L.kc.ld;
+        A.kc_slots = L.kc.slots;
+        A.kc_direct = L.kc.direct;
         const bool one_cluster_on_chip = L.shape.resident && L.shape.cs == L.shape.G;
         A.compact_below = (relayout_ok && hh > 0 && !one_cluster_on_chip && L.n >= 2048) ? L.n * 3 / 4 : 0;
         CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
@@ -1258,7 +1282,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         C.idx = idx;
         C.gmap = S.sub_gmap;
         C.dmat = S.sub_dmat;
-        C.shape = pick_shape(m, nnz_m, sub_indptr, kc_slots > 0 ? smo_kdir_bytes(m, kc_slots, kc_direct) : 0);
+        C.kc = kc_cap ? plan_kc(m, kc_cap) : KcPlan{};
+        C.shape = pick_shape(m, nnz_m, sub_indptr, C.kc.slots > 0 ? smo_kdir_bytes(m, C.kc.slots, C.kc.direct) : 0);
         k_reset_active<<<C.shape.G, 256, 0, st>>>(m, C.shape.G, C.act, C.seg_cnt);
         CK(cudaGetLastError());
         ++launches;
