@@ -182,6 +182,9 @@ struct __align__(16) CandFull {
     int32_t pad[3];
 };
 static_assert(sizeof(CandFull) % 16 == 0, "candidate slots are read with vector loads");
+// the leader exchange reads a side's first 48 bytes as three 16-byte words
+static_assert(offsetof(Side, f) == 0 && offsetof(Side, i) == 32 && offsetof(Side, m) == 48 &&
+              sizeof(Side) % 16 == 0 && offsetof(CandFull, low) == sizeof(Side), "Side layout");
 // global exchange slots: each candidate and each flag on lines of its own
 constexpr size_t kCandStride = 256;
 static_assert(sizeof(CandFull) <= kCandStride, "candidate slot too small");
@@ -1439,11 +1442,16 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         const CandFull *gp = nullptr;
                         long long cc = 0;
                         int timed_out = 0;
+                        // the first 48 bytes of both sides (all but the bit
+                        // masks), read with the keys: the winning lane then
+                        // writes its side without another trip to L2
+                        uint4 wu0 = make_uint4(0, 0, 0, 0), wu1 = wu0, wu2 = wu0, wl0 = wu0, wl1 = wu0, wl2 = wu0;
                         if (c < nlead) {
                             const unsigned *sp = A.seq + ((size_t)par * nlead + c) * kSeqStride;
                             uint64_t t0 = 0;
                             int spins = 0;
-                            while (ld_relaxed_u32(sp) < epoch) {
+                            // acquire loads: the slot was written before the flag
+                            while (ld_acquire_u32(sp) < epoch) {
                                 if (++spins >= 256) {
                                     spins = 0;
                                     uint64_t now = global_ns();
@@ -1453,16 +1461,18 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 }
                             }
                             if (!timed_out) {
-                                fence_acq_rel_gpu();   // acquire: the slot written before the flag
-                                // L2 reads (bypass L1, which is not coherent across SMs);
-                                // the winners' full sides are copied below
+                                // L2 reads (bypass L1, which is not coherent across SMs)
                                 gp = reinterpret_cast<const CandFull *>(static_cast<const unsigned char *>(A.cand) +
                                                                         ((size_t)par * nlead + c) * kCandStride);
-                                ai = __ldcg(&gp->up.i);
-                                bi = __ldcg(&gp->low.i);
-                                af = __ldcg(&gp->up.f);
-                                bf = __ldcg(&gp->low.f);
+                                const uint4 *pu = reinterpret_cast<const uint4 *>(&gp->up);
+                                const uint4 *pl = reinterpret_cast<const uint4 *>(&gp->low);
+                                wu0 = __ldcg(pu); wu1 = __ldcg(pu + 1); wu2 = __ldcg(pu + 2);
+                                wl0 = __ldcg(pl); wl1 = __ldcg(pl + 1); wl2 = __ldcg(pl + 2);
                                 cc = __ldcg(&gp->count);
+                                ai = (int)wu2.x;
+                                bi = (int)wl2.x;
+                                af = __hiloint2double((int)wu0.y, (int)wu0.x);
+                                bf = __hiloint2double((int)wl0.y, (int)wl0.x);
                             }
                         }
                         const int any_to = __any_sync(0xffffffffu, timed_out);
@@ -1481,8 +1491,22 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             sh.rcount[warp] = cc;
                             sh.rto[warp] = any_to;
                         }
-                        if (i1 != INT_MAX && ai == i1) copy_side_ldcg(&sh.rup[warp], &gp->up);
-                        if (i2 != INT_MAX && bi == i2) copy_side_ldcg(&sh.rlow[warp], &gp->low);
+                        if constexpr (BITS) {
+                            if (i1 != INT_MAX && ai == i1) copy_side_ldcg(&sh.rup[warp], &gp->up);
+                            if (i2 != INT_MAX && bi == i2) copy_side_ldcg(&sh.rlow[warp], &gp->low);
+                        } else {
+                            auto put48 = [](Side *dst, const uint4 &a, const uint4 &b, const uint4 &c) {
+                                unsigned long long *d8 = reinterpret_cast<unsigned long long *>(dst);
+                                const uint4 v[3] = {a, b, c};
+#pragma unroll
+                                for (int w = 0; w < 3; ++w) {
+                                    d8[2 * w] = ((unsigned long long)v[w].y << 32) | v[w].x;
+                                    d8[2 * w + 1] = ((unsigned long long)v[w].w << 32) | v[w].z;
+                                }
+                            };
+                            if (i1 != INT_MAX && ai == i1) put48(&sh.rup[warp], wu0, wu1, wu2);
+                            if (i2 != INT_MAX && bi == i2) put48(&sh.rlow[warp], wl0, wl1, wl2);
+                        }
                     }
                     __syncthreads();
                     if (warp == 0) {
