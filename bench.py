@@ -179,7 +179,7 @@ def job_totals(dist, seconds: float, units: float, device) -> tuple[float, float
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("smo_step.cuh", "svm_internal.cuh"):
+    for name in ("smo_step.cuh", "svm_internal.cuh", "fp64_math.cuh"):
         with open(os.path.join(ROOT, "paper_1406_5161_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -199,6 +199,15 @@ typedef struct svm_kernel {
  * pass on the CUDA cores (same arithmetic type, another summation order). */
 #define SVM_FLAG_CUDA_CORE_ROWS 64
 #define SVM_FLAG_TENSOR_ROWS 128
+/* Gradient reconstruction (Algorithm 6) always as the full sum over the
+ * support vectors. By default, when the launch over all rows that follows a
+ * multiple-reconstruction restart ends at its first shrink event and its
+ * active rows are gathered by the re-layout, the rows shrunk there (whose f
+ * was exact at that moment) are reconstructed as that f plus the sum over the
+ * gathered rows whose alpha changed since: the same value up to rounding
+ * order, over far fewer terms. CUDA-core contraction only (FP64, binary and
+ * SVM_MIXED_BF16_SIMT inputs); svm_stats.incremental_recons counts them. */
+#define SVM_FLAG_FULL_RECON 256
 
 typedef struct svm_shrink_policy {
     int32_t kind;            /* enum svm_shrink_kind */
@@ -248,7 +257,7 @@ typedef struct svm_stats {
     int64_t cache_misses;    /* ... that were computed (and stored) */
     int64_t relayouts;       /* active-set re-layouts (see SVM_FLAG_NO_RELAYOUT) */
     int32_t row_tiles;       /* 1 when the kernel rows ran on the tensor cores */
-    int32_t reserved;
+    int32_t incremental_recons;   /* reconstructions done incrementally (SVM_FLAG_FULL_RECON) */
 } svm_stats;
 
 /*

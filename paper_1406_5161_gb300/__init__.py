@@ -9,7 +9,7 @@ from ._abi import (  # noqa: F401
     SVM_OK, SVM_NOT_CONVERGED, SVM_PENDING, SVM_ERR_ARG, SVM_ERR_OOM, SVM_ERR_BUDGET,
     SVM_ERR_TIMEOUT, SVM_ERR_CUDA, SVM_ERR_CANCELLED, SVM_ERR_UNSUPPORTED,
     SVM_FP64, SVM_MIXED_BF16, SVM_MIXED_BF16_SIMT, SVM_SHRINK_NONE, SVM_SHRINK_FIXED, SVM_SHRINK_FRACTION,
-    SVM_RECON_SINGLE, SVM_RECON_MULTI, SVM_FLAG_STREAM_ROWS, SVM_FLAG_PHASE_TIMES, SVM_FLAG_NO_CLUSTERS, SVM_FLAG_CSR_ROWS, SVM_FLAG_WSS2, SVM_FLAG_NO_RELAYOUT, SVM_FLAG_CUDA_CORE_ROWS, SVM_FLAG_TENSOR_ROWS, SVM_KERNEL_RBF, SVM_KERNEL_LINEAR, SVM_KERNEL_POLY, SVM_KERNEL_SIGMOID, SvmError, DeviceCSR, to_device, load, lib_path,
+    SVM_RECON_SINGLE, SVM_RECON_MULTI, SVM_FLAG_STREAM_ROWS, SVM_FLAG_PHASE_TIMES, SVM_FLAG_NO_CLUSTERS, SVM_FLAG_CSR_ROWS, SVM_FLAG_WSS2, SVM_FLAG_NO_RELAYOUT, SVM_FLAG_CUDA_CORE_ROWS, SVM_FLAG_TENSOR_ROWS, SVM_FLAG_FULL_RECON, SVM_KERNEL_RBF, SVM_KERNEL_LINEAR, SVM_KERNEL_POLY, SVM_KERNEL_SIGMOID, SvmError, DeviceCSR, to_device, load, lib_path,
     svm_train, svm_decision, svm_last_error, svm_version, svm_kernel_launches, svm_diag_wait_timeout, svm_diag_sfu_rate,
     svm_train_fixed_workspace, svm_train_batch, svm_batch_autotune, Server, Model,
 )

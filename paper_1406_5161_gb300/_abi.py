@@ -30,6 +30,7 @@ SVM_FLAG_WSS2 = 16
 SVM_FLAG_NO_RELAYOUT = 32
 SVM_FLAG_CUDA_CORE_ROWS = 64
 SVM_FLAG_TENSOR_ROWS = 128
+SVM_FLAG_FULL_RECON = 256
 SVM_KERNEL_RBF, SVM_KERNEL_LINEAR, SVM_KERNEL_POLY, SVM_KERNEL_SIGMOID = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "SVM_OK", 1: "SVM_NOT_CONVERGED", 2: "SVM_PENDING", -1: "SVM_ERR_ARG",
@@ -76,7 +77,7 @@ class svm_stats(ct.Structure):
                 ("cta_busy_ms_min", ct.c_double), ("cta_busy_ms_max", ct.c_double),
                 ("bit_rows", ct.c_int32), ("cache_slots", ct.c_int32),
                 ("cache_hits", ct.c_int64), ("cache_misses", ct.c_int64), ("relayouts", ct.c_int64),
-                ("row_tiles", ct.c_int32), ("reserved", ct.c_int32)]
+                ("row_tiles", ct.c_int32), ("incremental_recons", ct.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}

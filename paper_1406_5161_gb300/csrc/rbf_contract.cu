@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
         const int r = zrow[tid];
         double v = s + c.add_scalar;
         if (c.yq) v -= (double)c.yq[r];
-        c.out[c.out_by_row ? (int64_t)r : qbase + tid] = v;
+        const int64_t o = c.out_by_row ? (int64_t)r : qbase + tid;
+        if (c.accumulate) v = c.out[o] + v;
+        c.out[o] = v;
     }
 }
 

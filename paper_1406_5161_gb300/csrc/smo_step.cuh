@@ -732,8 +732,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     } else {
                         if (A.kernel == KERNEL_RBF) {
                             if constexpr (MODE == MODE_FP64) {
+                                // the table-driven exp: a shorter dependency
+                                // chain on the serial pair step than CUDA's exp
                                 double d2 = up.nrm + low.nrm - 2.0 * s;
-                                kul = exp(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                                kul = exp_tang(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2), exp2_s);
                             } else {
                                 float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
                                 kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));

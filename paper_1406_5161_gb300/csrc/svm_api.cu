@@ -214,6 +214,33 @@ __global__ void k_mark_active(int64_t n, int G, const int32_t *act, const int32_
     for (int k = threadIdx.x; k < seg_cnt[s]; k += blockDim.x) mark[lo + act[lo + k]] = 1;
 }
 
+// Incremental reconstruction. For the m rows gathered into a re-layout level
+// (idx: their rows in the caller's problem, a0: their alpha at the gather):
+// the change of alpha since the gather at each such row (dalpha, marked in
+// dmark when not zero) and a mark of the gathered rows.
+__global__ void k_inc_delta(int64_t m, const int32_t *idx, const double *a0, const double *alpha,
+                            double *dalpha, uint8_t *dmark, uint8_t *gathered)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int i = idx[k];
+    const double d = alpha[i] - a0[k];
+    dalpha[i] = d;
+    dmark[i] = d != 0.0;
+    gathered[i] = 1;
+}
+
+// Query marks of the two reconstructions (a row is a query where its mark is
+// 0): q1 the rows shrunk before the gather, q2 the gathered rows shrunk after.
+__global__ void k_inc_marks(int64_t n, const uint8_t *active, const uint8_t *gathered, uint8_t *q1,
+                            uint8_t *q2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    q1[i] = (uint8_t)(active[i] | gathered[i]);
+    q2[i] = (uint8_t)!(gathered[i] && !active[i]);
+}
+
 // stored entries per segment
 __global__ void k_seg_nnz(int64_t n, int G, const int64_t *indptr, int64_t *out)
 {
@@ -1307,14 +1334,39 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         CK(cudaGetLastError());
         launches += 3;
     };
+    // Incremental reconstruction: when a run's launch over the caller's
+    // problem ends at its first shrink event and its active rows are gathered
+    // into a level, the rows shrunk there hold f exact at that moment, and
+    // afterwards only the gathered rows' alpha change. Their f at the end is
+    // then that f plus the contraction over the gathered rows whose alpha
+    // changed (Algorithm 6's sum over all support vectors, less the terms
+    // whose alpha did not change since f was exact). inc_*: the gather.
+    bool inc_track = false, inc_ok = false;
+    const int32_t *inc_idx = nullptr;
+    int64_t inc_m = 0;
+    double *inc_a0 = nullptr;
     auto run = [&](int select_only, double thr, int64_t hh, int64_t limit) {
         int sel = select_only;
+        bool top = true;
+        if (inc_track) inc_ok = false;
         for (;;) {
+            const int64_t se0 = hc.shrink_events;
             launch_level(lv.back(), sel, thr, hh, limit);
             if (hc.exit_reason != 2) break;
+            const bool one_event = top && hc.shrink_events - se0 == 1;
             // the same state continues on the gathered rows (a selection
             // pass there finds the pair this launch had chosen)
-            if (!push_level()) relayout_ok = false;
+            if (!push_level()) {
+                relayout_ok = false;
+            } else if (inc_track && one_event && lv.size() == 2) {
+                const Level &Cl = lv.back();
+                inc_idx = Cl.idx;
+                inc_m = Cl.n;
+                inc_a0 = ar.alloc<double>(inc_m);
+                CK(cudaMemcpyAsync(inc_a0, Cl.alpha, sizeof(double) * inc_m, cudaMemcpyDeviceToDevice, st));
+                inc_ok = true;
+            }
+            top = false;
             sel = 1;
         }
         while (lv.size() > 1) pop_level();
@@ -1328,8 +1380,13 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     uint8_t *mark = nullptr;
     int32_t *list_w = nullptr, *list_sv = nullptr;
     double *coef = nullptr;
+    // the CUDA-core contraction can add to f (the tensor-core one writes it)
+    const bool inc_allowed = (P->flags & SVM_FLAG_FULL_RECON) == 0 && !(use_tc && mode == MODE_MIXED);
+    int64_t inc_recons = 0;
     for (;;) {
+        inc_track = inc_allowed && shrinking;
         run(1, thr, shrinking ? h : 0, max_iter);
+        inc_track = false;
         if (hc.exit_reason == 1) {
             status_code = SVM_NOT_CONVERGED;
             break;
@@ -1348,8 +1405,33 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             k_mark_active<<<G, 256, 0, st>>>(n, G, act, seg_cnt, mark);
             CK(cudaGetLastError());
             ++launches;
-            int64_t nw = compact(ar, PRED_UNMARKED, n, mark, alpha, D.y, list_w, nullptr, st, &launches);
-            int64_t nsv = compact(ar, PRED_ALPHA_POS, n, mark, alpha, D.y, list_sv, coef, st, &launches);
+            // incremental part: rows shrunk at the gather get f += the
+            // contraction over the gathered rows whose alpha changed
+            int64_t inc_nq = 0, inc_nd = 0;
+            int32_t *inc_q = nullptr, *inc_list = nullptr;
+            double *inc_coef = nullptr;
+            const uint8_t *full_mark = mark;
+            if (inc_ok) {
+                uint8_t *gathered = ar.alloc<uint8_t>(n), *dmark = ar.alloc<uint8_t>(n);
+                uint8_t *q1 = ar.alloc<uint8_t>(n), *q2 = ar.alloc<uint8_t>(n);
+                double *dalpha = ar.alloc<double>(n);
+                CK(cudaMemsetAsync(gathered, 0, n, st));
+                CK(cudaMemsetAsync(dmark, 0, n, st));
+                CK(cudaMemsetAsync(dalpha, 0, sizeof(double) * n, st));
+                k_inc_delta<<<grid1(inc_m), 256, 0, st>>>(inc_m, inc_idx, inc_a0, alpha, dalpha, dmark, gathered);
+                k_inc_marks<<<grid1(n), 256, 0, st>>>(n, mark, gathered, q1, q2);
+                CK(cudaGetLastError());
+                launches += 2;
+                inc_q = ar.alloc<int32_t>(n);
+                inc_list = ar.alloc<int32_t>(n);
+                inc_coef = ar.alloc<double>(n);
+                inc_nq = compact(ar, PRED_UNMARKED, n, q1, alpha, D.y, inc_q, nullptr, st, &launches);
+                inc_nd = compact(ar, PRED_MARKED, n, dmark, dalpha, D.y, inc_list, inc_coef, st, &launches);
+                full_mark = q2;   // the full sum only for the gathered rows shrunk later
+                ++inc_recons;
+            }
+            int64_t nw = compact(ar, PRED_UNMARKED, n, full_mark, alpha, D.y, list_w, nullptr, st, &launches);
+            int64_t nsv = nw > 0 ? compact(ar, PRED_ALPHA_POS, n, mark, alpha, D.y, list_sv, coef, st, &launches) : 0;
             RbfContract c;
             std::memset(&c, 0, sizeof c);
             c.x_indptr = D.indptr;
@@ -1389,7 +1471,18 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
                     set_err("a wait in the tensor-core reconstruction exceeded its limit");
                     throw Fail{SVM_ERR_TIMEOUT};
                 }
-            } else {
+            } else if (nw > 0) {
+                CK(launch_rbf_contract(c, st));
+                ++launches;
+            }
+            if (inc_nq > 0 && inc_nd > 0) {
+                c.sv = inc_list;
+                c.coef = inc_coef;
+                c.nsv = inc_nd;
+                c.q = inc_q;
+                c.nq = inc_nq;
+                c.yq = nullptr;
+                c.accumulate = 1;
                 CK(launch_rbf_contract(c, st));
                 ++launches;
             }
@@ -1448,6 +1541,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         stats->iters = hc.iter;
         stats->shrink_events = hc.shrink_events;
         stats->reconstructions = n_recon;
+        stats->incremental_recons = (int32_t)inc_recons;
         stats->final_active = hc.active;
         stats->n_sv = fp.nsv;
         stats->n_bound = fp.nbound;

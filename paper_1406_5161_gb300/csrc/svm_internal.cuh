@@ -302,6 +302,7 @@ struct RbfContract {
     double *out;
     const int8_t *yq;          // subtract yq[row] when non-NULL
     double add_scalar;
+    int32_t accumulate;        // 1: add to out[] instead of writing (CUDA-core path only)
 };
 cudaError_t launch_rbf_contract(const RbfContract &c, cudaStream_t st);
 

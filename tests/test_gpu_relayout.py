@@ -150,3 +150,30 @@ def test_automatic_shape_with_relayout_against_the_oracle():
     t = first_mismatch(r["trace"], ref["trace"], ref.get("margin"), 300)
     assert t >= 200
     check_end_state(p, r, ref)
+
+
+@pytest.mark.parametrize("prec,name,flags", [(pkg.SVM_FP64, "Multi500", 0), (pkg.SVM_FP64, "Multi5pc", 0),
+                                             (pkg.SVM_MIXED_BF16_SIMT, "Multi500", pkg.SVM_FLAG_STREAM_ROWS)])
+def test_incremental_reconstruction_matches_full_sum(prec, name, flags):
+    """After a multiple-reconstruction restart the rows shrunk when the active
+    rows are gathered are reconstructed as their f at that moment plus the sum
+    over the gathered rows whose alpha changed since (Algorithm 6's sum less
+    the unchanged terms): the solve matches the one with Algorithm 6's full
+    sum (SVM_FLAG_FULL_RECON) up to rounding order, and in FP64 passes the
+    oracle's KKT check (a mixed-precision solve is optimal for the
+    BF16-rounded kernel, not for the oracle's)."""
+    p = synth.covtype_like(n=40000, n_test=0, seed=17)
+    Xd = pkg.to_device(p.X)
+    yd = torch.as_tensor(p.y, device="cuda")
+    pol = pkg.POLICIES[name]
+    a = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=prec, shrink=pol, flags=flags)
+    b = pkg.svm_train(Xd, yd, p.C, p.gamma, p.tau, precision=prec, shrink=pol,
+                      flags=flags | pkg.SVM_FLAG_FULL_RECON)
+    assert a["status"] == b["status"] == pkg.SVM_OK
+    assert a["stats"]["incremental_recons"] >= 1 and b["stats"]["incremental_recons"] == 0
+    assert a["stats"]["reconstructions"] == b["stats"]["reconstructions"]
+    wa, wb = a["stats"]["objective"], b["stats"]["objective"]
+    assert abs(wa - wb) <= 1e-9 * abs(wb)
+    assert abs(a["b"] - b["b"]) <= 1e-6
+    if prec == pkg.SVM_FP64:
+        _kkt(p, a)
