@@ -1,6 +1,7 @@
 """The stored oracle answer for the full covtype-shaped workload
 (tests/golden/covtype_full*, written by make_covtype_full.py from oracle/
-alone) is complete and consistent: it belongs to the generator's current
+alone: without shrinking, and with the Multi500 policy) is complete and
+consistent: it belongs to the generator's current
 output, its alpha is feasible (0 <= alpha <= C, sum y alpha = 0) and has the
 recorded hash and support-vector counts, its gap met the stopping rule
 (Eq. kktterm), and the 10,000 held-out decision values are all there."""
@@ -18,10 +19,14 @@ from paper_1406_5161_gb300 import synth  # noqa: E402
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def test_covtype_full_answer_is_consistent():
-    meta = json.load(open(os.path.join(GOLDEN, "covtype_full.json")))
-    dec = np.loadtxt(os.path.join(GOLDEN, "covtype_full_decision.txt"), comments="#")
-    a = np.load(os.path.join(GOLDEN, "covtype_full_alpha.npz"))["alpha"]
+import pytest  # noqa: E402
+
+
+@pytest.mark.parametrize("tag", ["covtype_full", "covtype_full_multi500"])
+def test_covtype_full_answer_is_consistent(tag):
+    meta = json.load(open(os.path.join(GOLDEN, tag + ".json")))
+    dec = np.loadtxt(os.path.join(GOLDEN, tag + "_decision.txt"), comments="#")
+    a = np.load(os.path.join(GOLDEN, tag + "_alpha.npz"))["alpha"]
     p = synth.covtype_like()
     assert input_digest(p) == meta["input_sha256"]
     assert (meta["n"], meta["d"], meta["C"], meta["gamma"], meta["tau"]) == (p.X.n, p.X.d, p.C, p.gamma, p.tau)
