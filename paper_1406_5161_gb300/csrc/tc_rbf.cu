@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kTile = 128;            // rows per query tile and per SV tile (M = N)
 constexpr int kKB = 64;               // BF16 elements per 128-byte swizzle row
-constexpr int kTcThreads = 256;       // 8 warps: TMEM lane quadrant w % 4, column half w / 4
+constexpr int kTcThreads = 320;       // warp 0 loads, warp 1 MMA, warps 2..9 epilogue
 constexpr int kMaxKBlocks = 4;        // d_pad <= 256
 constexpr uint32_t kTileBytes = kTile * kKB * 2;   // 16 KiB per k-block tile
 constexpr long long kWaitLimit = 1ll << 26;        // mbarrier polls before giving up
@@ -114,6 +114,7 @@ constexpr uint32_t kIdesc = (1u << 4)                  // D format F32
 struct TcArgs {
     int64_t nq, nsv;
     int kblocks;                 // d_pad / 64
+    int stages;                  // support-tile slots in shared memory (2..4)
     const float *zc;             // per query: -gamma * log2(e) * ||z||^2
     const float *xc;             // per SV (padded): -gamma * log2(e) * ||x||^2
     const float *coef;           // per SV (padded): alpha * y (0 on padding)
@@ -158,11 +159,64 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// One CTA: a 128-row query tile against all support-vector tiles. Support
-// tiles are double-buffered in shared memory and their products in two
-// 128-column tensor-memory accumulators, so that the TMA load of tile t+1 and
-// the MMA of tile t run while the four warps evaluate the epilogue of tile
-// t-1.
+// One CTA: a 128-row query tile against all support-vector tiles, with the
+// roles split by warp and handed over by mbarriers only (no CTA-wide barrier
+// inside the tile loop):
+//   warp 0 (one thread)  TMA loads of the support tiles and their constants
+//                        into a ring of `stages` shared-memory slots;
+//   warp 1 (one thread)  tcgen05.mma of each tile into one of two 128-column
+//                        tensor-memory accumulators;
+//   warps 2..9           the epilogue: each reads its 32-lane quadrant
+//                        (warp % 4) and half of the columns of an accumulator
+//                        with tcgen05.ld, evaluates coef * 2^(...) and sums.
+// full[s]  : the tile in slot s has landed (TMA transaction bytes);
+// empty[s] : slot s is free again (the MMA's commit + one arrival per
+//            epilogue warp, which also read the slot's constants);
+// accf[b]  : accumulator b holds a finished tile (MMA commit);
+// acce[b]  : the epilogue has read accumulator b (one arrival per warp).
+// Tile t uses slot t % stages (round t / stages) and accumulator t & 1 (use
+// t >> 1); the k-th completion of a barrier has parity k & 1.
+constexpr int kEpiWarps = 8;
+constexpr int kMaxStages = 4;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait that also gives up once another role has failed. The thread
+// sleeps in the barrier (suspend-time hint) until the phase completes or the
+// hint runs out, so waiting warps take no issue slots from the epilogue; the
+// whole wait is bounded by kWaitNs of the global timer.
+constexpr uint64_t kWaitNs = 5ull * 1000 * 1000 * 1000;
+__device__ __forceinline__ bool mbar_wait_or_fail(uint64_t *bar, uint32_t parity, const volatile int *fail)
+{
+    const uint32_t a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity), "r"(20000u)
+            : "memory");
+        if (ok) return true;
+        if (*fail) return false;
+        const uint64_t now = global_ns();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > kWaitNs) return false;
+    }
+}
+
 __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constant__ CUtensorMap mapZ,
                                                             const __grid_constant__ CUtensorMap mapX,
                                                             TcArgs a)
@@ -170,28 +224,36 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *dsm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *tileA = dsm;                                       // [kblocks][16 KiB]
-    unsigned char *tileB0 = dsm + (size_t)a.kblocks * kTileBytes;     // [2][kblocks][16 KiB]
-    __shared__ __align__(8) uint64_t bar_q, bar_load[2], bar_mma[2], bar_drain;
+    const int S = a.stages;
+    const size_t tile_all = (size_t)a.kblocks * kTileBytes;   // one tile, all k-blocks
+    unsigned char *tileA = dsm;                               // the query tile
+    unsigned char *tileB = dsm + tile_all;                    // [S][kblocks][16 KiB]
+    __shared__ __align__(8) uint64_t bar_q, bar_full[kMaxStages], bar_empty[kMaxStages], bar_accf[2],
+        bar_acce[2], bar_drain;
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(16) float s_xc[3][kTile], s_coef[3][kTile];   // per-SV constants of 3 tiles
+    __shared__ __align__(16) float s_xc[kMaxStages][kTile], s_coef[kMaxStages][kTile];
     __shared__ double s_acc[kTile];   // the second column half's row sums
     __shared__ int s_fail;
+    const volatile int *fail = &s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t q0 = (int64_t)blockIdx.x * kTile;
     if (tid == 0) {
         mbar_init(&bar_q, 1);
-        mbar_init(&bar_load[0], 1);
-        mbar_init(&bar_load[1], 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
+        for (int k = 0; k < kMaxStages; ++k) {
+            mbar_init(&bar_full[k], 1);
+            mbar_init(&bar_empty[k], 1 + kEpiWarps);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&bar_accf[k], 1);
+            mbar_init(&bar_acce[k], kEpiWarps);
+        }
         mbar_init(&bar_drain, 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(&tmem_base)), "r"(2 * kTile) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -202,52 +264,52 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
     const uint32_t tmem = tmem_base;
     const int64_t ntiles = (a.nsv + kTile - 1) / kTile;
 
-    // support tile t: rows into buffer t & 1 (TMA), per-SV constants into
-    // slot t % 3 (bulk copies), issued by one thread
-    unsigned pending = 0;   // bit b: a load into buffer b not yet waited for
-    auto load_tile = [&](int64_t t) {
-        const int b = (int)(t & 1), cs = (int)(t % 3);
-        if (tid == 0) {
-            unsigned char *tb = tileB0 + (size_t)b * a.kblocks * kTileBytes;
-            // the buffer's last readers (generic proxy) passed a barrier before this
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar_load[b], (uint32_t)a.kblocks * kTileBytes + 2 * kTile * 4);
-            for (int kb = 0; kb < a.kblocks; ++kb)
-                tma_load_2d(tb + (size_t)kb * kTileBytes, &mapX, kb * kKB, (int)(t * kTile), &bar_load[b]);
-            bulk_load(s_xc[cs], a.xc + t * kTile, kTile * 4, &bar_load[b]);
-            bulk_load(s_coef[cs], a.coef + t * kTile, kTile * 4, &bar_load[b]);
-        }
-        pending |= 1u << b;
-    };
-    // the query tile (all k-blocks) stays in shared memory
-    if (tid == 0) {
-        mbar_expect_tx(&bar_q, (uint32_t)a.kblocks * kTileBytes);
-        for (int kb = 0; kb < a.kblocks; ++kb)
-            tma_load_2d(tileA + (size_t)kb * kTileBytes, &mapZ, kb * kKB, (int)q0, &bar_q);
-    }
-    bool q_pending = true;
-    load_tile(0);
-    if (ntiles > 1) load_tile(1);
-    bool ok = __syncthreads_and(mbar_wait(&bar_q, 0)) != 0;   // uniform decision
-    if (ok) q_pending = false;
-
-    const int quad = warp & 3, half = warp >> 2;
-    const int my_row = quad * 32 + lane;                 // TMEM lane = query row in tile
-    const int64_t q = q0 + my_row;
-    const float zc = (q < a.nq) ? a.zc[q] : 0.f;
+    bool ok = true;
+    int64_t issued = 0;         // producer: support tiles whose loads were issued
+    bool q_issued = false;
+    const int quad = warp & 3, half = (warp - 2) >> 2;    // epilogue warps
+    const int my_row = quad * 32 + lane;                  // TMEM lane = query row in tile
     double acc = 0.0;
-    uint32_t ph_load = 0, ph_mma = 0;   // bit b: parity of the next phase of buffer b
-    for (int64_t t = 0; t <= ntiles && ok; ++t) {
-        if (t < ntiles) {
-            // MMA of tile t: D[b] = Z_tile * X_tile^T over all K
-            const int b = (int)(t & 1);
-            ok = __syncthreads_and(mbar_wait(&bar_load[b], (ph_load >> b) & 1u)) != 0;
-            if (!ok) break;
-            ph_load ^= 1u << b;
-            pending &= ~(1u << b);
-            if (tid == 0) {
+
+    if (warp == 0) {
+        // ---- producer
+        if (lane == 0) {
+            mbar_expect_tx(&bar_q, (uint32_t)tile_all);
+            for (int kb = 0; kb < a.kblocks; ++kb)
+                tma_load_2d(tileA + (size_t)kb * kTileBytes, &mapZ, kb * kKB, (int)q0, &bar_q);
+            q_issued = true;
+            for (int64_t t = 0; t < ntiles; ++t) {
+                const int sl = (int)(t % S);
+                const int64_t r = t / S;
+                if (r >= 1 && !mbar_wait_or_fail(&bar_empty[sl], (uint32_t)((r - 1) & 1), fail)) {
+                    ok = false;
+                    break;
+                }
+                // the slot's last readers included the epilogue's generic loads
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                unsigned char *tb = tileB + (size_t)sl * tile_all;
+                mbar_expect_tx(&bar_full[sl], (uint32_t)tile_all + 2 * kTile * 4);
+                for (int kb = 0; kb < a.kblocks; ++kb)
+                    tma_load_2d(tb + (size_t)kb * kTileBytes, &mapX, kb * kKB, (int)(t * kTile), &bar_full[sl]);
+                bulk_load(s_xc[sl], a.xc + t * kTile, kTile * 4, &bar_full[sl]);
+                bulk_load(s_coef[sl], a.coef + t * kTile, kTile * 4, &bar_full[sl]);
+                issued = t + 1;
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issue: D[b] = Z_tile * X_tile^T over all K
+        if (lane == 0) {
+            ok = mbar_wait_or_fail(&bar_q, 0, fail);
+            for (int64_t t = 0; ok && t < ntiles; ++t) {
+                const int sl = (int)(t % S), b = (int)(t & 1);
+                const int64_t r = t / S, u = t >> 1;
+                if (!mbar_wait_or_fail(&bar_full[sl], (uint32_t)(r & 1), fail) ||
+                    (u >= 1 && !mbar_wait_or_fail(&bar_acce[b], (uint32_t)((u - 1) & 1), fail))) {
+                    ok = false;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const unsigned char *tb = tileB0 + (size_t)b * a.kblocks * kTileBytes;
+                const unsigned char *tb = tileB + (size_t)sl * tile_all;
                 const uint32_t dcol = tmem + (uint32_t)(b * kTile);
                 for (int kb = 0; kb < a.kblocks; ++kb) {
                     const uint32_t sa = smem_u32(tileA + (size_t)kb * kTileBytes);
@@ -265,73 +327,107 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
                             : "memory");
                     }
                 }
+                // both fire when these MMAs are done: the accumulator is
+                // ready, and the MMA no longer reads the slot
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             ::"r"(smem_u32(&bar_mma[b])) : "memory");
+                             ::"r"(smem_u32(&bar_accf[b])) : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&bar_empty[sl])) : "memory");
             }
         }
-        if (t >= 1) {
-            // epilogue of tile t-1 while the MMA of tile t runs
-            const int pb = (int)((t - 1) & 1), pc = (int)((t - 1) % 3);
-            ok = __syncthreads_and(mbar_wait(&bar_mma[pb], (ph_mma >> pb) & 1u)) != 0;
-            if (!ok) break;
-            ph_mma ^= 1u << pb;
-            // the MMA of tile t-1 is done with buffer pb: load tile t+1 into
-            // it now, a whole epilogue ahead of its use (its constants go to
-            // slot (t+1) % 3, last read by the epilogue of tile t-2)
-            if (t + 1 < ntiles) load_tile(t + 1);
+    } else {
+        // ---- epilogue
+        const int64_t q = q0 + my_row;
+        const float zc = (q < a.nq) ? a.zc[q] : 0.f;
+        const unsigned long long zc2 = pack_f32x2(zc, zc), g2v = pack_f32x2(a.g2, a.g2);
+        // The row's scaled norm factors out of the sum:
+        //   sum_j c_j 2^min(g2 dot_j + xc_j + zc, 0)
+        //     = 2^zc sum_j c_j 2^min(g2 dot_j + xc_j, -zc),
+        // one addition less per pair; 2^zc is applied once per tile. A warp
+        // with a row whose 2^-zc would leave FP32 (-zc > 120) keeps the
+        // per-pair form.
+        const float nzc = -zc;
+        const bool factored = !__any_sync(0xffffffffu, nzc > 120.f);
+        const double row_scale = factored ? exp2((double)zc) : 1.0;
+        for (int64_t t = 0; t < ntiles; ++t) {
+            const int sl = (int)(t % S), b = (int)(t & 1);
+            const int64_t r = t / S, u = t >> 1;
+            const bool w_ok = mbar_wait_or_fail(&bar_accf[b], (uint32_t)(u & 1), fail) &&
+                              mbar_wait_or_fail(&bar_full[sl], (uint32_t)(r & 1), fail);
+            if (!__all_sync(0xffffffffu, w_ok)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            unsigned long long part = pack_f32x2(0.f, 0.f);   // (columns j, j + 1) partial sums
-            const unsigned long long zc2 = pack_f32x2(zc, zc), g2v = pack_f32x2(a.g2, a.g2);
+            // (columns j, j + 1) partial sums, two chains
+            unsigned long long partA = pack_f32x2(0.f, 0.f), partB = partA;
 #pragma unroll 1
             for (int c0 = half * (kTile / 2); c0 < (half + 1) * (kTile / 2); c0 += 32) {
-                uint32_t r[32];
-                const uint32_t addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(pb * kTile + c0);
+                uint32_t rr[32];
+                const uint32_t addr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kTile + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                      "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]),
+                      "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]),
+                      "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]), "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]),
+                      "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]), "=r"(rr[28]), "=r"(rr[29]), "=r"(rr[30]),
+                      "=r"(rr[31])
                     : "r"(addr)
                     : "memory");
-                // the tile's constants for these 32 columns as column pairs:
-                // zc + xc (the row's and the column's scaled norms) and coef.
-                // The FP32 arithmetic runs on packed pairs (f32x2), half the
-                // instructions of the scalar form and the same IEEE result
-                // in each lane.
-                unsigned long long xz[16], cf[16];
-#pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const float4 x4 = reinterpret_cast<const float4 *>(&s_xc[pc][c0])[v];
-                    const float4 c4 = reinterpret_cast<const float4 *>(&s_coef[pc][c0])[v];
-                    xz[2 * v] = add_f32x2(pack_f32x2(x4.x, x4.y), zc2);
-                    xz[2 * v + 1] = add_f32x2(pack_f32x2(x4.z, x4.w), zc2);
-                    cf[2 * v] = pack_f32x2(c4.x, c4.y);
-                    cf[2 * v + 1] = pack_f32x2(c4.z, c4.w);
-                }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // the FP32 arithmetic runs on packed column pairs (f32x2),
+                // the same IEEE result in each lane as the scalar form
+                const float4 *xs = reinterpret_cast<const float4 *>(&s_xc[sl][c0]);
+                const float4 *cs = reinterpret_cast<const float4 *>(&s_coef[sl][c0]);
+                if (factored) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
-                    // log2 K = -gamma log2(e) (||z||^2 + ||x||^2 - 2 <z, x>), clamped at 0
-                    float e0, e1;
-                    unpack_f32x2(fma_f32x2(pack_f32x2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])), g2v,
-                                           xz[j >> 1]), e0, e1);
-                    const unsigned long long k2 = pack_f32x2(ex2_approx(fminf(e0, 0.f)), ex2_approx(fminf(e1, 0.f)));
-                    part = fma_f32x2(cf[j >> 1], k2, part);
+                    for (int v = 0; v < 8; ++v) {
+                        const float4 x4 = xs[v], c4 = cs[v];   // the same address in every lane
+                        const int j = 4 * v;
+                        float e0, e1, e2, e3;
+                        unpack_f32x2(fma_f32x2(pack_f32x2(__uint_as_float(rr[j]), __uint_as_float(rr[j + 1])), g2v,
+                                               pack_f32x2(x4.x, x4.y)), e0, e1);
+                        unpack_f32x2(fma_f32x2(pack_f32x2(__uint_as_float(rr[j + 2]), __uint_as_float(rr[j + 3])),
+                                               g2v, pack_f32x2(x4.z, x4.w)), e2, e3);
+                        const unsigned long long k01 = pack_f32x2(ex2_approx(fminf(e0, nzc)), ex2_approx(fminf(e1, nzc)));
+                        const unsigned long long k23 = pack_f32x2(ex2_approx(fminf(e2, nzc)), ex2_approx(fminf(e3, nzc)));
+                        partA = fma_f32x2(pack_f32x2(c4.x, c4.y), k01, partA);
+                        partB = fma_f32x2(pack_f32x2(c4.z, c4.w), k23, partB);
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const float4 x4 = xs[v], c4 = cs[v];
+                        const int j = 4 * v;
+                        float e0, e1, e2, e3;
+                        unpack_f32x2(fma_f32x2(pack_f32x2(__uint_as_float(rr[j]), __uint_as_float(rr[j + 1])), g2v,
+                                               add_f32x2(pack_f32x2(x4.x, x4.y), zc2)), e0, e1);
+                        unpack_f32x2(fma_f32x2(pack_f32x2(__uint_as_float(rr[j + 2]), __uint_as_float(rr[j + 3])),
+                                               g2v, add_f32x2(pack_f32x2(x4.z, x4.w), zc2)), e2, e3);
+                        const unsigned long long k01 = pack_f32x2(ex2_approx(fminf(e0, 0.f)), ex2_approx(fminf(e1, 0.f)));
+                        const unsigned long long k23 = pack_f32x2(ex2_approx(fminf(e2, 0.f)), ex2_approx(fminf(e3, 0.f)));
+                        partA = fma_f32x2(pack_f32x2(c4.x, c4.y), k01, partA);
+                        partB = fma_f32x2(pack_f32x2(c4.z, c4.w), k23, partB);
+                    }
                 }
             }
-            float part0, part1;
-            unpack_f32x2(part, part0, part1);
-            acc += (double)(part0 + part1);
-            // accumulator pb is rewritten by the MMA of tile t+1 only after
-            // the next iteration's barrier
+            float pa0, pa1, pb0, pb1;
+            unpack_f32x2(partA, pa0, pa1);
+            unpack_f32x2(partB, pb0, pb1);
+            acc += (double)((pa0 + pa1) + (pb0 + pb1)) * row_scale;
+            // this warp is done with accumulator b and with slot sl
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&bar_acce[b]);
+                mbar_arrive(&bar_empty[sl]);
+            }
         }
     }
-    if (!ok && tid == 0) {
+    if (!ok && lane == 0) {
         s_fail = 1;
         atomicExch(a.err, 1);
     }
@@ -339,29 +435,35 @@ __global__ void __launch_bounds__(kTcThreads) tc_rbf_kernel(const __grid_constan
     if (s_fail) {
         // let this CTA's outstanding asynchronous work finish (bounded)
         // before its shared and tensor memory are released
-        // (a commit tracks every earlier MMA of the issuing thread)
-        if (tid == 0) {
+        if (warp == 1 && lane == 0) {
+            // a commit tracks every earlier MMA of this thread
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          ::"r"(smem_u32(&bar_drain)) : "memory");
+            (void)mbar_wait(&bar_drain, 0);
         }
-        for (int b = 0; b < 2; ++b)
-            if ((pending >> b) & 1u) (void)mbar_wait(&bar_load[b], (ph_load >> b) & 1u);
-        if (q_pending) (void)mbar_wait(&bar_q, 0);
-        (void)mbar_wait(&bar_drain, 0);
+        if (warp == 0 && lane == 0) {
+            // loads in flight: at most the last `stages` tiles, one per slot
+            for (int64_t t = issued > S ? issued - S : 0; t < issued; ++t)
+                (void)mbar_wait(&bar_full[t % S], (uint32_t)((t / S) & 1));
+            if (q_issued) (void)mbar_wait(&bar_q, 0);
+        }
     } else {
         // the two column halves of a row meet in shared memory (fixed order)
-        if (half == 1) s_acc[my_row] = acc;
+        if (warp >= 2 && half == 1) s_acc[my_row] = acc;
         __syncthreads();
-        if (half == 0 && q < a.nq) {
-            const int32_t row = a.qrow[q];
-            double v = (acc + s_acc[my_row]) + a.add_scalar;
-            if (a.yq) v -= (double)a.yq[row];
-            a.out[row] = v;
+        if (warp >= 2 && half == 0) {
+            const int64_t q = q0 + my_row;
+            if (q < a.nq) {
+                const int32_t row = a.qrow[q];
+                double v = (acc + s_acc[my_row]) + a.add_scalar;
+                if (a.yq) v -= (double)a.yq[row];
+                a.out[row] = v;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTile)
                      : "memory");
     }
@@ -496,10 +598,11 @@ cudaError_t launch_rbf_contract_tc(const RbfContract &c, void *ws, int *err_host
     a.add_scalar = c.add_scalar;
     a.out = c.out;
     a.err = err;
-    // query tile + two support tiles; at least 80 KiB so that at most 2 CTAs
-    // share an SM: their 2 x 256 tensor-memory columns then fit the SM's 512
-    // without waiting
-    const size_t smem = std::max<size_t>(3 * (size_t)kblocks * kTileBytes + 1024, 80 * 1024);
+    // query tile + a ring of support tiles: 4 slots at d <= 64, else 2; at
+    // least 80 KiB so that at most 2 CTAs share an SM: their 2 x 256
+    // tensor-memory columns then fit the SM's 512 without waiting
+    a.stages = kblocks == 1 ? 4 : 2;
+    const size_t smem = std::max<size_t>((size_t)(1 + a.stages) * kblocks * kTileBytes + 1024, 80 * 1024);
     e = cudaFuncSetAttribute(tc_rbf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (c.nsv > 0) {
