@@ -702,10 +702,34 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         if (warp == 0) {
             if (!first) {
                 Acc s = 0;
+                bool kul_cached = false;   // FP64: K(up, low) read from the kernel-row cache
+                double kul_c = 0.0;
                 if constexpr (BITS) {
                     // ||x_up - x_low||^2 of binary rows
 #pragma unroll
                     for (int w = 0; w < 4 * W4; ++w) s += __popc(up.m[w] ^ low.m[w]);
+                } else if constexpr (MODE == MODE_FP64) {
+                    // K(up, low) with the row pass's own arithmetic for the
+                    // row of x_low against the x_up target (its entries in
+                    // order, split over LPR lanes as the row pass splits a
+                    // row), so that it equals, bit for bit, the entry the
+                    // kernel-row cache holds for it; when x_up's row is in
+                    // the cache that entry is read instead (written by the
+                    // owner of x_low's segment in an earlier step of this
+                    // launch, visible here through the exchanges since)
+                    if (kc_on && sh.kc_hu) {
+                        kul_c = __ldcg(static_cast<const double *>(A.kc) + (size_t)sh.kc_su * A.kc_ld + low.i);
+                        kul_cached = true;
+                    } else {
+                        if (lane < LPR) {
+                            for (int k = lane; k < low.len; k += LPR) {
+                                const Tgt t = T[tcl[k]];
+                                s = fma(t.y, t.x, s);
+                            }
+                        }
+#pragma unroll
+                        for (int off = LPR / 2; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                    }
                 } else {
                     for (int k = lane; k < low.len; k += 32) {
                         const Tgt t = T[tcl[k]];
@@ -732,10 +756,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     } else {
                         if (A.kernel == KERNEL_RBF) {
                             if constexpr (MODE == MODE_FP64) {
-                                // the table-driven exp: a shorter dependency
-                                // chain on the serial pair step than CUDA's exp
+                                // the table-driven exp, as in the row pass
                                 double d2 = up.nrm + low.nrm - 2.0 * s;
-                                kul = exp_tang(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2), exp2_s);
+                                kul = kul_cached ? kul_c
+                                                 : exp_tang(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2), exp2_s);
                             } else {
                                 float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
                                 kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
@@ -745,7 +769,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             // eta = K_uu + K_ll - 2 K_ul, K_uu from ||x_up||^2
                             double kuu, kll;
                             if constexpr (MODE == MODE_FP64) {
-                                kul = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, s);
+                                kul = kul_cached ? kul_c : kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, s);
                                 kuu = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, up.nrm);
                                 kll = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, low.nrm);
                             } else {
