@@ -55,9 +55,15 @@ enum svm_status {
 /* ------------------------------------------------------------- precision */
 enum svm_precision {
     /* FP64 everywhere the result depends on it: inner products, kernel
-     * values, f, the pair step, b and the gap. Binary (all values 1.0) CSR
-     * input is detected at ingest and its kernel values are taken from an
-     * exact FP64 table of exp(-gamma * k), k the integer squared distance. */
+     * values, f, the pair step, b and the gap. Inner products (and the
+     * squared norms) of float rows are computed exactly in 128-bit integer
+     * arithmetic and rounded once to the nearest double, when the nonzero
+     * values of the matrix lie within 31 binades below the largest (rows
+     * shorter than 2^17 entries; fewer binades for longer rows) and none is
+     * subnormal; otherwise they are FP64 sums in row order. Binary (all
+     * values 1.0) CSR input is detected at ingest and its kernel values are
+     * taken from an exact FP64 table of exp(-gamma * k), k the integer
+     * squared distance. */
     SVM_FP64 = 0,
     /* Inner products and exp in FP32 on BF16-rounded feature values (the
      * reconstruction and decision contractions on the tcgen05 tensor cores

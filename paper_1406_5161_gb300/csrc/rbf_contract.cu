@@ -39,7 +39,14 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
                  typename std::conditional<MODE == MODE_MIXED, float, unsigned>::type>::type;
     Elem *Zt = reinterpret_cast<Elem *>(dsm);
     const int tile_words = MODE == MODE_BINARY ? d : d * TQ;
-    for (int w = tid; w < tile_words; w += kCThreads) Zt[w] = (Elem)0;
+    // FP64 with exact inner products: a tile entry holds (m, b) of the value
+    // as two ints (xd_mant, xd_exp); an absent value is m = 0, b = tmin
+    const bool xd = MODE == MODE_FP64 && c.xd.on;
+    Elem zero = (Elem)0;
+    if constexpr (MODE == MODE_FP64) {
+        if (xd) zero = __hiloint2double(c.xd.tmin, 0);
+    }
+    for (int w = tid; w < tile_words; w += kCThreads) Zt[w] = zero;
     if constexpr (MODE == MODE_FP64) {
         for (int w = tid; w < kExp2TabLen; w += kCThreads) exp2_s[w] = kExp2Tab[w];
     }
@@ -62,7 +69,11 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
         for (int64_t p = p0 + tid; p < p1; p += kCThreads) {
             const int col = c.z_indices[p];
             if constexpr (MODE == MODE_BINARY) atomicOr(&Zt[col], 1u << q);
-            else if constexpr (MODE == MODE_FP64) Zt[(size_t)col * TQ + q] = widen_f32(c.z_values[p]);
+            else if constexpr (MODE == MODE_FP64) {
+                const float v = c.z_values[p];
+                const uint32_t u = __float_as_uint(v);
+                Zt[(size_t)col * TQ + q] = xd ? __hiloint2double(xd_exp(u, c.xd.tmin), xd_mant(u)) : widen_f32(v);
+            }
             else Zt[(size_t)col * TQ + q] = (Elem)c.z_values[p];
         }
     }
@@ -93,13 +104,34 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
             }
         } else if constexpr (MODE == MODE_FP64) {
             double acc[TQ];
+            if (xd) {
+                // exact inner products in integer arithmetic, rounded once
+                XdAcc a[TQ];
 #pragma unroll
-            for (int q = 0; q < TQ; ++q) acc[q] = 0.0;
-            for (int64_t p = p0; p < p1; ++p) {
-                const double v = widen_f32(c.x_values[p]);
-                const double *zc = Zt + (size_t)c.x_indices[p] * TQ;
+                for (int q = 0; q < TQ; ++q) a[q] = xd_zero();
+                const int2 *Z2 = reinterpret_cast<const int2 *>(Zt);
+                for (int64_t p = p0; p < p1; ++p) {
+                    const uint32_t u = __float_as_uint(c.x_values[p]);
+                    const int32_t m = xd_mant(u);
+                    const int e = xd_exp(u, c.xd.tmin) + c.xd.bias;
+                    const int2 *zc = Z2 + (size_t)c.x_indices[p] * TQ;
 #pragma unroll
-                for (int q = 0; q < TQ; ++q) acc[q] = fma(v, zc[q], acc[q]);
+                    for (int q = 0; q < TQ; ++q) {
+                        const int2 t = zc[q];
+                        xd_add(a[q], m, t.x, e + t.y);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < TQ; ++q) acc[q] = xd_round(a[q], c.xd.unit);
+            } else {
+#pragma unroll
+                for (int q = 0; q < TQ; ++q) acc[q] = 0.0;
+                for (int64_t p = p0; p < p1; ++p) {
+                    const double v = widen_f32(c.x_values[p]);
+                    const double *zc = Zt + (size_t)c.x_indices[p] * TQ;
+#pragma unroll
+                    for (int q = 0; q < TQ; ++q) acc[q] = fma(v, zc[q], acc[q]);
+                }
             }
             const double xn = c.x_norm[j];
             if (c.kernel == KERNEL_RBF) {

@@ -135,8 +135,17 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
         const double thr = 2.0 * J.tau;
         const int32_t *rows = J.rows;
 
+        // FP64 with exact inner products (J.xd.on): target entries hold (m, b)
+        // pairs as in the single-solve kernel; an absent value m = 0, b = tmin
+        const bool xd = MODE == MODE_FP64 && J.xd.on;
+        const int xd_tmin = J.xd.tmin, xd_bias = J.xd.bias, xd_unit = J.xd.unit;
+        Tgt tclear;
+        tgt_clear<MODE>(tclear);
+        if constexpr (MODE == MODE_FP64) {
+            if (xd) tclear = make_double2(__hiloint2double(xd_tmin, 0), __hiloint2double(xd_tmin, 0));
+        }
         // ---- job set-up: tables, empty target buffers, alpha = 0, f = -y
-        for (int c = tid; c < 2 * dmax; c += kThreads) tgt_clear<MODE>(tbuf[c]);
+        for (int c = tid; c < 2 * dmax; c += kThreads) tbuf[c] = tclear;
         if constexpr (MODE == MODE_BINARY) {
             for (int k = tid; k < B.ktab_len; k += kThreads) {
                 const double kv = exp(-gamma * (double)k);
@@ -184,14 +193,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                         const int c = indices[up.p0 + k];
                         tcu[k] = c;
                         if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
-                        else if constexpr (MODE == MODE_FP64) T[c].x = (double)values[up.p0 + k];
+                        else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], values[up.p0 + k], xd, xd_tmin);
                         else T[c].x = vmix[up.p0 + k];
                     }
                     for (int k = tid; k < low.len; k += kThreads) {
                         const int c = indices[low.p0 + k];
                         tcl[k] = c;
                         if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
-                        else if constexpr (MODE == MODE_FP64) T[c].y = (double)values[low.p0 + k];
+                        else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], values[low.p0 + k], xd, xd_tmin);
                         else T[c].y = vmix[low.p0 + k];
                     }
                 }
@@ -206,6 +215,17 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                     if (dense) {
                         if constexpr (MODE == MODE_MIXED)
                             for (int c = lane; c < d; c += 32) s = fmaf(T[c].y, T[c].x, s);
+                    } else if (xd) {
+                        if constexpr (MODE == MODE_FP64) {
+                            const int4 *T4 = reinterpret_cast<const int4 *>(T);
+                            XdAcc a = xd_zero();
+                            for (int k = lane; k < low.len; k += 32) {
+                                const int4 t = T4[tcl[k]];
+                                xd_add(a, t.z, t.x, t.w + t.y + xd_bias);
+                            }
+                            xd_lane_sum<32>(a);
+                            s = xd_round(a, xd_unit);
+                        }
                     } else {
                         for (int k = lane; k < low.len; k += 32) {
                             const Tgt t = T[tcl[k]];
@@ -214,8 +234,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                             else s = fmaf(t.y, t.x, s);
                         }
                     }
+                    if (!xd) {
 #pragma unroll
-                    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    }
                     if (lane == 0) {
                         double kul, rinv = 0.0;
                         if constexpr (MODE == MODE_BINARY) {
@@ -524,6 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                             }
                         }
                         Acc su = 0, sl = 0;
+                        XdAcc au = xd_zero(), al = xd_zero();   // FP64, exact inner products
                         if (!first && valid) {
                             if (dense) {
                                 if constexpr (MODE == MODE_MIXED) {
@@ -541,6 +564,18 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                                         sl = fmaf(v.y, t1.y, sl);
                                     }
                                 }
+                                }
+                            } else if (xd) {
+                                if constexpr (MODE == MODE_FP64) {
+                                    const int4 *T4 = reinterpret_cast<const int4 *>(T);
+                                    for (int64_t p = p0 + gl; p < p1; p += LPR) {
+                                        const uint32_t u = __float_as_uint(values[p]);
+                                        const int32_t mx = xd_mant(u);
+                                        const int e = xd_exp(u, xd_tmin) + xd_bias;
+                                        const int4 t = T4[indices[p]];
+                                        xd_add(au, mx, t.x, e + t.y);
+                                        xd_add(al, mx, t.z, e + t.w);
+                                    }
                                 }
                             } else {
                                 for (int64_t p = p0 + gl; p < p1; p += LPR) {
@@ -563,7 +598,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                                 }
                             }
                         }
-                        if (!first) {
+                        if (!first && xd) {
+                            if constexpr (MODE == MODE_FP64) {
+                                xd_lane_sum<LPR>(au);
+                                xd_lane_sum<LPR>(al);
+                                su = xd_round(au, xd_unit);
+                                sl = xd_round(al, xd_unit);
+                            }
+                        } else if (!first) {
 #pragma unroll
                             for (int o = LPR / 2; o >= 1; o >>= 1) {
                                 su += __shfl_xor_sync(0xffffffffu, su, o);
@@ -639,8 +681,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                 } else {
                     const int *pcu = tcol + (size_t)((1 - buf) * 2 + 0) * maxnnz;
                     const int *pcl = tcol + (size_t)((1 - buf) * 2 + 1) * maxnnz;
-                    for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) tgt_clear<MODE>(P[pcu[k]]);
-                    for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) tgt_clear<MODE>(P[pcl[k]]);
+                    for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) P[pcu[k]] = tclear;
+                    for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) P[pcl[k]] = tclear;
                 }
             }
             cluster.sync();

@@ -377,6 +377,37 @@ __device__ __forceinline__ void tgt_clear(typename RowMath<MODE>::Tgt &t)
     else t = make_float2(0.f, 0.f);
 }
 
+// FP64 target entry, side 0 (x_up) or 1 (x_low): the value as a double, or,
+// with exact inner products, its (m, b) as two ints in the double's place
+template <int SIDE>
+__device__ __forceinline__ void xd_put(double2 &t, float v, bool xd, int tmin)
+{
+    double w;
+    if (xd) {
+        const uint32_t u = __float_as_uint(v);
+        w = __hiloint2double(xd_exp(u, tmin), xd_mant(u));
+    } else {
+        w = (double)v;
+    }
+    if (SIDE == 0) t.x = w;
+    else t.y = w;
+}
+
+// the exact partial sums of LPR consecutive lanes, added in every one of them
+template <int LPR>
+__device__ __forceinline__ void xd_lane_sum(XdAcc &a)
+{
+#pragma unroll
+    for (int off = LPR / 2; off >= 1; off >>= 1) {
+        XdAcc b;
+        b.w0 = __shfl_xor_sync(0xffffffffu, a.w0, off);
+        b.w1 = __shfl_xor_sync(0xffffffffu, a.w1, off);
+        b.w2 = __shfl_xor_sync(0xffffffffu, a.w2, off);
+        b.w3 = __shfl_xor_sync(0xffffffffu, a.w3, off);
+        xd_add(a, b);
+    }
+}
+
 // SOLO: the grid is one thread-block cluster (exchange through distributed
 // shared memory only); a separate instantiation, so that the kernels for
 // several clusters carry none of its code. WSS: i_low by the second-order
@@ -432,9 +463,19 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     const int nseg = (int)(seg_lo(A.n, G, cta + 1) - lo);
     const int64_t base = A.indptr[lo];   // global CSR offset of the segment
 
+    // FP64 mode with exact inner products (A.xd.on): a target entry holds, as
+    // four ints, (m, b) of x_up's value and (m, b) of x_low's value at its
+    // column (xd_mant, xd_exp); an absent value is m = 0, b = tmin
+    const bool xd = MODE == MODE_FP64 && A.xd.on;
+    const int xd_tmin = A.xd.tmin, xd_bias = A.xd.bias, xd_unit = A.xd.unit;
+    Tgt tclear;
+    tgt_clear<MODE>(tclear);
+    if constexpr (MODE == MODE_FP64) {
+        if (xd) tclear = make_double2(__hiloint2double(xd_tmin, 0), __hiloint2double(xd_tmin, 0));
+    }
     // ---- set-up
     if constexpr (!BITS) {
-        for (int c = tid; c < 2 * d; c += kThreads) tgt_clear<MODE>(tbuf[c]);
+        for (int c = tid; c < 2 * d; c += kThreads) tbuf[c] = tclear;
     }
     if constexpr (MODE == MODE_BINARY || BITS) {
         for (int c = tid; c < 3 * A.ktab_len; c += kThreads) ktab[c] = A.ktab[c];
@@ -674,14 +715,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 int c = A.indices[up.p0 + k];
                 tcu[k] = c;
                 if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
-                else if constexpr (MODE == MODE_FP64) T[c].x = (double)A.values[up.p0 + k];
+                else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], A.values[up.p0 + k], xd, xd_tmin);
                 else T[c].x = A.vmix[up.p0 + k];
             }
             if constexpr (!BITS) for (int k = tid; k < low.len; k += kThreads) {
                 int c = A.indices[low.p0 + k];
                 tcl[k] = c;
                 if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
-                else if constexpr (MODE == MODE_FP64) T[c].y = (double)A.values[low.p0 + k];
+                else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], A.values[low.p0 + k], xd, xd_tmin);
                 else T[c].y = A.vmix[low.p0 + k];
             }
             if (A.h > 0) {
@@ -720,6 +761,18 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     if (kc_on && sh.kc_hu) {
                         kul_c = __ldcg(static_cast<const double *>(A.kc) + (size_t)sh.kc_su * A.kc_ld + low.i);
                         kul_cached = true;
+                    } else if (xd) {
+                        // exact: the same value whatever the order or split
+                        const int4 *T4 = reinterpret_cast<const int4 *>(T);
+                        XdAcc a = xd_zero();
+                        if (lane < LPR) {
+                            for (int k = lane; k < low.len; k += LPR) {
+                                const int4 t = T4[tcl[k]];
+                                xd_add(a, t.z, t.x, t.w + t.y + xd_bias);
+                            }
+                        }
+                        xd_lane_sum<LPR>(a);
+                        s = xd_round(a, xd_unit);
                     } else {
                         if (lane < LPR) {
                             for (int k = lane; k < low.len; k += LPR) {
@@ -1046,7 +1099,38 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     }
                 }
                 Acc su = 0, sl = 0;
-                if constexpr (BITS) {
+                if (xd && !first && !skip_sums) {
+                    if constexpr (MODE == MODE_FP64) {
+                        // exact inner products in integer arithmetic, each
+                        // lane loading its next 8 entries at once
+                        const int4 *T4 = reinterpret_cast<const int4 *>(T);
+                        XdAcc au = xd_zero(), al = xd_zero();
+                        for (int64_t pb = p0 + gl; pb < p1; pb += 8 * LPR) {
+                            int cb[8];
+                            uint32_t ub[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int64_t p = pb + (int64_t)j * LPR;
+                                const bool in = p < p1;
+                                cb[j] = in ? COL(p) : 0;
+                                ub[j] = in ? __float_as_uint(VAL(p)) : 0u;
+                            }
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                if (pb + (int64_t)j * LPR >= p1) break;
+                                const int32_t m = xd_mant(ub[j]);
+                                const int e = xd_exp(ub[j], xd_tmin) + xd_bias;
+                                const int4 t = T4[cb[j]];
+                                xd_add(au, m, t.x, e + t.y);
+                                xd_add(al, m, t.z, e + t.w);
+                            }
+                        }
+                        xd_lane_sum<LPR>(au);
+                        xd_lane_sum<LPR>(al);
+                        su = xd_round(au, xd_unit);
+                        sl = xd_round(al, xd_unit);
+                    }
+                } else if constexpr (BITS) {
                     // squared distances to x_up and x_low (one lane per row)
                     if (!first && valid) {
                         const uint4 *rb = RES ? bits_s + (size_t)r * W4 : bits_g + (size_t)(lo + r) * W4;
@@ -1388,8 +1472,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 Tgt *P = tbuf + (size_t)(1 - buf) * d;
                 const int *pcu = tcol + (size_t)((1 - buf) * 2 + 0) * maxnnz;
                 const int *pcl = tcol + (size_t)((1 - buf) * 2 + 1) * maxnnz;
-                for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) tgt_clear<MODE>(P[pcu[k]]);
-                for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) tgt_clear<MODE>(P[pcl[k]]);
+                for (int k = tid - 256; k < prev_len_u; k += kThreads - 256) P[pcu[k]] = tclear;
+                for (int k = tid - 256; k < prev_len_l; k += kThreads - 256) P[pcl[k]] = tclear;
             }
             if constexpr (solo) {
                 if (warp == 0) {
@@ -1629,7 +1713,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     for (int k = tid; k < up.len; k += kThreads) {
                         const int c = A.indices[up.p0 + k];
                         if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(Tn + c)[0] = 1;
-                        else if constexpr (MODE == MODE_FP64) Tn[c].x = (double)A.values[up.p0 + k];
+                        else if constexpr (MODE == MODE_FP64) xd_put<0>(Tn[c], A.values[up.p0 + k], xd, xd_tmin);
                         else Tn[c].x = A.vmix[up.p0 + k];
                     }
                     __syncthreads();
@@ -1657,14 +1741,28 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             if (cand) ROWP(r, p0, p1);
                         }
                         Acc su = 0;
-                        for (int64_t p = p0 + gl; p < p1; p += LPR) {
-                            const int c = COL(p);
-                            if constexpr (MODE == MODE_BINARY) su += (int)(Tn[c] & 0xff);
-                            else if constexpr (MODE == MODE_FP64) su = fma(widen_f32(VAL(p)), Tn[c].x, su);
-                            else su = fmaf(VAL(p), Tn[c].x, su);
-                        }
+                        if (xd) {
+                            if constexpr (MODE == MODE_FP64) {
+                                const int4 *T4 = reinterpret_cast<const int4 *>(Tn);
+                                XdAcc a = xd_zero();
+                                for (int64_t p = p0 + gl; p < p1; p += LPR) {
+                                    const uint32_t u = __float_as_uint(VAL(p));
+                                    const int4 t = T4[COL(p)];
+                                    xd_add(a, xd_mant(u), t.x, xd_exp(u, xd_tmin) + xd_bias + t.y);
+                                }
+                                xd_lane_sum<LPR>(a);
+                                su = xd_round(a, xd_unit);
+                            }
+                        } else {
+                            for (int64_t p = p0 + gl; p < p1; p += LPR) {
+                                const int c = COL(p);
+                                if constexpr (MODE == MODE_BINARY) su += (int)(Tn[c] & 0xff);
+                                else if constexpr (MODE == MODE_FP64) su = fma(widen_f32(VAL(p)), Tn[c].x, su);
+                                else su = fmaf(VAL(p), Tn[c].x, su);
+                            }
 #pragma unroll
-                        for (int off = LPR / 2; off >= 1; off >>= 1) su += __shfl_xor_sync(0xffffffffu, su, off);
+                            for (int off = LPR / 2; off >= 1; off >>= 1) su += __shfl_xor_sync(0xffffffffu, su, off);
+                        }
                         if (cand && gl == 0) {
                             double eta;
                             if constexpr (MODE == MODE_BINARY) {

@@ -98,61 +98,107 @@ struct IngestInfo {
     unsigned long long npos;
     int maxnnz;
     int pad2;
+    // biased exponents of the nonzero values: the largest, 255 - the
+    // smallest, and whether a subnormal value occurs (exact inner products)
+    int bmax;
+    int nbmin;
+    int subnormal;
+    int pad3;
 };
 
-// Validates the CSR structure and labels; detects binary (all 1.0) values.
+// Validates the CSR structure and labels; detects binary (all 1.0) values;
+// the longest row and the exponent range of the values (one atomic per warp).
 __global__ void k_validate(int64_t n, int64_t d, const int64_t *indptr, const int32_t *indices,
                            const float *values, const int8_t *y, IngestInfo *info)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t p0 = indptr[i], p1 = indptr[i + 1];
-    if (p1 < p0 || (i == 0 && p0 != 0)) {
-        atomicOr(&info->bad_indptr, 1);
-        return;
-    }
-    int prev = -1;
-    bool nb = false, nf = false, bi = false;
-    for (int64_t p = p0; p < p1; ++p) {
-        int c = indices[p];
-        if (c <= prev || c >= d) bi = true;
-        prev = c;
-        if (values) {
-            float v = values[p];
-            if (!isfinite(v)) nf = true;
-            if (v != 1.0f) nb = true;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int len = 0, bmax = 0, nbmin = 0, sub = 0;
+    if (i < n) {
+        const int64_t p0 = indptr[i], p1 = indptr[i + 1];
+        if (p1 < p0 || (i == 0 && p0 != 0)) {
+            atomicOr(&info->bad_indptr, 1);
+        } else {
+            int prev = -1;
+            bool nb = false, nf = false, bi = false;
+            for (int64_t p = p0; p < p1; ++p) {
+                int c = indices[p];
+                if (c <= prev || c >= d) bi = true;
+                prev = c;
+                if (values) {
+                    const float v = values[p];
+                    if (!isfinite(v)) nf = true;
+                    if (v != 1.0f) nb = true;
+                    const uint32_t u = __float_as_uint(v);
+                    const int b = (int)((u >> 23) & 0xffu);
+                    if (b != 0) {
+                        bmax = max(bmax, b);
+                        nbmin = max(nbmin, 255 - b);
+                    } else if (u & 0x007fffffu) {
+                        sub = 1;
+                    }
+                }
+            }
+            if (bi) atomicOr(&info->bad_index, 1);
+            if (nf) atomicOr(&info->nonfinite, 1);
+            if (nb) atomicOr(&info->not_binary, 1);
+            len = (int)(p1 - p0);
+            if (y) {
+                int8_t v = y[i];
+                if (v != 1 && v != -1) atomicOr(&info->bad_y, 1);
+                if (v == 1) atomicAdd(&info->npos, 1ull);
+            }
         }
     }
-    if (bi) atomicOr(&info->bad_index, 1);
-    if (nf) atomicOr(&info->nonfinite, 1);
-    if (nb) atomicOr(&info->not_binary, 1);
-    atomicMax(&info->maxnnz, (int)(p1 - p0));
-    if (y) {
-        int8_t v = y[i];
-        if (v != 1 && v != -1) atomicOr(&info->bad_y, 1);
-        if (v == 1) atomicAdd(&info->npos, 1ull);
+    len = __reduce_max_sync(0xffffffffu, len);
+    bmax = __reduce_max_sync(0xffffffffu, bmax);
+    nbmin = __reduce_max_sync(0xffffffffu, nbmin);
+    sub = __reduce_or_sync(0xffffffffu, sub);
+    if ((threadIdx.x & 31) == 0) {
+        if (len) atomicMax(&info->maxnnz, len);
+        if (bmax) atomicMax(&info->bmax, bmax);
+        if (nbmin) atomicMax(&info->nbmin, nbmin);
+        if (sub) atomicOr(&info->subnormal, 1);
     }
 }
 
-// ||x_i||^2 in FP64 (row order), and the BF16-rounded copy with its FP32 norm.
+// The exact-inner-product format of one matrix from its validation record
+// (values NULL: every value is 1.0); host and device compute the same.
+__host__ __device__ XdFormat xd_of_info(const IngestInfo &h, const float *values)
+{
+    const int bmax = values ? h.bmax : 127, bmin = values ? 255 - h.nbmin : 127;
+    return xd_format(bmax, bmin, h.maxnnz, values && h.subnormal != 0);
+}
+
+// ||x_i||^2 in FP64: exact and rounded once when the matrix's format allows
+// (the inner product of the row with itself, as the row passes compute it),
+// else summed in row order; and the BF16-rounded copy with its FP32 norm.
+// info: the matrix's validation record, written by k_validate before.
 __global__ void k_norms(int64_t n, const int64_t *indptr, const float *values, double *norm,
-                        float *vmix, float *normf)
+                        float *vmix, float *normf, const IngestInfo *info)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const XdFormat xd = xd_of_info(*info, values);
     int64_t p0 = indptr[i], p1 = indptr[i + 1];
     double s = 0.0;
+    XdAcc a = xd_zero();
     float sf = 0.f;
     for (int64_t p = p0; p < p1; ++p) {
         float v = values ? values[p] : 1.0f;
-        s += (double)v * (double)v;
+        if (xd.on) {
+            const uint32_t u = __float_as_uint(v);
+            const int32_t m = xd_mant(u);
+            xd_add(a, m, m, 2 * xd_exp(u, xd.tmin) + xd.bias);
+        } else {
+            s += (double)v * (double)v;
+        }
         if (vmix) {
             float r = __bfloat162float(__float2bfloat16_rn(v));
             vmix[p] = r;
             sf = fmaf(r, r, sf);
         }
     }
-    if (norm) norm[i] = s;
+    if (norm) norm[i] = xd.on ? xd_round(a, xd.unit) : s;
     if (normf) normf[i] = sf;
 }
 
@@ -590,7 +636,18 @@ struct DevCSR {
     bool binary = false;
     int maxnnz = 0;
     int64_t npos = 0;
+    const IngestInfo *info = nullptr;   // the validation record (device)
+    XdFormat xd{};                      // exact inner products of the matrix with itself
+    int bmax = 0, bmin = 255;           // exponent range of the nonzero values
+    bool subnormal = false;
 };
+
+// The exact-inner-product format for products between two matrices.
+XdFormat xd_pair(const DevCSR &A, const DevCSR &B)
+{
+    return xd_format(std::max(A.bmax, B.bmax), std::min(A.bmin, B.bmin), std::max(A.maxnnz, B.maxnnz),
+                     A.subnormal || B.subnormal);
+}
 
 __global__ void k_fill_ones(int64_t m, float *v)
 {
@@ -667,13 +724,19 @@ void ingest(Arena &ar, const svm_csr *X, const int8_t *y, bool need_fp64, bool n
     }
     out.maxnnz = h.maxnnz;
     out.npos = (int64_t)h.npos;
+    out.info = info;
+    // input without values: every value is 1.0 (b = 127), filled or not
+    out.bmax = X->values ? h.bmax : 127;
+    out.bmin = X->values ? 255 - h.nbmin : 127;
+    out.subnormal = X->values && h.subnormal != 0;
+    out.xd = xd_format(out.bmax, out.bmin, out.maxnnz, out.subnormal);
     if (!out.binary && need_fp64) out.norm = ar.alloc<double>(X->n);
     if (!out.binary && need_mixed) {
         out.vmix = ar.alloc<float>(nnz);
         out.normf = ar.alloc<float>(X->n);
     }
     if (out.norm || out.vmix) {
-        k_norms<<<grid1(X->n), 256, 0, st>>>(X->n, out.indptr, out.values, out.norm, out.vmix, out.normf);
+        k_norms<<<grid1(X->n), 256, 0, st>>>(X->n, out.indptr, out.values, out.norm, out.vmix, out.normf, info);
         CK(cudaGetLastError());
         ++*launches;
     }
@@ -750,14 +813,22 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     int ktab_len = 2 * D.maxnnz + 1;
     const size_t lim = smem_limit() - 8192;
     if (mode == MODE_BINARY && smo_layout(MODE_BINARY, (int)D.d, ktab_len, D.maxnnz, 0, 0, 0).total > lim) {
-        // too many columns for the binary tables: use the generic path
+        // too many columns for the binary tables: use the generic path,
+        // with explicit 1.0 values when the matrix has none
         mode = mixed ? MODE_MIXED : MODE_FP64;
+        if (!D.values && D.nnz > 0) {
+            float *v = ar.alloc<float>(D.nnz);
+            k_fill_ones<<<grid1(D.nnz), 256, 0, st>>>(D.nnz, v);
+            CK(cudaGetLastError());
+            ++launches;
+            D.values = v;
+        }
         if (mode == MODE_FP64 && !D.norm) D.norm = ar.alloc<double>(n);
         if (mode == MODE_MIXED && !D.vmix) {
             D.vmix = ar.alloc<float>(D.nnz);
             D.normf = ar.alloc<float>(n);
         }
-        k_norms<<<grid1(n), 256, 0, st>>>(n, D.indptr, D.values, D.norm, D.vmix, D.normf);
+        k_norms<<<grid1(n), 256, 0, st>>>(n, D.indptr, D.values, D.norm, D.vmix, D.normf, D.info);
         CK(cudaGetLastError());
         ++launches;
     }
@@ -1061,6 +1132,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             c.out = f;
             c.yq = D.y;
             c.add_scalar = 0.0;
+            c.xd = D.xd;
             if (use_tc && mode == MODE_MIXED && tc_rbf_supported((int)D.d)) {
                 void *ws = ar.alloc<unsigned char>(tc_rbf_workspace_bytes(n, w_nsv, (int)D.d));
                 int tc_err = 0;
@@ -1120,6 +1192,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     A.ktab = ktab;
     A.ktab_len = ktab_len;
     A.maxnnz = D.maxnnz;
+    A.xd = D.xd;
     A.resident = resident;
     A.seg_rows_max = top.seg_rows_max;
     A.seg_nnz_max = top.seg_nnz_max;
@@ -1461,6 +1534,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
             c.out = f;
             c.yq = D.y;
             c.add_scalar = 0.0;
+            c.xd = D.xd;
             if (use_tc && mode == MODE_MIXED && nsv > 0 && tc_rbf_supported((int)D.d)) {
                 void *ws = ar.alloc<unsigned char>(tc_rbf_workspace_bytes(nw, nsv, (int)D.d));
                 int tc_err = 0;
@@ -1612,7 +1686,7 @@ void decision_eval(Arena &ar, DevCSR DX, const int32_t *list_sv, const double *c
                 D->vmix = ar.alloc<float>(D->nnz);
                 D->normf = ar.alloc<float>(D->n);
             }
-            k_norms<<<grid1(D->n), 256, 0, st>>>(D->n, D->indptr, D->values, D->norm, D->vmix, D->normf);
+            k_norms<<<grid1(D->n), 256, 0, st>>>(D->n, D->indptr, D->values, D->norm, D->vmix, D->normf, D->info);
             CK(cudaGetLastError());
             ++launches;
         }
@@ -1661,6 +1735,7 @@ void decision_eval(Arena &ar, DevCSR DX, const int32_t *list_sv, const double *c
     c.out = out_d;
     c.yq = nullptr;
     c.add_scalar = -b;
+    c.xd = xd_pair(DX, DZ);
     if (rbf && precision == SVM_MIXED_BF16 && mode == MODE_MIXED && nsv > 0 && tc_rbf_supported((int)DX.d)) {
         void *ws = ar.alloc<unsigned char>(tc_rbf_workspace_bytes(DZ.n, nsv, (int)DX.d));
         int tc_err = 0;
@@ -1941,7 +2016,7 @@ void batch_prepare(Arena &ar, const svm_csr *X, int precision, cudaStream_t st, 
             D.vmix = ar.alloc<float>(D.nnz);
             D.normf = ar.alloc<float>(D.n);
         }
-        k_norms<<<grid1(D.n), 256, 0, st>>>(D.n, D.indptr, D.values, D.norm, D.vmix, D.normf);
+        k_norms<<<grid1(D.n), 256, 0, st>>>(D.n, D.indptr, D.values, D.norm, D.vmix, D.normf, D.info);
         CK(cudaGetLastError());
         ++*launches;
     }
@@ -2026,6 +2101,7 @@ int train_batch_impl(const svm_csr *X, const svm_job *jobs, int32_t n_jobs, svm_
         hj[j].gamma = J.gamma;
         hj[j].tau = J.tau;
         hj[j].max_iter = J.max_iter > 0 ? J.max_iter : 100 * J.n_rows + 1000000;
+        hj[j].xd = D.xd;
         total += J.n_rows;
     }
     int32_t *rows = ar.alloc<int32_t>(total);
@@ -2333,7 +2409,7 @@ void srv_admit(Server &S, const std::shared_ptr<SrvJob> &J)
     CK(cudaMemcpyAsync(y, J->y.data(), J->n, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(S.info_d, 0, sizeof(IngestInfo), st));
     k_validate<<<grid1(J->n), 256, 0, st>>>(J->n, J->d, indptr, indices, values, y, S.info_d);
-    k_norms<<<grid1(J->n), 256, 0, st>>>(J->n, indptr, values, norm, vmix, normf);
+    k_norms<<<grid1(J->n), 256, 0, st>>>(J->n, indptr, values, norm, vmix, normf, S.info_d);
     k_iota<<<grid1(J->n), 256, 0, st>>>(J->n, rows);
     if (dense) k_dense_bf16<<<(unsigned)J->n, 128, 0, st>>>(J->n, (int)J->d, dpad, indptr, indices, vmix, dmat);
     CK(cudaGetLastError());
@@ -2382,6 +2458,7 @@ void srv_admit(Server &S, const std::shared_ptr<SrvJob> &J)
     D.gamma = J->gamma;
     D.tau = J->tau;
     D.max_iter = J->max_iter > 0 ? J->max_iter : 100 * J->n + 1000000;
+    D.xd = xd_of_info(h, values);
     __atomic_store_n(&S.done_h[slot], 0, __ATOMIC_RELAXED);
     const unsigned tail = __atomic_load_n(&S.ctl_h->tail, __ATOMIC_RELAXED);
     S.ring_h[tail % (unsigned)S.cfg.max_slots] = slot;
@@ -2593,7 +2670,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
         k_ktab<<<grid1(ktab_len), 256, 0, st>>>(P->gamma, ktab_len, ktab);
     } else {
         norm = W.take<double>(n);
-        k_norms<<<grid1(n), 256, 0, st>>>(n, X->indptr, X->values, norm, nullptr, nullptr);
+        k_norms<<<grid1(n), 256, 0, st>>>(n, X->indptr, X->values, norm, nullptr, nullptr, info);
     }
     CK(cudaGetLastError());
     ++launches;
@@ -2660,6 +2737,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     A.ktab = ktab;
     A.ktab_len = ktab_len;
     A.maxnnz = h.maxnnz;
+    A.xd = xd_of_info(h, X->values);
     A.resident = 0;
     A.C = P->C;
     A.gamma = P->gamma;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "svm_gb300.h"
+#include "fp64_math.cuh"
 
 namespace svmgb {
 
@@ -145,6 +146,9 @@ struct SmoArgs {
     // optional: (step, active rows) after each shrink event, 2 per event
     int64_t *atrace;
     int64_t atrace_len;
+    // FP64 mode: inner products exact in 128-bit integers, rounded once
+    // (xd.on), else FP64 sums in row order
+    XdFormat xd;
 };
 
 // ---- batched and served solves: one job = one two-class problem
@@ -169,6 +173,7 @@ struct BatchJobDev {
     int32_t pad;
     double C, gamma, tau;
     int64_t max_iter;
+    XdFormat xd;               // FP64 mode: exact inner products (xd.on)
 };
 
 struct BatchResultDev {
@@ -303,6 +308,7 @@ struct RbfContract {
     const int8_t *yq;          // subtract yq[row] when non-NULL
     double add_scalar;
     int32_t accumulate;        // 1: add to out[] instead of writing (CUDA-core path only)
+    XdFormat xd;               // FP64 mode: exact inner products (xd.on) for X and Z together
 };
 cudaError_t launch_rbf_contract(const RbfContract &c, cudaStream_t st);
 

@@ -1,11 +1,13 @@
 // Host check of the FP64 helpers of the CUDA path (fp64_math.cuh): the same
-// IEEE operations the device runs, compared with the conversion instruction
-// and with long double exp.
+// IEEE and integer operations the device runs, compared with the conversion
+// instruction, with long double exp, and (xd mode, driven by
+// test_fp64_math_cpu.py) with exact rational arithmetic.
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 
 #include "fp64_math.cuh"
 
@@ -13,8 +15,81 @@ static const double T[256] = {
 #include "exp2_table.inc"
 };
 
+// "xd" mode: cases on standard input, one per line. A line
+//   D n x_1 z_1 ... x_n z_n    (float bit patterns in hex)
+// prints the exact inner product rounded by xd_round (as the bits of a
+// double), computed three ways that must agree: in order, in reverse order,
+// and split over 4 lanes whose accumulators are then added; or "off" when
+// the format rejects the operands. A line
+//   R hi lo unit              (a 128-bit integer and a unit exponent)
+// prints xd_round(hi:lo, unit).
+static int xd_mode()
+{
+    char tag[4];
+    int bad = 0;
+    while (scanf("%3s", tag) == 1) {
+        if (tag[0] == 'R') {
+            unsigned long long hi, lo;
+            int unit;
+            if (scanf("%llx %llx %d", &hi, &lo, &unit) != 3) return 2;
+            svmgb::XdAcc a;
+            a.w0 = (uint32_t)lo;
+            a.w1 = (uint32_t)(lo >> 32);
+            a.w2 = (uint32_t)hi;
+            a.w3 = (uint32_t)(hi >> 32);
+            const double r = svmgb::xd_round(a, unit);
+            printf("%016llx\n", (unsigned long long)svmgb::double_to_bits(r));
+            continue;
+        }
+        int n;
+        if (scanf("%d", &n) != 1) return 2;
+        uint32_t *x = new uint32_t[n > 0 ? n : 1], *z = new uint32_t[n > 0 ? n : 1];
+        int bmax = 0, bmin = 255;
+        bool sub = false;
+        for (int i = 0; i < n; ++i) {
+            unsigned a, b;
+            if (scanf("%x %x", &a, &b) != 2) return 2;
+            x[i] = a;
+            z[i] = b;
+            for (uint32_t u : {x[i], z[i]}) {
+                const int e = (int)((u >> 23) & 0xff);
+                if (e == 0 && (u & 0x7fffffu)) sub = true;
+                if (e != 0) {
+                    bmax = e > bmax ? e : bmax;
+                    bmin = e < bmin ? e : bmin;
+                }
+            }
+        }
+        const svmgb::XdFormat f = svmgb::xd_format(bmax, bmin, n, sub);
+        if (!f.on) {
+            printf("off\n");
+        } else {
+            svmgb::XdAcc a = svmgb::xd_zero(), r = a, l[4] = {a, a, a, a};
+            for (int i = 0; i < n; ++i) {
+                const int k = svmgb::xd_exp(x[i], f.tmin) + svmgb::xd_exp(z[i], f.tmin) + f.bias;
+                if (k < 0 || k > 63) ++bad;
+                svmgb::xd_add(a, svmgb::xd_mant(x[i]), svmgb::xd_mant(z[i]), k);
+                svmgb::xd_add(l[i & 3], svmgb::xd_mant(x[i]), svmgb::xd_mant(z[i]), k);
+            }
+            for (int i = n - 1; i >= 0; --i)
+                svmgb::xd_add(r, svmgb::xd_mant(x[i]), svmgb::xd_mant(z[i]),
+                              svmgb::xd_exp(x[i], f.tmin) + svmgb::xd_exp(z[i], f.tmin) + f.bias);
+            svmgb::xd_add(l[0], l[2]);
+            svmgb::xd_add(l[1], l[3]);
+            svmgb::xd_add(l[0], l[1]);
+            if (memcmp(&a, &r, sizeof a) != 0 || memcmp(&a, &l[0], sizeof a) != 0) ++bad;
+            printf("%016llx\n", (unsigned long long)svmgb::double_to_bits(svmgb::xd_round(a, f.unit)));
+        }
+        delete[] x;
+        delete[] z;
+    }
+    printf("xd bad %d\n", bad);
+    return bad ? 1 : 0;
+}
+
 int main(int argc, char **argv)
 {
+    if (argc > 1 && strcmp(argv[1], "xd") == 0) return xd_mode();
     const long long stride = argc > 1 ? atoll(argv[1]) : 1;
     // 1. widen_f32 against the conversion, over float bit patterns
     long long checked = 0, bad = 0;
