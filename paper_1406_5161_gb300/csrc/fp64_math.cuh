@@ -6,25 +6,23 @@
 // K = exp(-gamma ||x - z||^2) of Section IV-E is the bulk of the FP64 work of
 // the SMO step (Algorithm 2's inner product and the exponential, twice per
 // active row) and of the gradient reconstruction (Algorithm 6). These helpers
-// keep the arithmetic FP64 while moving work off that pipe:
+// give FP64 results (or better) while moving that work onto the integer
+// pipes:
 //
-//   widen_f32(x)   the float x as a double, exactly (the same value as the
-//                  conversion instruction), by integer operations on the bit
-//                  pattern;
-//   exp_tang(x, T) exp(x) by the table-driven method of P. T. P. Tang,
-//                  "Table-driven implementation of the exponential function
-//                  in IEEE floating-point arithmetic", ACM TOMS 15(2), 1989:
-//                  x = (256 m + j) ln2/256 + r with |r| <= ln2/512, so
-//                  exp(x) = 2^m * 2^(j/256) * exp(r); 2^(j/256) from a
-//                  correctly rounded table T (exp2_table.inc, 256 doubles),
-//                  exp(r) - 1 by its Taylor polynomial of degree 5. Ten FP64
-//                  operations in the common case; within about one unit in
-//                  the last place of the exact value (checked on the host
-//                  against long double exp by tests/test_fp64_math_cpu.py).
+//   widen_f32(x)       the float x as a double, exactly (the same value as
+//                      the conversion instruction), by integer operations on
+//                      the bit pattern;
+//   exp_neg_fx(y, T)   exp(-y), y >= 0, in fixed-point integer arithmetic
+//                      after the table-driven method of P. T. P. Tang,
+//                      "Table-driven implementation of the exponential
+//                      function in IEEE floating-point arithmetic", ACM TOMS
+//                      15(2), 1989; within 0.53 units in the last place;
+//   xd_*               inner products of float rows, exact in 128-bit
+//                      integers and rounded once to the nearest double.
 //
-// Both are plain IEEE arithmetic (fma, add, multiply) plus integer
-// operations, written for host and device alike: the host build computes the
-// same bits, which is how the tests check them without a GPU.
+// They are written for host and device alike: the host build computes the
+// same bits, which is how tests/test_fp64_math_cpu.py checks them without a
+// GPU (against the conversion, long double exp and exact rationals).
 #ifndef SVM_FP64_MATH_CUH
 #define SVM_FP64_MATH_CUH
 
@@ -102,35 +100,93 @@ SVM_HD double widen_f32(float x)
     return bits_to_double(b | ((uint64_t)(u & 0x80000000u) << 32));
 }
 
-// 256 / ln 2, and ln 2 / 256 split into a double and its remainder (the
-// mathematical constants, rounded to nearest; computed with mpmath).
-constexpr double kTangInvL = 369.3299304675746;
-constexpr double kTangL1 = 2.7076061740622863e-03;
-constexpr double kTangL2 = 9.058776616587108e-20;
-constexpr double kTangShift = 6755399441055744.0;   // 1.5 * 2^52: rounds to an integer
-
-// exp(x) for -707 <= x <= 700 by Tang's method; outside that range (and for
-// NaN) the library exp. T: the 256 entries of exp2_table.inc.
-SVM_HD double exp_tang(double x, const double *T)
+SVM_HD uint64_t mul_hi64(uint64_t a, uint64_t b)
 {
-    if (!(x >= -707.0 && x <= 700.0)) return exp(x);
-    // n = round(x * 256 / ln 2): the shifted sum holds n in its low bits
-    const double s = fma(x, kTangInvL, kTangShift);
-    const int32_t n = (int32_t)(uint32_t)double_to_bits(s);
-    const double nd = s - kTangShift;
-    double r = fma(-nd, kTangL1, x);
-    r = fma(-nd, kTangL2, r);
-    // exp(r) - 1 = r + r^2 (1/2 + r (1/6 + r (1/24 + r / 120)))
-    double q = fma(1.0 / 120.0, r, 1.0 / 24.0);
-    q = fma(q, r, 1.0 / 6.0);
-    q = fma(q, r, 0.5);
-    const double p = fma(q, r * r, r);
-    const double t = T[n & 255];
-    const double y = fma(t, p, t);
-    // times 2^m, m = floor(n / 256), on the exponent field (y stays normal)
-    const int64_t m = (int64_t)(n >> 8);
-    return bits_to_double(double_to_bits(y) + ((uint64_t)m << 52));
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
 }
+
+SVM_HD int count_leading_zeros64(uint64_t v)
+{
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)v);
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+#include "expfx_table.inc"
+
+constexpr int kExpfxTabLen = 256;
+constexpr uint64_t kExpfxBits700 = 0x4085e00000000000ull;   // the bits of 700.0
+
+// exp(-y) for 0 <= y <= 700 in fixed-point integer arithmetic, after the
+// table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989):
+//   y = n ln2/256 + r, n = floor(y 256 / ln 2), 0 <= r < ln2/256,
+//   exp(-y) = 2^-(n div 256) * 2^-((n mod 256)/256) * exp(-r).
+// y is taken exactly into Q64 (64 fraction bits; below 2^-64 it counts as
+// 0); n from a 64-bit product with 256/ln 2, corrected by one from the
+// remainder r = y - n ln2/256, which is formed with ln2/256 to 128 bits;
+// exp(-r) by its Taylor polynomial of degree 5 in Q63 (Horner, every
+// intermediate positive); 2^-(j/256) from the table T (Q63, expfx_table.inc);
+// the product normalised and rounded once to a double. The fixed-point
+// errors stay below 2^-58 of the result, so the result is within about 0.52
+// units in the last place. y outside [0, 700] (and NaN) goes to the library
+// exp(-y). No FP64 arithmetic instruction is used on the integer path.
+SVM_HD double exp_neg_fx(double y, const uint64_t *T)
+{
+    typedef unsigned __int128 u128;
+    const uint64_t b = double_to_bits(y);
+    if (b > kExpfxBits700) return exp(-y);   // y < 0, y > 700 or NaN
+    // y = m 2^(be - 1075); in Q64: m << (be - 1011), at most 21 here
+    const int be = (int)(b >> 52);
+    const uint64_t m = (b & 0x000fffffffffffffull) | (be ? 0x0010000000000000ull : 0ull);
+    const int sh = be - 1011;
+    uint64_t hi = 0, lo = 0;
+    if (sh >= 0) {
+        lo = m << sh;
+        hi = sh ? m >> (64 - sh) : 0ull;
+    } else if (sh > -64) {
+        lo = m >> -sh;
+    }
+    // n: (y 2^53) (256/ln2 2^54) / 2^(64 + 43), then corrected from r
+    uint32_t n = (uint32_t)(mul_hi64((hi << 53) | (lo >> 11), kExpfxInvL54) >> 43);
+    const u128 yq = ((u128)hi << 64) | lo;
+    u128 nl = (u128)n * kExpfxLH + (((u128)n * kExpfxLL) >> 64);
+    if (yq < nl) {
+        n -= 1;
+        nl -= kExpfxLH;
+    } else if (yq - nl >= (u128)kExpfxLH) {
+        n += 1;
+        nl += kExpfxLH;
+    }
+    const uint64_t r = (uint64_t)(yq - nl);   // Q64, below 2^56
+    // exp(-r) = 1 - r (1 - r (1/2 - r (1/6 - r (1/24 - r / 120)))), Q63
+    uint64_t q = kExpfxC4 - mul_hi64(r, kExpfxC5);
+    q = kExpfxC3 - mul_hi64(r, q);
+    q = kExpfxC2 - mul_hi64(r, q);
+    q = 0x8000000000000000ull - mul_hi64(r, q);
+    const uint64_t e = 0x8000000000000000ull - mul_hi64(r, q);
+    // 2^-(j/256) exp(-r) in Q62: in (2^60.99, 2^62]
+    const uint64_t z = mul_hi64(T[n & 255u], e);
+    const int lz = count_leading_zeros64(z);   // 1 .. 3
+    const uint64_t zn = z << lz;              // leading one at bit 63
+    uint64_t mant = (zn >> 11) + ((zn >> 10) & 1u);
+    int ex = 1 - lz - (int)(n >> 8);          // z / 2^62 = (zn / 2^63) 2^(1 - lz)
+    if (mant >> 53) {
+        mant >>= 1;
+        ex += 1;
+    }
+    return bits_to_double(((uint64_t)(ex + 1023) << 52) | (mant & 0x000fffffffffffffull));
+}
+
+#if defined(__CUDACC__)
+// The table in device memory; kernels copy it into shared memory once.
+static __device__ const uint64_t kExpfxTab[kExpfxTabLen] = {SVM_EXPFX_TABLE};
+#endif
 
 // ---- exact inner products of float-valued rows (a fused dot product)
 //
@@ -256,15 +312,6 @@ SVM_HD void xd_add(XdAcc &a, int32_t mx, int32_t mz, int k)
     else xd_add4(a, t0, t1, t2, sx);
 }
 
-SVM_HD int count_leading_zeros64(uint64_t v)
-{
-#if defined(__CUDA_ARCH__)
-    return __clzll((long long)v);
-#else
-    return v ? __builtin_clzll(v) : 64;
-#endif
-}
-
 // The double nearest to a 2^unit (a read as a signed 128-bit integer), ties
 // to even. For the formats above the result is a normal number or zero.
 SVM_HD double xd_round(const XdAcc &acc, int unit)
@@ -289,15 +336,6 @@ SVM_HD double xd_round(const XdAcc &acc, int unit)
     const uint64_t bits = ((uint64_t)(e + 1023) << 52) | (m & 0x000fffffffffffffull);
     return bits_to_double(bits | (neg ? 0x8000000000000000ull : 0));
 }
-
-constexpr int kExp2TabLen = 256;
-
-#if defined(__CUDACC__)
-// The table in device memory; kernels copy it into shared memory once.
-static __device__ const double kExp2Tab[kExp2TabLen] = {
-#include "exp2_table.inc"
-};
-#endif
 
 }  // namespace svmgb
 

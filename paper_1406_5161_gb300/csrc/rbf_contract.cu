@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ double red[kCWarps][TQ];
-    __shared__ double exp2_s[MODE == MODE_FP64 ? kExp2TabLen : 1];   // FP64: table-driven exp
+    __shared__ uint64_t expfx_s[MODE == MODE_FP64 ? kExpfxTabLen : 1];   // FP64: fixed-point exp
     __shared__ double zn[TQ];
     __shared__ int zlen[TQ];
     __shared__ int zrow[TQ];
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
     }
     for (int w = tid; w < tile_words; w += kCThreads) Zt[w] = zero;
     if constexpr (MODE == MODE_FP64) {
-        for (int w = tid; w < kExp2TabLen; w += kCThreads) exp2_s[w] = kExp2Tab[w];
+        for (int w = tid; w < kExpfxTabLen; w += kCThreads) expfx_s[w] = kExpfxTab[w];
     }
     if (tid < TQ) {
         int r = -1;
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kCThreads) rbf_contract_kernel(RbfContract c)
 #pragma unroll
                 for (int q = 0; q < TQ; ++q) {
                     double d2 = zn[q] + xn - 2.0 * acc[q];
-                    part[q] = fma(coef, exp_tang(-c.gamma * (d2 < 0.0 ? 0.0 : d2), exp2_s), part[q]);
+                    part[q] = fma(coef, exp_neg_fx(c.gamma * (__double_as_longlong(d2) < 0 ? 0.0 : d2), expfx_s), part[q]);
                 }
             } else {
 #pragma unroll

@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
     using Acc = typename RowMath<MODE>::Acc;
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ BatchShared sh;
+    // FP64: 2^(-j/256) in Q63 for the fixed-point exp
+    __shared__ uint64_t expfx_s[MODE == MODE_FP64 ? kExpfxTabLen : 1];
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int csize = (int)cluster.num_blocks();
@@ -80,6 +82,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
     int *tcol = reinterpret_cast<int *>(dsm + L.tcol);
     double *ktab = reinterpret_cast<double *>(dsm + L.ktab);
     const double *rtab = ktab + B.ktab_len;
+    if constexpr (MODE == MODE_FP64) {
+        for (int c = tid; c < kExpfxTabLen; c += kThreads) expfx_s[c] = kExpfxTab[c];   // ordered by the cluster sync below
+    }
 
     for (;;) {
         // ---- next job from the work-list, broadcast to the cluster
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                             rinv = rtab[dist];
                         } else if constexpr (MODE == MODE_FP64) {
                             double d2 = up.nrm + low.nrm - 2.0 * s;
-                            kul = exp(-gamma * (dless(d2, 0.0) ? 0.0 : d2));
+                            kul = exp_neg_fx(gamma * dpos(d2), expfx_s);
                         } else {
                             float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
                             kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
@@ -326,8 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                             const double nrm_i = norm[g];
                             double d2u = up.nrm + nrm_i - 2.0 * su;
                             double d2l = low.nrm + nrm_i - 2.0 * sl;
-                            ku = exp(-gamma * (dless(d2u, 0.0) ? 0.0 : d2u));
-                            kl = exp(-gamma * (dless(d2l, 0.0) ? 0.0 : d2l));
+                            ku = exp_neg_fx(gamma * dpos(d2u), expfx_s);
+                            kl = exp_neg_fx(gamma * dpos(d2l), expfx_s);
                         } else {
                             const float nf = normf[g];
                             float d2u = (float)up.nrm + nf - 2.0f * su;

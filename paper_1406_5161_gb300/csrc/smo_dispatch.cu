@@ -32,7 +32,7 @@ int smo_threads() { return smo::kThreads; }
 size_t smo_cand_bytes() { return smo::kCandStride; }
 size_t smo_static_smem(int mode)
 {
-    return sizeof(smo::Shared) + sizeof(double) * (mode == MODE_FP64 ? kExp2TabLen : 1);
+    return sizeof(smo::Shared) + sizeof(uint64_t) * (mode == MODE_FP64 ? kExpfxTabLen : 1);
 }
 
 cudaError_t launch_smo_persistent(int mode, int lpr, const SmoArgs &a, size_t smem, cudaStream_t st,

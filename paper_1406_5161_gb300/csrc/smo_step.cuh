@@ -207,6 +207,8 @@ __device__ __forceinline__ unsigned long long dkey(double f)
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 __device__ __forceinline__ bool dless(double a, double b) { return dkey(a) < dkey(b); }
+// max(v, 0) of a squared distance, on the sign bit (no FP64 instruction)
+__device__ __forceinline__ double dpos(double v) { return __double_as_longlong(v) < 0 ? 0.0 : v; }
 __device__ __forceinline__ double neg_if(double v, bool neg)
 {
     return neg ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull) : v;
@@ -422,8 +424,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     constexpr int W4 = mode_words(MODE) / 4;   // uint4 words of a bit-mask row
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ Shared sh;
-    // FP64 rows: 2^(j/256) for the table-driven exp of the row pass
-    __shared__ double exp2_s[MODE == MODE_FP64 ? kExp2TabLen : 1];
+    // FP64 rows: 2^(-j/256) in Q63 for the fixed-point exp of the row pass
+    __shared__ uint64_t expfx_s[MODE == MODE_FP64 ? kExpfxTabLen : 1];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = A.G, cta = blockIdx.x;
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         for (int c = tid; c < 3 * A.ktab_len; c += kThreads) ktab[c] = A.ktab[c];
     }
     if constexpr (MODE == MODE_FP64) {
-        for (int c = tid; c < kExp2TabLen; c += kThreads) exp2_s[c] = kExp2Tab[c];
+        for (int c = tid; c < kExpfxTabLen; c += kThreads) expfx_s[c] = kExpfxTab[c];
     }
     const double *rtab = ktab + A.ktab_len;      // 1 / eta (0 when eta <= 1e-12)
     const double *etab = ktab + 2 * A.ktab_len;  // eta = 2 - 2 exp(-gamma k)
@@ -809,10 +811,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     } else {
                         if (A.kernel == KERNEL_RBF) {
                             if constexpr (MODE == MODE_FP64) {
-                                // the table-driven exp, as in the row pass
+                                // the fixed-point exp, as in the row pass
                                 double d2 = up.nrm + low.nrm - 2.0 * s;
                                 kul = kul_cached ? kul_c
-                                                 : exp_tang(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2), exp2_s);
+                                                 : exp_neg_fx(A.gamma * dpos(d2), expfx_s);
                             } else {
                                 float d2 = (float)up.nrm + (float)low.nrm - 2.0f * s;
                                 kul = (double)__expf(-gammaf * fmaxf(d2, 0.f));
@@ -1226,7 +1228,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                     ku = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, (double)su);
                                 } else {
                                     const double d2u = up.nrm + nrr - 2.0 * su;
-                                    ku = exp_tang(-A.gamma * (dless(d2u, 0.0) ? 0.0 : d2u), exp2_s);
+                                    ku = exp_neg_fx(A.gamma * dpos(d2u), expfx_s);
                                 }
                                 if (kc_step) kc_ru[gi] = ku;
                             }
@@ -1237,7 +1239,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                     kl = kernel_of_dot(A.kernel, A.gamma, A.coef0, A.degree, (double)sl);
                                 } else {
                                     const double d2l = low.nrm + nrr - 2.0 * sl;
-                                    kl = exp_tang(-A.gamma * (dless(d2l, 0.0) ? 0.0 : d2l), exp2_s);
+                                    kl = exp_neg_fx(A.gamma * dpos(d2l), expfx_s);
                                 }
                                 if (kc_step) kc_rl[gi] = kl;
                             }
@@ -1772,7 +1774,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 double kut;
                                 if constexpr (MODE == MODE_FP64) {
                                     const double d2 = up.nrm + NRM(r) - 2.0 * su;
-                                    kut = exp_tang(-A.gamma * (dless(d2, 0.0) ? 0.0 : d2), exp2_s);
+                                    kut = exp_neg_fx(A.gamma * dpos(d2), expfx_s);
                                 } else {
                                     const float d2 = (float)up.nrm + NRMF(r) - 2.0f * su;
                                     kut = widen_f32(__expf(-gammaf * fmaxf(d2, 0.f)));

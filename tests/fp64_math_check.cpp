@@ -11,9 +11,7 @@
 
 #include "fp64_math.cuh"
 
-static const double T[256] = {
-#include "exp2_table.inc"
-};
+static const uint64_t T[256] = {SVM_EXPFX_TABLE};
 
 // "xd" mode: cases on standard input, one per line. A line
 //   D n x_1 z_1 ... x_n z_n    (float bit patterns in hex)
@@ -115,36 +113,39 @@ int main(int argc, char **argv)
         ++checked;
     }
     printf("widen checked %lld bad %lld\n", checked, bad);
-    // 2. exp_tang against long double exp, in units of the last place of the
-    // correctly rounded value
+    // 2. exp_neg_fx against long double exp, in units of the last place of
+    // the correctly rounded value
     double worst = 0, wx = 0;
     long long n = 0;
-    const long long N = 20000000;
-    for (long long k = 0; k <= N; ++k) {
-        const double x = -707.0 + 707.0 * (double)k / (double)N;
-        const long double ref = expl((long double)x);
-        const double got = svmgb::exp_tang(x, T);
-        const double rd = (double)ref;
-        if (rd == 0.0 || !std::isnormal(rd)) continue;
+    auto check = [&](double y) {
+        const long double ref = expl(-(long double)y);
+        const double rd = (double)ref, got = svmgb::exp_neg_fx(y, T);
+        if (rd == 0.0 || !std::isnormal(rd)) return;
         const double ulp = nextafter(rd, INFINITY) - rd;
         const double err = (double)fabsl((long double)got - ref) / ulp;
-        if (err > worst) { worst = err; wx = x; }
+        if (err > worst) { worst = err; wx = y; }
         ++n;
+    };
+    const long long N = 20000000;
+    for (long long k = 0; k <= N; ++k) check(700.0 * (double)k / (double)N);
+    // small arguments on a log scale, and points around multiples of ln2/256
+    for (int e = -80; e <= 9; ++e)
+        for (int k = 0; k < 4096; ++k) check(ldexp(1.0 + k / 4096.0, e));
+    for (int j = 0; j <= 256 * 1009; j += 97) {
+        const double c = j * 0.0027076061740622863;
+        check(c);
+        check(nextafter(c, 0.0));
+        check(nextafter(c, INFINITY));
     }
-    // special points
-    const double sp[] = {0.0, -0.0, -1e-300, -1e-17, -0.5, -1.0, -0.00135, -0.0013538, -707.0, -706.99,
-                         -100.25, 1e-10, 1.0, 0.6931471805599453, 700.0};
-    for (double x : sp) {
-        const long double ref = expl((long double)x);
-        const double rd = (double)ref, got = svmgb::exp_tang(x, T);
-        const double ulp = nextafter(rd, INFINITY) - rd;
-        const double err = (double)fabsl((long double)got - ref) / ulp;
-        if (err > worst) { worst = err; wx = x; }
-    }
-    printf("exp points %lld max_ulp %.4f at %.17g exp0 %a\n", n, worst, wx, svmgb::exp_tang(0.0, T));
-    if (svmgb::exp_tang(0.0, T) != 1.0 || svmgb::exp_tang(-0.0, T) != 1.0) ++bad;
-    // NaN and arguments outside the table range go to the library exp
-    if (!std::isnan(svmgb::exp_tang(NAN, T)) || svmgb::exp_tang(-800.0, T) != exp(-800.0)) ++bad;
-    if (worst > 1.0 + 1e-9) ++bad;   // faithful: within one unit in the last place
+    const double sp[] = {0.0, 1e-300, 4.9e-324, 1e-17, 5.551115123125783e-17, 1.1102230246251565e-16, 0.5, 1.0,
+                         0.0027076061740622863, 0.0013538, 100.25, 699.9999999999999, 700.0};
+    for (double y : sp) check(y);
+    printf("exp points %lld max_ulp %.4f at %.17g\n", n, worst, wx);
+    if (svmgb::exp_neg_fx(0.0, T) != 1.0 || svmgb::exp_neg_fx(1e-300, T) != 1.0) ++bad;
+    // outside [0, 700] and NaN: the library exp
+    if (!std::isnan(svmgb::exp_neg_fx(NAN, T)) || svmgb::exp_neg_fx(800.0, T) != exp(-800.0) ||
+        svmgb::exp_neg_fx(-0.5, T) != exp(0.5) || svmgb::exp_neg_fx(-0.0, T) != 1.0)
+        ++bad;
+    if (worst > 0.53) ++bad;   // the fixed-point errors stay far below half a unit
     return bad ? 1 : 0;
 }

@@ -1,15 +1,18 @@
 """The FP64 helpers of the CUDA path's FP64 mode (csrc/fp64_math.cuh), built
-for the host with the same IEEE operations the device runs (fma, add,
-multiply and integer bit operations; no contraction):
+for the host with the same IEEE and integer operations the device runs (no
+contraction):
 
 * widen_f32 returns the conversion instruction's double for every float bit
   pattern below 2^24 (zeros, all subnormals, the smallest normals), every
   subnormal with the sign set, and a stride-7 sweep of all other finite
   patterns;
-* exp_tang (Tang's table-driven exponential with a correctly rounded
-  2^(j/256) table) is within one unit in the last place of long double exp
-  over 2e7 points of [-707, 0], equals 1 at 0 and hands NaN and arguments
-  outside its range to the library exp."""
+* exp_neg_fx (exp(-y) in fixed-point integer arithmetic after Tang's
+  table-driven method) is within 0.53 units in the last place of long
+  double exp over 2e7 points of [0, 700], small arguments down to 2^-80 and
+  the neighbours of multiples of ln2/256; it is exactly 1 at 0 and hands
+  negative arguments, arguments above 700 and NaN to the library exp;
+* the exact inner products (xd_*) equal the exact rational sums rounded to
+  nearest (below)."""
 import os
 import struct
 import subprocess
