@@ -179,7 +179,7 @@ def job_totals(dist, seconds: float, units: float, device) -> tuple[float, float
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for name in ("smo_step.cuh", "svm_internal.cuh", "fp64_math.cuh"):
+    for name in ("smo_step.cuh", "svm_internal.cuh", "fp64_math.cuh", "expfx_table.inc"):
         with open(os.path.join(ROOT, "paper_1406_5161_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -190,6 +190,21 @@ def measured_traffic(workload: str, precision: str):
     summary of this workload, or None when there is none or the kernel source
     changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"smo_step_{workload}_{precision}_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return rec
+
+
+def measured_issue(workload: str, precision: str):
+    """Warp-instructions per row visit of the fused step on this workload's
+    full-set level, from the committed ncu summary, or None when there is
+    none or the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"smo_step_{workload}_{precision}_issue.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
@@ -447,19 +462,22 @@ def run_gb300(args, rank, world, local):
     if trec:
         roofline["traffic_launch"] = trec.get("launch")
         roofline["traffic_alg_bytes"] = trec.get("alg_bytes_per_launch")
-    fp64_pipe = None
-    if args.precision == "fp64" and not stats["binary_input"]:
-        # the FP64 row pass is bound by the FP64 pipe, not by memory: per
-        # active row, 2 nnz FMAs (the two inner products), 2 x 3 for the
-        # distances and scaling, 2 x 10 for the exponentials (the table-driven
-        # method) and 2 FMAs for Eq. (fup)
-        instr_row = 2 * p.X.nnz / p.X.n + 28
-        ach = row_visits * instr_row / (ms_smo / 1e3) / 1e9
-        fp64_pipe = {"bound": "alu", "achieved": ach, "peak": 625.0, "unit": "G FP64 instr/s",
-                     "frac": ach / 625.0, "instr_per_row_visit": instr_row,
-                     "peak_source": "nominal FP64 rate 1.25 TFLOP/s (FMA = 2 flops) = 625 G FP64 "
-                                    "instructions/s (152 SMs x 2 per clock x 2.07 GHz); a DFMA "
-                                    "microbenchmark measures 1.59 per clock per SM (500 G/s)"}
+    issue = None
+    irec = measured_issue(args.workload, args.precision)
+    if irec:
+        # the FP64 row pass runs its inner products and exponentials on the
+        # integer pipes (exact 128-bit sums, fixed-point exp), which leaves the
+        # fused step bound by instruction issue and latency, not by the FP64
+        # pipe or memory: warp-instructions executed (ncu, per row visit of
+        # the full-set level) over the fused-step time, against one
+        # instruction per clock per scheduler
+        wpr = float(irec["warp_instr_per_row_visit"])
+        ach = row_visits * wpr / (ms_smo / 1e3)
+        peak_issue = 152 * 4 * 2.07e9
+        issue = {"bound": "issue", "achieved": ach, "peak": peak_issue, "unit": "warp-instr/s",
+                 "frac": ach / peak_issue, "warp_instr_per_row_visit": wpr,
+                 "peak_source": "152 SMs x 4 schedulers x 1 warp-instruction per clock x 2.07 GHz",
+                 "source": irec.get("source")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -474,8 +492,8 @@ def run_gb300(args, rank, world, local):
             "objective": stats["objective"],
             "gpu_launches": int(launches),
             "clocks": clk, "roofline": roofline, "e2e": e2e}
-    if fp64_pipe:
-        line["roofline_fp64_pipe"] = fp64_pipe
+    if issue:
+        line["roofline_issue"] = issue
     if args.max_iter:
         line["config"]["max_iter"] = args.max_iter
     if args.cache_mb:

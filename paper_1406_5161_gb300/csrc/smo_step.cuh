@@ -753,10 +753,11 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     for (int w = 0; w < 4 * W4; ++w) s += __popc(up.m[w] ^ low.m[w]);
                 } else if constexpr (MODE == MODE_FP64) {
                     // K(up, low) with the row pass's own arithmetic for the
-                    // row of x_low against the x_up target (its entries in
-                    // order, split over LPR lanes as the row pass splits a
-                    // row), so that it equals, bit for bit, the entry the
-                    // kernel-row cache holds for it; when x_up's row is in
+                    // row of x_low against the x_up target (exact inner
+                    // products; else its entries in order, split over LPR
+                    // lanes as the row pass splits a row), so that it equals,
+                    // bit for bit, the entry the kernel-row cache holds for
+                    // it and the value the row pass computes; when x_up's row is in
                     // the cache that entry is read instead (written by the
                     // owner of x_low's segment in an earlier step of this
                     // launch, visible here through the exchanges since)
@@ -764,16 +765,15 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         kul_c = __ldcg(static_cast<const double *>(A.kc) + (size_t)sh.kc_su * A.kc_ld + low.i);
                         kul_cached = true;
                     } else if (xd) {
-                        // exact: the same value whatever the order or split
+                        // exact: the same value whatever the order or split,
+                        // so all 32 lanes share the entries
                         const int4 *T4 = reinterpret_cast<const int4 *>(T);
                         XdAcc a = xd_zero();
-                        if (lane < LPR) {
-                            for (int k = lane; k < low.len; k += LPR) {
-                                const int4 t = T4[tcl[k]];
-                                xd_add(a, t.z, t.x, t.w + t.y + xd_bias);
-                            }
+                        for (int k = lane; k < low.len; k += 32) {
+                            const int4 t = T4[tcl[k]];
+                            xd_add(a, t.z, t.x, t.w + t.y + xd_bias);
                         }
-                        xd_lane_sum<LPR>(a);
+                        xd_lane_sum<32>(a);
                         s = xd_round(a, xd_unit);
                     } else {
                         if (lane < LPR) {
