@@ -109,6 +109,15 @@ SVM_HD uint64_t mul_hi64(uint64_t a, uint64_t b)
 #endif
 }
 
+SVM_HD uint32_t mul_hi32(uint32_t a, uint32_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
 SVM_HD int count_leading_zeros64(uint64_t v)
 {
 #if defined(__CUDA_ARCH__)
@@ -127,46 +136,53 @@ constexpr uint64_t kExpfxBits700 = 0x4085e00000000000ull;   // the bits of 700.0
 // table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989):
 //   y = n ln2/256 + r, n = floor(y 256 / ln 2), 0 <= r < ln2/256,
 //   exp(-y) = 2^-(n div 256) * 2^-((n mod 256)/256) * exp(-r).
-// y is taken exactly into Q64 (64 fraction bits; below 2^-64 it counts as
-// 0); n from a 64-bit product with 256/ln 2, corrected by one from the
-// remainder r = y - n ln2/256, which is formed with ln2/256 to 128 bits;
-// exp(-r) by its Taylor polynomial of degree 5 in Q63 (Horner, every
-// intermediate positive); 2^-(j/256) from the table T (Q63, expfx_table.inc);
-// the product normalised and rounded once to a double. The fixed-point
-// errors stay below 2^-58 of the result, so the result is within about 0.52
-// units in the last place. y outside [0, 700] (and NaN) goes to the library
-// exp(-y). No FP64 arithmetic instruction is used on the integer path.
+// n comes from a 64-bit product of y 2^53 with 256/ln 2 (possibly one too
+// small or too large), r from the fraction bits of y 2^64 minus those of
+// n ln2/256 (ln2/256 known to 128 bits): the integer parts cancel, so the
+// low 64 bits of each are enough, and the sign or size of the difference
+// corrects n by one. exp(-r) by its Taylor polynomial of degree 5 in Q63
+// (Horner, every intermediate positive; the innermost term, which needs
+// only 2^-28, in 32 bits); 2^-(j/256) from the table T (Q63,
+// expfx_table.inc); the product normalised and rounded once to a double.
+// The fixed-point errors stay below 2^-58 of the result, so the result is
+// within about 0.52 units in the last place. y outside [0, 700] (and NaN)
+// goes to the library exp(-y). No FP64 arithmetic instruction is used on
+// the integer path.
 SVM_HD double exp_neg_fx(double y, const uint64_t *T)
 {
-    typedef unsigned __int128 u128;
     const uint64_t b = double_to_bits(y);
     if (b > kExpfxBits700) return exp(-y);   // y < 0, y > 700 or NaN
-    // y = m 2^(be - 1075); in Q64: m << (be - 1011), at most 21 here
+    // y = m 2^(be - 1075), so y 2^64 = m << sh, sh = be - 1011 <= 21
     const int be = (int)(b >> 52);
     const uint64_t m = (b & 0x000fffffffffffffull) | (be ? 0x0010000000000000ull : 0ull);
     const int sh = be - 1011;
-    uint64_t hi = 0, lo = 0;
-    if (sh >= 0) {
+    uint64_t y53, lo;   // y 2^53 (truncated) and the low 64 bits of y 2^64
+    if (sh >= 11) {
+        y53 = m << (sh - 11);
         lo = m << sh;
-        hi = sh ? m >> (64 - sh) : 0ull;
-    } else if (sh > -64) {
-        lo = m >> -sh;
+    } else if (sh >= 0) {
+        y53 = m >> (11 - sh);
+        lo = m << sh;
+    } else {
+        y53 = 0;   // y < 2^-11: n = 0
+        lo = sh > -64 ? m >> -sh : 0ull;
     }
-    // n: (y 2^53) (256/ln2 2^54) / 2^(64 + 43), then corrected from r
-    uint32_t n = (uint32_t)(mul_hi64((hi << 53) | (lo >> 11), kExpfxInvL54) >> 43);
-    const u128 yq = ((u128)hi << 64) | lo;
-    u128 nl = (u128)n * kExpfxLH + (((u128)n * kExpfxLL) >> 64);
-    if (yq < nl) {
+    uint32_t n = (uint32_t)(mul_hi64(y53, kExpfxInvL54) >> 43);
+    // the low 64 bits of n ln2/256 in Q64: n LH + floor(n LL / 2^64)
+    const uint64_t nll = ((uint64_t)n * (uint32_t)(kExpfxLL >> 32) +
+                          (((uint64_t)n * (uint32_t)kExpfxLL) >> 32)) >> 32;
+    uint64_t r = lo - ((uint64_t)n * kExpfxLH + nll);
+    if ((int64_t)r < 0) {
         n -= 1;
-        nl -= kExpfxLH;
-    } else if (yq - nl >= (u128)kExpfxLH) {
+        r += kExpfxLH;
+    } else if (r >= kExpfxLH) {
         n += 1;
-        nl += kExpfxLH;
+        r -= kExpfxLH;
     }
-    const uint64_t r = (uint64_t)(yq - nl);   // Q64, below 2^56
     // exp(-r) = 1 - r (1 - r (1/2 - r (1/6 - r (1/24 - r / 120)))), Q63
-    uint64_t q = kExpfxC4 - mul_hi64(r, kExpfxC5);
-    q = kExpfxC3 - mul_hi64(r, q);
+    const uint32_t r32 = (uint32_t)(r >> 32);   // r in Q32
+    const uint32_t q4 = (uint32_t)(kExpfxC4 >> 31) - mul_hi32(r32, (uint32_t)(kExpfxC5 >> 31));
+    uint64_t q = kExpfxC3 - mul_hi64(r, (uint64_t)q4 << 31);
     q = kExpfxC2 - mul_hi64(r, q);
     q = 0x8000000000000000ull - mul_hi64(r, q);
     const uint64_t e = 0x8000000000000000ull - mul_hi64(r, q);
@@ -313,28 +329,45 @@ SVM_HD void xd_add(XdAcc &a, int32_t mx, int32_t mz, int k)
 }
 
 // The double nearest to a 2^unit (a read as a signed 128-bit integer), ties
-// to even. For the formats above the result is a normal number or zero.
+// to even. For the formats above the result is a normal number or zero. The
+// magnitude is (a xor s) - s, s the sign mask; the limb holding the leading
+// one and the two below it give a 96-bit window whose top 53 bits are the
+// significand, the next bit the rounding bit, and the rest (with the limb
+// below the window) the sticky bit.
 SVM_HD double xd_round(const XdAcc &acc, int unit)
 {
-    typedef unsigned __int128 u128;
-    const u128 a = ((u128)acc.w3 << 96) | ((u128)acc.w2 << 64) | ((u128)acc.w1 << 32) | (u128)acc.w0;
-    if (a == 0) return 0.0;
-    const bool neg = (acc.w3 >> 31) != 0;
-    u128 mag = neg ? (u128)0 - a : a;
-    const uint64_t h0 = (uint64_t)(mag >> 64);
-    const int lz = h0 ? count_leading_zeros64(h0) : 64 + count_leading_zeros64((uint64_t)mag);
-    mag <<= lz;   // leading one at bit 127
-    const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
-    uint64_t m = hi >> 11;   // 53 bits
-    const bool half = (hi >> 10) & 1u;
-    const bool sticky = (hi & 0x3ffu) != 0 || lo != 0;
-    int e = 127 - lz + unit;   // |a| 2^unit = 1.f 2^e
-    if (half && (sticky || (m & 1u))) {
-        m += 1;
-        if (m >> 53) { m >>= 1; e += 1; }
+    const uint32_t s = (uint32_t)((int32_t)acc.w3 >> 31);
+    XdAcc g;
+    g.w0 = acc.w0 ^ s;
+    g.w1 = acc.w1 ^ s;
+    g.w2 = acc.w2 ^ s;
+    g.w3 = acc.w3 ^ s;
+    xd_add4(g, s & 1u, 0u, 0u, 0u);
+    uint32_t a, b, c, rest;
+    int top;
+    if (g.w3) {
+        a = g.w3; b = g.w2; c = g.w1; rest = g.w0; top = 3;
+    } else if (g.w2) {
+        a = g.w2; b = g.w1; c = g.w0; rest = 0u; top = 2;
+    } else if (g.w1) {
+        a = g.w1; b = g.w0; c = 0u; rest = 0u; top = 1;
+    } else if (g.w0) {
+        a = g.w0; b = 0u; c = 0u; rest = 0u; top = 0;
+    } else {
+        return 0.0;
     }
-    const uint64_t bits = ((uint64_t)(e + 1023) << 52) | (m & 0x000fffffffffffffull);
-    return bits_to_double(bits | (neg ? 0x8000000000000000ull : 0));
+    const int lz = count_leading_zeros32(a);
+    const uint32_t h = xd_funnel(b, a, lz), mid = xd_funnel(c, b, lz), low = c << lz;
+    uint64_t mant = ((uint64_t)h << 21) | (mid >> 11);   // leading one at bit 52
+    const bool half = (mid >> 10) & 1u;
+    const bool sticky = ((mid & 0x3ffu) | low | rest) != 0u;
+    int e = 32 * top + 31 - lz + unit;   // |a| 2^unit = 1.f 2^e
+    if (half && (sticky || (mant & 1u))) {
+        mant += 1;
+        if (mant >> 53) { mant >>= 1; e += 1; }
+    }
+    const uint64_t bits = ((uint64_t)(e + 1023) << 52) | (mant & 0x000fffffffffffffull);
+    return bits_to_double(bits | ((uint64_t)(s & 1u) << 63));
 }
 
 }  // namespace svmgb

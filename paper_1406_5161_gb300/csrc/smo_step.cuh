@@ -1104,21 +1104,23 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 if (xd && !first && !skip_sums) {
                     if constexpr (MODE == MODE_FP64) {
                         // exact inner products in integer arithmetic, each
-                        // lane loading its next 8 entries at once
+                        // lane loading its next XB entries at once (4: fewer
+                        // live registers than 8, measured 3% faster)
                         const int4 *T4 = reinterpret_cast<const int4 *>(T);
                         XdAcc au = xd_zero(), al = xd_zero();
-                        for (int64_t pb = p0 + gl; pb < p1; pb += 8 * LPR) {
-                            int cb[8];
-                            uint32_t ub[8];
+                        constexpr int XB = 4;
+                        for (int64_t pb = p0 + gl; pb < p1; pb += XB * LPR) {
+                            int cb[XB];
+                            uint32_t ub[XB];
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
+                            for (int j = 0; j < XB; ++j) {
                                 const int64_t p = pb + (int64_t)j * LPR;
                                 const bool in = p < p1;
                                 cb[j] = in ? COL(p) : 0;
                                 ub[j] = in ? __float_as_uint(VAL(p)) : 0u;
                             }
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
+                            for (int j = 0; j < XB; ++j) {
                                 if (pb + (int64_t)j * LPR >= p1) break;
                                 const int32_t m = xd_mant(ub[j]);
                                 const int e = xd_exp(ub[j], xd_tmin) + xd_bias;

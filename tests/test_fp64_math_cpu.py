@@ -125,6 +125,15 @@ def test_exact_inner_products_on_the_host(tmp_path):
             hi, lo = v >> 64, v & ((1 << 64) - 1)
         rounds.append((hi, lo, int(rng.integers(-400, 200))))
     rounds += [(0, 1, 0), (0, (1 << 53) + 1, 0), (0, (1 << 54) + 2, -3), (1, 0, -64), ((1 << 64) - 1, (1 << 64) - 1, 0)]
+    # ties and near ties at leading-bit positions in every limb: 2^P + 2^(P-53)
+    # (a tie, even significand), the same with an odd significand, and one
+    # unit above and below the tie (the deciding bit far below the window)
+    for P in (54, 60, 63, 64, 70, 95, 96, 100, 117, 126):
+        for v in (2 ** P + 2 ** (P - 53), 2 ** P + 2 ** (P - 52) + 2 ** (P - 53),
+                  2 ** P + 2 ** (P - 53) + 1, 2 ** P + 2 ** (P - 53) - 1):
+            for sgn in (1, -1):
+                w = (sgn * v) & ((1 << 128) - 1)
+                rounds.append((w >> 64, w & ((1 << 64) - 1), -7))
     lines = []
     for x, z in cases + off_cases:
         lines.append("D %d %s" % (len(x), " ".join("%08x %08x" % (_bits(a), _bits(b)) for a, b in zip(x, z))))
