@@ -503,9 +503,13 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             if (tid == 0) rp_s[nseg] = (int)(A.indptr[lo + nseg] - base);
             const int64_t segnnz = A.indptr[lo + nseg] - base;
             for (int64_t p = tid; p < segnnz; p += kThreads) {
-                col_s[p] = (unsigned short)A.indices[base + p];
-                if constexpr (MODE == MODE_FP64) val_s[p] = A.values[base + p];
-                if constexpr (MODE == MODE_MIXED) val_s[p] = A.vmix[base + p];
+                if constexpr (MODE == MODE_MIXED) {
+                    // one word per entry: the column and the BF16 value
+                    reinterpret_cast<uint32_t *>(val_s)[p] = A.ew[base + p];
+                } else {
+                    col_s[p] = (unsigned short)A.indices[base + p];
+                    if constexpr (MODE == MODE_FP64) val_s[p] = A.values[base + p];
+                }
             }
         }
         for (int k = tid; k < cnt; k += kThreads) act_s[k] = A.act[lo + k];
@@ -596,12 +600,17 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         if constexpr (RES) { p0 = rp_s[r]; p1 = rp_s[r + 1]; }
         else { p0 = A.indptr[lo + r]; p1 = A.indptr[lo + r + 1]; }
     };
+    // mixed rows on chip: one word per entry, the column in the low half and
+    // the BF16 value's bits in the high half
     auto COL = [&](int64_t p) -> int {
-        if constexpr (RES) return (int)col_s[p];
+        if constexpr (RES && MODE == MODE_MIXED) return (int)(reinterpret_cast<const uint32_t *>(val_s)[p] & 0xffffu);
+        else if constexpr (RES) return (int)col_s[p];
         else return A.indices[p];
     };
     auto VAL = [&](int64_t p) -> float {
-        if constexpr (RES) return val_s[p];
+        if constexpr (RES && MODE == MODE_MIXED)
+            return __uint_as_float(reinterpret_cast<const uint32_t *>(val_s)[p] & 0xffff0000u);
+        else if constexpr (RES) return val_s[p];
         else if constexpr (MODE == MODE_FP64) return A.values[p];
         else return A.vmix[p];
     };
@@ -1149,7 +1158,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     }
                 } else if (!RES && !first && !skip_sums) {
                     // streamed rows: each lane loads its next 8 entries at once
-                    // (one memory round trip per 8 entries, not one per entry)
+                    // (one memory round trip per 8 entries, not one per entry;
+                    // mixed rows one word per entry when packed)
                     for (int64_t pb = p0 + gl; pb < p1; pb += 8 * LPR) {
                         int cb[8];
                         float vb[8];
@@ -1157,8 +1167,20 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         for (int j = 0; j < 8; ++j) {
                             const int64_t p = pb + (int64_t)j * LPR;
                             const bool in = p < p1;
-                            cb[j] = in ? COL(p) : 0;
-                            if constexpr (MODE != MODE_BINARY) vb[j] = in ? VAL(p) : 0.f;
+                            if constexpr (MODE == MODE_MIXED) {
+                                if (A.ew) {
+                                    // mixed rows packed one word per entry (d < 2^16)
+                                    const uint32_t w = in ? A.ew[p] : 0u;
+                                    cb[j] = (int)(w & 0xffffu);
+                                    vb[j] = __uint_as_float(w & 0xffff0000u);
+                                } else {
+                                    cb[j] = in ? COL(p) : 0;
+                                    vb[j] = in ? VAL(p) : 0.f;
+                                }
+                            } else {
+                                cb[j] = in ? COL(p) : 0;
+                                if constexpr (MODE != MODE_BINARY) vb[j] = in ? VAL(p) : 0.f;
+                            }
                         }
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {

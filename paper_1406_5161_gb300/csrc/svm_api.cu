@@ -161,6 +161,15 @@ __global__ void k_validate(int64_t n, int64_t d, const int64_t *indptr, const in
     }
 }
 
+// Mixed rows for the row pass: each stored entry as one word, the column
+// (< 2^16) in bits 0-15 and the BF16-rounded value's bits in 16-31 (its
+// FP32 copy has zero low half, so nothing is lost).
+__global__ void k_pack_ew(int64_t nnz, const int32_t *indices, const float *vmix, uint32_t *ew)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) ew[p] = (__float_as_uint(vmix[p]) & 0xffff0000u) | (uint32_t)indices[p];
+}
+
 // The exact-inner-product format of one matrix from its validation record
 // (values NULL: every value is 1.0); host and device compute the same.
 __host__ __device__ XdFormat xd_of_info(const IngestInfo &h, const float *values)
@@ -391,6 +400,8 @@ struct SubRowsArgs {
     int8_t *sub_y;
     uint8_t *sub_status;
     uint32_t *sub_bits;
+    const uint32_t *ew;          // mixed rows one word per entry, or NULL
+    uint32_t *sub_ew;
     int32_t *sub_gmap;
     const __nv_bfloat16 *dmat;   // dense BF16 rows (tensor-core row tiles), or NULL
     __nv_bfloat16 *sub_dmat;
@@ -408,6 +419,7 @@ __global__ void k_sub_rows(SubRowsArgs S)
             S.sub_indices[q0 + k] = S.indices[p0 + k];
             if (S.sub_values) S.sub_values[q0 + k] = S.values[p0 + k];
             if (S.sub_vmix) S.sub_vmix[q0 + k] = S.vmix[p0 + k];
+            if (S.sub_ew) S.sub_ew[q0 + k] = S.ew[p0 + k];
         }
         for (int k = lane; k < S.bit_words; k += 32) S.sub_bits[j * S.bit_words + k] = S.bits[i * S.bit_words + k];
         if (S.dmat) {
@@ -1246,13 +1258,24 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         Shape shape;
         const __nv_bfloat16 *dmat;   // dense BF16 rows for the row tiles, or NULL
         KcPlan kc;                   // kernel-row cache plan of this level
+        const uint32_t *ew;          // mixed rows one word per entry (d < 2^16), or NULL
     };
     const bool relayout_on = (P->flags & SVM_FLAG_NO_RELAYOUT) == 0;
     bool relayout_ok = relayout_on;
     const int bit_words = mode_bits(kmode) ? mode_words(kmode) : 0;
+    // mixed rows: one word per stored entry (column and BF16 value), which
+    // the row pass loads once instead of the column and the value; required
+    // for rows held on chip, which need d < 2^16 anyway
+    uint32_t *ew = nullptr;
+    if (kmode == MODE_MIXED && D.d <= 65535 && D.vmix && D.nnz > 0) {
+        ew = ar.alloc<uint32_t>(D.nnz);
+        k_pack_ew<<<grid1(D.nnz), 256, 0, st>>>(D.nnz, D.indices, D.vmix, ew);
+        CK(cudaGetLastError());
+        ++launches;
+    }
     std::vector<Level> lv;
     lv.push_back(Level{n, D.nnz, D.indptr, D.indices, vals_fp32, D.vmix, D.normf, D.norm, D.y, bits,
-                       alpha, f, status, act, seg_cnt, nullptr, nullptr, top, dmat, top_kc});
+                       alpha, f, status, act, seg_cnt, nullptr, nullptr, top, dmat, top_kc, ew});
     int64_t relayouts = 0;
     auto launch_level = [&](const Level &L, int select_only, double thr, int64_t hh, int64_t limit) {
         A.n = L.n;
@@ -1261,6 +1284,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         A.indices = L.indices;
         A.values = L.values;
         A.vmix = L.vmix;
+        A.ew = L.ew;
         A.y = L.y;
         A.norm = L.norm;
         A.normf = L.normf;
@@ -1349,6 +1373,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         // only the values the row pass reads: FP32 (FP64 mode) or BF16-rounded (mixed)
         S.sub_values = (Pa.values && kmode == MODE_FP64) ? ar.alloc<float>(nnz_m) : nullptr;
         S.sub_vmix = (Pa.vmix && kmode == MODE_MIXED) ? ar.alloc<float>(nnz_m) : nullptr;
+        S.ew = Pa.ew;
+        S.sub_ew = Pa.ew ? ar.alloc<uint32_t>(nnz_m) : nullptr;
         S.sub_normf = Pa.normf ? ar.alloc<float>(m) : nullptr;
         S.sub_norm = Pa.norm ? ar.alloc<double>(m) : nullptr;
         S.sub_alpha = ar.alloc<double>(m);
@@ -1382,6 +1408,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         C.idx = idx;
         C.gmap = S.sub_gmap;
         C.dmat = S.sub_dmat;
+        C.ew = S.sub_ew;
         C.kc = kc_cap ? plan_kc(m, kc_cap) : KcPlan{};
         C.shape = pick_shape(m, nnz_m, sub_indptr, C.kc.slots > 0 ? smo_kdir_bytes(m, C.kc.slots, C.kc.direct) : 0);
         k_reset_active<<<C.shape.G, 256, 0, st>>>(m, C.shape.G, C.act, C.seg_cnt);

@@ -91,6 +91,9 @@ struct SmoArgs {
     const int32_t *indices;
     const float *values;       // FP64 mode
     const float *vmix;         // mixed mode: values rounded to BF16, held as FP32
+    const uint32_t *ew;        // mixed mode, d < 2^16: each entry as one word, column in
+                               // bits 0-15 and the BF16 value's bits in 16-31 (or NULL;
+                               // required for rows held on chip)
     const int8_t *y;
     const double *norm;        // ||x_i||^2 (FP64 / binary: exact)
     const uint32_t *bits;      // bit-mask modes: row i = words [i * W, (i + 1) * W)
@@ -232,7 +235,9 @@ __host__ __device__ inline SmoLayout smo_layout(int mode, int d, int ktab_len, i
     L.rowptr = o; o = smo_align16(o + (size_t)(resident && !bits ? rows + 1 : 0) * 4);
     L.act = o;    o = smo_align16(o + (size_t)rows * 4);
     L.st = o;     o = smo_align16(o + (size_t)rows);
-    L.col = o;    o = smo_align16(o + (size_t)nnz * 2);
+    // on-chip entries: FP64 a 16-bit column and an FP32 value; mixed one word
+    // (column and BF16 value); binary the column
+    L.col = o;    o = smo_align16(o + (size_t)nnz * (mode == 2 ? 0 : 2));
     L.val = o;    o = smo_align16(o + (size_t)nnz * (mode == 0 ? 0 : 4));
     L.bits = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 * mode_words(mode) : 0));
     L.dist = o;   o = smo_align16(o + (bits ? (size_t)rows * 4 : 0));   // two 16-bit distances per row
