@@ -265,6 +265,15 @@ SVM_HD int32_t xd_mant(uint32_t u)
     return (u >> 31) ? -m : m;
 }
 
+// A value's (m, b - t) in one word, for rows read many times: m (signed, 25
+// bits) in bits 5-31, b - t (0 .. 31 within the window) in bits 0-4.
+SVM_HD uint32_t xd_word(uint32_t u, int tmin)
+{
+    return ((uint32_t)xd_mant(u) << 5) | (uint32_t)(xd_exp(u, tmin) - tmin);
+}
+SVM_HD int32_t xd_word_m(uint32_t w) { return (int32_t)w >> 5; }
+SVM_HD int xd_word_e(uint32_t w) { return (int)(w & 31u); }
+
 // 128-bit two's-complement accumulator, least significant limb first
 struct XdAcc {
     uint32_t w0, w1, w2, w3;

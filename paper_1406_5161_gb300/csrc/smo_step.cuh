@@ -380,14 +380,16 @@ __device__ __forceinline__ void tgt_clear(typename RowMath<MODE>::Tgt &t)
 }
 
 // FP64 target entry, side 0 (x_up) or 1 (x_low): the value as a double, or,
-// with exact inner products, its (m, b) as two ints in the double's place
+// with exact inner products, (m, b + te_off) as two ints in the double's
+// place (te_off = bias + t, so that a row entry's b - t plus it is the shift
+// k = b_x + b_z + bias)
 template <int SIDE>
-__device__ __forceinline__ void xd_put(double2 &t, float v, bool xd, int tmin)
+__device__ __forceinline__ void xd_put(double2 &t, float v, bool xd, int tmin, int te_off)
 {
     double w;
     if (xd) {
         const uint32_t u = __float_as_uint(v);
-        w = __hiloint2double(xd_exp(u, tmin), xd_mant(u));
+        w = __hiloint2double(xd_exp(u, tmin) + te_off, xd_mant(u));
     } else {
         w = (double)v;
     }
@@ -470,10 +472,13 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     // column (xd_mant, xd_exp); an absent value is m = 0, b = tmin
     const bool xd = MODE == MODE_FP64 && A.xd.on;
     const int xd_tmin = A.xd.tmin, xd_bias = A.xd.bias, xd_unit = A.xd.unit;
+    // target entries hold b + te_off: a row entry's word adds its b - t
+    const int xd_te = xd_bias + xd_tmin;
     Tgt tclear;
     tgt_clear<MODE>(tclear);
     if constexpr (MODE == MODE_FP64) {
-        if (xd) tclear = make_double2(__hiloint2double(xd_tmin, 0), __hiloint2double(xd_tmin, 0));
+        // an absent value: m = 0, b = t
+        if (xd) tclear = make_double2(__hiloint2double(xd_tmin + xd_te, 0), __hiloint2double(xd_tmin + xd_te, 0));
     }
     // ---- set-up
     if constexpr (!BITS) {
@@ -508,7 +513,12 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     reinterpret_cast<uint32_t *>(val_s)[p] = A.ew[base + p];
                 } else {
                     col_s[p] = (unsigned short)A.indices[base + p];
-                    if constexpr (MODE == MODE_FP64) val_s[p] = A.values[base + p];
+                    if constexpr (MODE == MODE_FP64) {
+                        // exact inner products: the value's (m, b - t) word
+                        const float v = A.values[base + p];
+                        if (xd) reinterpret_cast<uint32_t *>(val_s)[p] = xd_word(__float_as_uint(v), xd_tmin);
+                        else val_s[p] = v;
+                    }
                 }
             }
         }
@@ -613,6 +623,24 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         else if constexpr (RES) return val_s[p];
         else if constexpr (MODE == MODE_FP64) return A.values[p];
         else return A.vmix[p];
+    };
+    // FP64 with exact inner products: entry p's column and (m, b - t) word
+    // (on chip: the word is in place of the value; streamed: from the packed
+    // 64-bit entries when there are some)
+    auto XCW = [&](int64_t p, int &c, uint32_t &w) {
+        if constexpr (RES) {
+            c = (int)col_s[p];
+            w = reinterpret_cast<const uint32_t *>(val_s)[p];
+        } else {
+            if (A.ew64) {
+                const uint64_t e = A.ew64[p];
+                c = (int)(e & 0xffffu);
+                w = (uint32_t)(e >> 16);
+            } else {
+                c = A.indices[p];
+                w = xd_word(__float_as_uint(A.values[p]), xd_tmin);
+            }
+        }
     };
     auto GETF = [&](int r) -> double {
         if constexpr (RES) return f_s[r];
@@ -726,14 +754,14 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 int c = A.indices[up.p0 + k];
                 tcu[k] = c;
                 if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
-                else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], A.values[up.p0 + k], xd, xd_tmin);
+                else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], A.values[up.p0 + k], xd, xd_tmin, xd_te);
                 else T[c].x = A.vmix[up.p0 + k];
             }
             if constexpr (!BITS) for (int k = tid; k < low.len; k += kThreads) {
                 int c = A.indices[low.p0 + k];
                 tcl[k] = c;
                 if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
-                else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], A.values[low.p0 + k], xd, xd_tmin);
+                else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], A.values[low.p0 + k], xd, xd_tmin, xd_te);
                 else T[c].y = A.vmix[low.p0 + k];
             }
             if (A.h > 0) {
@@ -780,7 +808,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         XdAcc a = xd_zero();
                         for (int k = lane; k < low.len; k += 32) {
                             const int4 t = T4[tcl[k]];
-                            xd_add(a, t.z, t.x, t.w + t.y + xd_bias);
+                            xd_add(a, t.z, t.x, t.w + t.y - (xd_te + xd_tmin));
                         }
                         xd_lane_sum<32>(a);
                         s = xd_round(a, xd_unit);
@@ -1124,15 +1152,15 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
 #pragma unroll
                             for (int j = 0; j < XB; ++j) {
                                 const int64_t p = pb + (int64_t)j * LPR;
-                                const bool in = p < p1;
-                                cb[j] = in ? COL(p) : 0;
-                                ub[j] = in ? __float_as_uint(VAL(p)) : 0u;
+                                cb[j] = 0;
+                                ub[j] = 0u;
+                                if (p < p1) XCW(p, cb[j], ub[j]);
                             }
 #pragma unroll
                             for (int j = 0; j < XB; ++j) {
                                 if (pb + (int64_t)j * LPR >= p1) break;
-                                const int32_t m = xd_mant(ub[j]);
-                                const int e = xd_exp(ub[j], xd_tmin) + xd_bias;
+                                const int32_t m = xd_word_m(ub[j]);
+                                const int e = xd_word_e(ub[j]);
                                 const int4 t = T4[cb[j]];
                                 xd_add(au, m, t.x, e + t.y);
                                 xd_add(al, m, t.z, e + t.w);
@@ -1739,7 +1767,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     for (int k = tid; k < up.len; k += kThreads) {
                         const int c = A.indices[up.p0 + k];
                         if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(Tn + c)[0] = 1;
-                        else if constexpr (MODE == MODE_FP64) xd_put<0>(Tn[c], A.values[up.p0 + k], xd, xd_tmin);
+                        else if constexpr (MODE == MODE_FP64) xd_put<0>(Tn[c], A.values[up.p0 + k], xd, xd_tmin, xd_te);
                         else Tn[c].x = A.vmix[up.p0 + k];
                     }
                     __syncthreads();
@@ -1772,9 +1800,11 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 const int4 *T4 = reinterpret_cast<const int4 *>(Tn);
                                 XdAcc a = xd_zero();
                                 for (int64_t p = p0 + gl; p < p1; p += LPR) {
-                                    const uint32_t u = __float_as_uint(VAL(p));
-                                    const int4 t = T4[COL(p)];
-                                    xd_add(a, xd_mant(u), t.x, xd_exp(u, xd_tmin) + xd_bias + t.y);
+                                    int c;
+                                    uint32_t w;
+                                    XCW(p, c, w);
+                                    const int4 t = T4[c];
+                                    xd_add(a, xd_word_m(w), t.x, xd_word_e(w) + t.y);
                                 }
                                 xd_lane_sum<LPR>(a);
                                 su = xd_round(a, xd_unit);

@@ -170,6 +170,14 @@ __global__ void k_pack_ew(int64_t nnz, const int32_t *indices, const float *vmix
     if (p < nnz) ew[p] = (__float_as_uint(vmix[p]) & 0xffff0000u) | (uint32_t)indices[p];
 }
 
+// FP64 rows with exact inner products: each stored entry as its column
+// (< 2^16) in bits 0-15 and the (m, b - t) word of its value in 16-47.
+__global__ void k_pack_ew64(int64_t nnz, const int32_t *indices, const float *values, int tmin, uint64_t *ew64)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) ew64[p] = ((uint64_t)xd_word(__float_as_uint(values[p]), tmin) << 16) | (uint32_t)indices[p];
+}
+
 // The exact-inner-product format of one matrix from its validation record
 // (values NULL: every value is 1.0); host and device compute the same.
 __host__ __device__ XdFormat xd_of_info(const IngestInfo &h, const float *values)
@@ -402,6 +410,8 @@ struct SubRowsArgs {
     uint32_t *sub_bits;
     const uint32_t *ew;          // mixed rows one word per entry, or NULL
     uint32_t *sub_ew;
+    const uint64_t *ew64;        // FP64 rows, packed entries, or NULL
+    uint64_t *sub_ew64;
     int32_t *sub_gmap;
     const __nv_bfloat16 *dmat;   // dense BF16 rows (tensor-core row tiles), or NULL
     __nv_bfloat16 *sub_dmat;
@@ -420,6 +430,7 @@ __global__ void k_sub_rows(SubRowsArgs S)
             if (S.sub_values) S.sub_values[q0 + k] = S.values[p0 + k];
             if (S.sub_vmix) S.sub_vmix[q0 + k] = S.vmix[p0 + k];
             if (S.sub_ew) S.sub_ew[q0 + k] = S.ew[p0 + k];
+            if (S.sub_ew64) S.sub_ew64[q0 + k] = S.ew64[p0 + k];
         }
         for (int k = lane; k < S.bit_words; k += 32) S.sub_bits[j * S.bit_words + k] = S.bits[i * S.bit_words + k];
         if (S.dmat) {
@@ -1259,6 +1270,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         const __nv_bfloat16 *dmat;   // dense BF16 rows for the row tiles, or NULL
         KcPlan kc;                   // kernel-row cache plan of this level
         const uint32_t *ew;          // mixed rows one word per entry (d < 2^16), or NULL
+        const uint64_t *ew64;        // FP64 rows with exact inner products, packed entries, or NULL
     };
     const bool relayout_on = (P->flags & SVM_FLAG_NO_RELAYOUT) == 0;
     bool relayout_ok = relayout_on;
@@ -1273,9 +1285,18 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         CK(cudaGetLastError());
         ++launches;
     }
+    // FP64 rows with exact inner products: column and (m, b - t) word in one
+    // 8-byte entry, which the streamed row pass loads once
+    uint64_t *ew64 = nullptr;
+    if (kmode == MODE_FP64 && D.xd.on && D.d <= 65535 && vals_fp32 && D.nnz > 0) {
+        ew64 = ar.alloc<uint64_t>(D.nnz);
+        k_pack_ew64<<<grid1(D.nnz), 256, 0, st>>>(D.nnz, D.indices, vals_fp32, D.xd.tmin, ew64);
+        CK(cudaGetLastError());
+        ++launches;
+    }
     std::vector<Level> lv;
     lv.push_back(Level{n, D.nnz, D.indptr, D.indices, vals_fp32, D.vmix, D.normf, D.norm, D.y, bits,
-                       alpha, f, status, act, seg_cnt, nullptr, nullptr, top, dmat, top_kc, ew});
+                       alpha, f, status, act, seg_cnt, nullptr, nullptr, top, dmat, top_kc, ew, ew64});
     int64_t relayouts = 0;
     auto launch_level = [&](const Level &L, int select_only, double thr, int64_t hh, int64_t limit) {
         A.n = L.n;
@@ -1285,6 +1306,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         A.values = L.values;
         A.vmix = L.vmix;
         A.ew = L.ew;
+        A.ew64 = L.ew64;
         A.y = L.y;
         A.norm = L.norm;
         A.normf = L.normf;
@@ -1375,6 +1397,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         S.sub_vmix = (Pa.vmix && kmode == MODE_MIXED) ? ar.alloc<float>(nnz_m) : nullptr;
         S.ew = Pa.ew;
         S.sub_ew = Pa.ew ? ar.alloc<uint32_t>(nnz_m) : nullptr;
+        S.ew64 = Pa.ew64;
+        S.sub_ew64 = Pa.ew64 ? ar.alloc<uint64_t>(nnz_m) : nullptr;
         S.sub_normf = Pa.normf ? ar.alloc<float>(m) : nullptr;
         S.sub_norm = Pa.norm ? ar.alloc<double>(m) : nullptr;
         S.sub_alpha = ar.alloc<double>(m);
@@ -1409,6 +1433,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         C.gmap = S.sub_gmap;
         C.dmat = S.sub_dmat;
         C.ew = S.sub_ew;
+        C.ew64 = S.sub_ew64;
         C.kc = kc_cap ? plan_kc(m, kc_cap) : KcPlan{};
         C.shape = pick_shape(m, nnz_m, sub_indptr, C.kc.slots > 0 ? smo_kdir_bytes(m, C.kc.slots, C.kc.direct) : 0);
         k_reset_active<<<C.shape.G, 256, 0, st>>>(m, C.shape.G, C.act, C.seg_cnt);

@@ -94,6 +94,8 @@ struct SmoArgs {
     const uint32_t *ew;        // mixed mode, d < 2^16: each entry as one word, column in
                                // bits 0-15 and the BF16 value's bits in 16-31 (or NULL;
                                // required for rows held on chip)
+    const uint64_t *ew64;      // FP64 mode with xd.on, d < 2^16: each entry as column
+                               // (bits 0-15) and xd_word of its value (16-47), or NULL
     const int8_t *y;
     const double *norm;        // ||x_i||^2 (FP64 / binary: exact)
     const uint32_t *bits;      // bit-mask modes: row i = words [i * W, (i + 1) * W)

@@ -69,6 +69,15 @@ static int xd_mode()
                 svmgb::xd_add(a, svmgb::xd_mant(x[i]), svmgb::xd_mant(z[i]), k);
                 svmgb::xd_add(l[i & 3], svmgb::xd_mant(x[i]), svmgb::xd_mant(z[i]), k);
             }
+            // the row-pass convention: the row side as an (m, b - t) word, the
+            // target side's exponent stored as b + bias + t
+            svmgb::XdAcc w = svmgb::xd_zero();
+            for (int i = 0; i < n; ++i) {
+                const uint32_t xw = svmgb::xd_word(x[i], f.tmin);
+                const int te = svmgb::xd_exp(z[i], f.tmin) + f.bias + f.tmin;
+                svmgb::xd_add(w, svmgb::xd_word_m(xw), svmgb::xd_mant(z[i]), svmgb::xd_word_e(xw) + te);
+            }
+            if (memcmp(&a, &w, sizeof a) != 0) ++bad;
             for (int i = n - 1; i >= 0; --i)
                 svmgb::xd_add(r, svmgb::xd_mant(x[i]), svmgb::xd_mant(z[i]),
                               svmgb::xd_exp(x[i], f.tmin) + svmgb::xd_exp(z[i], f.tmin) + f.bias);
