@@ -234,15 +234,16 @@ def row_bytes(p, precision: str, binary: bool) -> tuple[float, float]:
     step for the two target rows. Per row: the CSR entries (column index, plus
     the value unless every value is 1.0), the row pointer, f read and write,
     the index set, and for non-binary rows the norm (FP64: 8 B per entry + 29,
-    125 B at 12 entries; mixed precision with BF16 values: 6 B per entry + 29,
-    101 B; binary: 4 B per entry + 25, 81 B at 14 entries)."""
+    125 B at 12 entries; mixed precision with BF16 values and, for d < 2^16,
+    16-bit columns: 4 B per entry + 29, 77 B, else 6 B per entry; binary: 4 B
+    per entry + 25, 81 B at 14 entries)."""
     nnz_row = p.X.nnz / p.X.n
     if binary:
         per_entry, fixed = 4.0, 8 + 16 + 1
     elif precision == "fp64":
         per_entry, fixed = 8.0, 29
     else:
-        per_entry, fixed = 6.0, 29
+        per_entry, fixed = (4.0 if p.X.d < 65536 else 6.0), 29
     return per_entry * nnz_row + fixed, 2 * per_entry * nnz_row
 
 
