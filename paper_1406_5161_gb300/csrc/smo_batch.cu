@@ -194,19 +194,25 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                         }
                     }
                 } else {
-                    for (int k = tid; k < up.len; k += kThreads) {
-                        const int c = indices[up.p0 + k];
-                        tcu[k] = c;
-                        if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
-                        else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], values[up.p0 + k], xd, xd_tmin, 0);
-                        else T[c].x = vmix[up.p0 + k];
-                    }
-                    for (int k = tid; k < low.len; k += kThreads) {
-                        const int c = indices[low.p0 + k];
-                        tcl[k] = c;
-                        if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
-                        else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], values[low.p0 + k], xd, xd_tmin, 0);
-                        else T[c].y = vmix[low.p0 + k];
+                    // x_up by the first half of the threads, x_low by the
+                    // second: both rows' loads in flight together
+                    constexpr int kHalf = kThreads / 2;
+                    if (tid < kHalf) {
+                        for (int k = tid; k < up.len; k += kHalf) {
+                            const int c = indices[up.p0 + k];
+                            tcu[k] = c;
+                            if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
+                            else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], values[up.p0 + k], xd, xd_tmin, 0);
+                            else T[c].x = vmix[up.p0 + k];
+                        }
+                    } else {
+                        for (int k = tid - kHalf; k < low.len; k += kHalf) {
+                            const int c = indices[low.p0 + k];
+                            tcl[k] = c;
+                            if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
+                            else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], values[low.p0 + k], xd, xd_tmin, 0);
+                            else T[c].y = vmix[low.p0 + k];
+                        }
                     }
                 }
                 __syncthreads();

@@ -749,20 +749,29 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 kc_misses += 2 - hu_ - hl_;
             }
             // ---- 1. targets: x_up into .x / byte 0, x_low into .y / byte 1
-            //         (bit-mask modes: the masks came with the exchange)
-            if constexpr (!BITS) for (int k = tid; k < up.len; k += kThreads) {
-                int c = A.indices[up.p0 + k];
-                tcu[k] = c;
-                if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
-                else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], A.values[up.p0 + k], xd, xd_tmin, xd_te);
-                else T[c].x = A.vmix[up.p0 + k];
-            }
-            if constexpr (!BITS) for (int k = tid; k < low.len; k += kThreads) {
-                int c = A.indices[low.p0 + k];
-                tcl[k] = c;
-                if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
-                else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], A.values[low.p0 + k], xd, xd_tmin, xd_te);
-                else T[c].y = A.vmix[low.p0 + k];
+            //         (bit-mask modes: the masks came with the exchange); x_up
+            //         by the first half of the threads and x_low by the
+            //         second, so that the loads of both rows are in flight
+            //         together (one round trip to L2, not two)
+            if constexpr (!BITS) {
+                constexpr int kHalf = kThreads / 2;
+                if (tid < kHalf) {
+                    for (int k = tid; k < up.len; k += kHalf) {
+                        int c = A.indices[up.p0 + k];
+                        tcu[k] = c;
+                        if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[0] = 1;
+                        else if constexpr (MODE == MODE_FP64) xd_put<0>(T[c], A.values[up.p0 + k], xd, xd_tmin, xd_te);
+                        else T[c].x = A.vmix[up.p0 + k];
+                    }
+                } else {
+                    for (int k = tid - kHalf; k < low.len; k += kHalf) {
+                        int c = A.indices[low.p0 + k];
+                        tcl[k] = c;
+                        if constexpr (MODE == MODE_BINARY) reinterpret_cast<unsigned char *>(T + c)[1] = 1;
+                        else if constexpr (MODE == MODE_FP64) xd_put<1>(T[c], A.values[low.p0 + k], xd, xd_tmin, xd_te);
+                        else T[c].y = A.vmix[low.p0 + k];
+                    }
+                }
             }
             if (A.h > 0) {
                 counter -= 1;
