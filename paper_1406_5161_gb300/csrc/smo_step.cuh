@@ -44,7 +44,8 @@ namespace smo {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxCluster = 16;   // largest thread-block cluster launched (non-portable size)
+constexpr int kMaxCluster = 16;
+constexpr int kKcThread = 32;      // the kernel-row cache's directory keeper (lane 0 of warp 1)   // largest thread-block cluster launched (non-portable size)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
 {
@@ -360,6 +361,7 @@ struct Shared {
     CandFull xc[2][kMaxCluster];              // one cluster: every CTA's candidate, by epoch parity
     Side none[2];                             // empty I_up / I_low sides
     int kc_su, kc_sl, kc_hu, kc_hl;           // kernel-row cache: slots of x_up / x_low, hits
+    double kc_kul;                            // FP64: K(up, low) from x_up's cached row (on a hit)
     unsigned long long xbar[2];               // one cluster: mbarriers of the two parities
     ResultArea res;                           // exchange result pushed by the leader
     long long rcount[8];
@@ -713,7 +715,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             // ---- 0. kernel-row cache: this step's rows of x_up and x_low
             //         (the same decisions in every CTA; a row found here was
             //         stored by this CTA in an earlier step of this launch)
-            if (kc_on && tid == 0) {
+            // (by lane 0 of warp 1, which has no part in the target fill of
+            // short rows, so that the FP64 K(up, low) it reads from the cache
+            // arrives while the other threads fill the targets)
+            if (kc_on && tid == kKcThread) {
                 auto lookup = [&](int i, int &slot, int &hit) {
                     if (A.kc_direct) {
                         const uint32_t bit = 1u << (i & 31);
@@ -747,6 +752,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 sh.kc_sl = sl_; sh.kc_hl = hl_;
                 kc_hits += hu_ + hl_;
                 kc_misses += 2 - hu_ - hl_;
+                if constexpr (MODE == MODE_FP64) {
+                    if (hu_) sh.kc_kul = __ldcg(static_cast<const double *>(A.kc) + (size_t)su_ * A.kc_ld + low.i);
+                }
             }
             // ---- 1. targets: x_up into .x / byte 0, x_low into .y / byte 1
             //         (bit-mask modes: the masks came with the exchange); x_up
@@ -808,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     // owner of x_low's segment in an earlier step of this
                     // launch, visible here through the exchanges since)
                     if (kc_on && sh.kc_hu) {
-                        kul_c = __ldcg(static_cast<const double *>(A.kc) + (size_t)sh.kc_su * A.kc_ld + low.i);
+                        kul_c = sh.kc_kul;
                         kul_cached = true;
                     } else if (xd) {
                         // exact: the same value whatever the order or split,
@@ -1900,8 +1908,10 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
         c->exit_reason = exit_reason;
         c->shrink_events = shrink_events;
         for (int k = 0; k < 8; ++k) c->phase_cycles[k] += ph[k];
-        c->kc_hits += kc_hits;
-        c->kc_misses += kc_misses;
+    }
+    if (cta == 0 && tid == kKcThread) {
+        A.ctrl->kc_hits += kc_hits;
+        A.ctrl->kc_misses += kc_misses;
     }
 }
 
