@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_batch_kernel(BatchArgs B)
                 }
                 sd.i = r;
                 sd.y = y_of(sb);
-                sd.pad = 0;
+                sd.owner = 0;
                 return sd;
             };
             {

@@ -44,8 +44,8 @@ namespace smo {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxCluster = 16;
-constexpr int kKcThread = 32;      // the kernel-row cache's directory keeper (lane 0 of warp 1)   // largest thread-block cluster launched (non-portable size)
+constexpr int kMaxCluster = 16;    // largest thread-block cluster launched (non-portable size)
+constexpr int kKcThread = 32;      // the kernel-row cache's directory keeper (lane 0 of warp 1)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
 {
@@ -70,6 +70,43 @@ __device__ __forceinline__ void step_bar_sync(int n) { asm volatile("bar.sync 1,
 __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Words of the several-cluster exchange: 32 bits of data in the low half of
+// an 8-byte word whose high half is the epoch that wrote it. An aligned
+// 8-byte access is single-copy atomic (each element of a .v2.b64 access is
+// one), so a reader that finds its epoch in a word has that word's data: the
+// data carry their own flag, with no fence behind the writer's stores and no
+// second trip to L2 for the data after the flag.
+__device__ __forceinline__ void st_tagged2(ulonglong2 *p, uint32_t d0, uint32_t d1, uint32_t ep)
+{
+    const unsigned long long w0 = ((unsigned long long)ep << 32) | d0, w1 = ((unsigned long long)ep << 32) | d1;
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(w0), "l"(w1) : "memory");
+}
+__device__ __forceinline__ ulonglong2 ld_tagged2(const ulonglong2 *p)
+{
+    ulonglong2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+    return v;
+}
+
+// Waits (acquire) until a leader's release flag reaches the given epoch;
+// gives up after timeout_ns of %globaltimer, or at once when another CTA has
+// flagged an error, and then flags the error itself.
+static __device__ __noinline__ void wait_released(const unsigned *flag, unsigned need, long long timeout_ns, int *err)
+{
+    uint64_t t0 = 0;
+    int spins = 0;
+    while (ld_acquire_u32(flag) < need) {
+        if (++spins >= 64) {
+            spins = 0;
+            if (*(volatile int *)err) return;
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > (uint64_t)timeout_ns) { atomicExch(err, 1); return; }
+        }
+    }
 }
 
 // named barrier 2 among the row warps only (warps 1..; the pair-step warp
@@ -173,7 +210,7 @@ struct Side {
     int32_t i;      // global sample index (INT_MAX when empty)
     int32_t len;    // CSR length of the row
     int32_t y;
-    int32_t pad;
+    int32_t owner;  // cluster of the CTA whose segment holds the row
     uint32_t m[8];  // bit-mask modes: the row's bits (unused words zero)
 };
 
@@ -189,6 +226,10 @@ static_assert(offsetof(Side, f) == 0 && offsetof(Side, i) == 32 && offsetof(Side
 // global exchange slots: each candidate and each flag on lines of its own
 constexpr size_t kCandStride = 256;
 static_assert(sizeof(CandFull) <= kCandStride, "candidate slot too small");
+// a leader's tagged slot: the first 48 bytes of both winning sides and the
+// cluster's active count, 25 data words in 13 pairs
+constexpr int kTagPairs = 13;
+static_assert(kTagPairs * 16 <= (int)kCandStride, "tagged slot too small");
 
 // Result of a step's exchange, written into every CTA of a cluster.
 struct __align__(16) ResultArea {   // (sizeof a multiple of 16)
@@ -197,6 +238,10 @@ struct __align__(16) ResultArea {   // (sizeof a multiple of 16)
     int flag;          // a wait timed out
     int gap_open;      // b_low - b_up > the launch's threshold (Eq. kktterm): step on
 };
+// the several-cluster exchange writes a result as 16-byte words: the first
+// 48 bytes of each side and (total, flag, gap_open)
+static_assert(offsetof(ResultArea, low) == 80 && offsetof(ResultArea, total) == 160 &&
+              offsetof(ResultArea, flag) == 168 && offsetof(ResultArea, gap_open) == 172, "ResultArea layout");
 
 // FP64 compares and selects are long-latency on sm_103a; comparisons here
 // use an order-preserving integer image of the double instead:
@@ -259,7 +304,7 @@ __device__ __forceinline__ void side_empty(Side &s, bool up)
     s.i = INT_MAX;
     s.len = 0;
     s.y = 0;
-    s.pad = 0;
+    s.owner = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) s.m[w] = 0;
 }
@@ -286,6 +331,11 @@ __device__ __forceinline__ void copy_result(ResultArea *dst, const ResultArea *s
     uint4 *d = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
     for (int w = 0; w < (int)(sizeof(ResultArea) / 16); ++w) d[w] = s[w];
+}
+__device__ __forceinline__ uint4 shfl_u4(uint4 v, int src)
+{
+    return make_uint4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                      __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 // (key, index) of the I_up and I_low sides of a candidate
 __device__ __forceinline__ void cand_keys(const CandFull &c, unsigned long long &k1, int &i1,
@@ -357,6 +407,7 @@ struct Shared {
     Side rup[8], rlow[8];                     // per-warp winners of the exchange
     unsigned long long rkup[8], rklow[8];
     int riup[8], rilow[8], rto[8];
+    unsigned rrel[kWarps];                    // several clusters: least epoch seen released by every leader, per warp
     CandFull ccand[kMaxCluster];              // cluster leader: its CTAs' candidates
     CandFull xc[2][kMaxCluster];              // one cluster: every CTA's candidate, by epoch parity
     Side none[2];                             // empty I_up / I_low sides
@@ -439,6 +490,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     const int crank = (int)cluster.block_rank();
     const int cid = cta / csize;                   // cluster index = leader slot
     const int nlead = G / csize;
+    // warps that poll the exchange slots; the warp after them releases the
+    // leader's epochs and the rest record those of all leaders (FP64 cache)
+    const int xwarps = (nlead + 31) / 32;
     const int d = A.d;
     // kernel-row cache: K(x_up, .) and K(x_low, .) of recent steps, per CTA
     // segment, in device memory (FP64 and mixed modes)
@@ -686,6 +740,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     const double snap = 1e-12 * C, c_snap = C - snap;
     const float gammaf = (float)A.gamma;
     unsigned epoch = 0;
+    int kc_pf0 = -1, kc_pf1 = -1;   // directory keeper: cache slots filled in the previous step
     int exit_reason = 0;
     bool gap_open = first || dless(A.thr, low.f - up.f);   // stopping test of the pair in up / low
     int prev_valid = 0;              // buffer (1 - buf) holds the previous targets
@@ -753,7 +808,26 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 kc_hits += hu_ + hl_;
                 kc_misses += 2 - hu_ - hl_;
                 if constexpr (MODE == MODE_FP64) {
-                    if (hu_) sh.kc_kul = __ldcg(static_cast<const double *>(A.kc) + (size_t)su_ * A.kc_ld + low.i);
+                    if (hu_) {
+                        // the entry was written by the CTA that owns x_low's
+                        // row. Several clusters: its leader's release of an
+                        // epoch after the write, acquired by this cluster's
+                        // leader during the exchange or here, makes it
+                        // visible: the epoch just ended for a slot filled in
+                        // the previous step, else the one before (the least
+                        // epoch this CTA saw released by every leader during
+                        // the last exchange is in sh.rrel)
+                        if constexpr (!SOLO) {
+                            const unsigned need = (su_ == kc_pf0 || su_ == kc_pf1) ? epoch : epoch - 1u;
+                            unsigned seen = 0xffffffffu;
+                            for (int w = xwarps + 1; w < kWarps; ++w) seen = min(seen, sh.rrel[w]);
+                            if (seen < need)
+                                wait_released(A.seq + (size_t)low.owner * kSeqStride, need, A.timeout_ns, &A.ctrl->err);
+                        }
+                        sh.kc_kul = __ldcg(static_cast<const double *>(A.kc) + (size_t)su_ * A.kc_ld + low.i);
+                    }
+                    kc_pf0 = hu_ ? -1 : su_;
+                    kc_pf1 = hl_ ? -1 : sl_;
                 }
             }
             // ---- 1. targets: x_up into .x / byte 0, x_low into .y / byte 1
@@ -1433,7 +1507,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             sd.i = (int)(lo + r);
             sd.len = (int)(p1 - p0);
             sd.y = y_of(sb);
-            sd.pad = 0;
+            sd.owner = cid;
 #pragma unroll
             for (int w = 0; w < 8; ++w) sd.m[w] = 0;
             if constexpr (BITS) {
@@ -1484,6 +1558,11 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             cnt = kept;
         }
         if (timed && tid == 0) { uint64_t t = clock64(); ph[2] += t - tp; tp = t; }
+        // tagged slot of the exchange through global memory, per leader (per
+        // CTA in a flat launch) and epoch parity
+        auto tslot = [&](int par, int c) {
+            return reinterpret_cast<ulonglong2 *>(static_cast<unsigned char *>(A.cand) + ((size_t)par * nlead + c) * kCandStride);
+        };
         auto exchange = [&](bool gx) {
             // ---- 4. grid-wide exchange. One cluster over the whole grid: each
             //         CTA writes its candidate into every CTA's shared memory and
@@ -1516,9 +1595,9 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         const uint4 *su = reinterpret_cast<const uint4 *>(mu ? &sh.wup[__ffs(mu) - 1] : &sh.none[0]);
                         const uint4 *sl = reinterpret_cast<const uint4 *>(ml ? &sh.wlow[__ffs(ml) - 1] : &sh.none[1]);
                         constexpr int kSideV = (int)(sizeof(Side) / 16);
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < kSideV; ++j) st_async_v4(dst + 16 * j, su[j], rbar);
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < kSideV; ++j) st_async_v4(dst + (uint32_t)sizeof(Side) + 16 * j, sl[j], rbar);
                         st_async_v4(dst + (uint32_t)offsetof(CandFull, count), make_uint4((unsigned)cnt, 0u, 0u, 0u), rbar);
                     }
@@ -1564,7 +1643,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     const int i1s = i1, i2s = i2;
                     warp_min_ki(k1, i1);
                     warp_min_ki(k2, i2);
-    #pragma unroll
+#pragma unroll
                     for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
                     const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                     const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
@@ -1588,7 +1667,21 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 __syncthreads();
             } else {
                 cluster.sync();
-                const int rwarps = (nlead + 31) / 32;
+                const int rwarps = xwarps;
+                // FP64 with the kernel-row cache: each CTA reads K(up, low)
+                // of a cached row from the entry another CTA wrote. Each
+                // leader releases the epoch (its cluster's writes before the
+                // barrier above) on a flag of its own, and every CTA records
+                // the least epoch it sees released by all leaders, both by
+                // warps that have no part in the exchange.
+                const bool rel_on = MODE == MODE_FP64 && kc_on;
+                if (rel_on && warp > rwarps) {
+                    unsigned m = 0xffffffffu;
+                    for (int c = (warp - rwarps - 1) * 32 + lane; c < nlead; c += (kWarps - rwarps - 1) * 32)
+                        m = min(m, ld_acquire_u32(A.seq + (size_t)c * kSeqStride));
+                    m = __reduce_min_sync(0xffffffffu, m);
+                    if (lane == 0) sh.rrel[warp] = m;
+                }
                 if (crank == 0) {
                     if (warp == 0) {
                         // cluster winner -> this leader's global slot
@@ -1601,21 +1694,33 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         const int i1s = i1, i2s = i2;
                         warp_min_ki(k1, i1);
                         warp_min_ki(k2, i2);
-    #pragma unroll
+#pragma unroll
                         for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
                         const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                         const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
-                        if (lane == 0) {
-                            CandFull *out = reinterpret_cast<CandFull *>(static_cast<unsigned char *>(A.cand) +
-                                                                         ((size_t)par * nlead + cid) * kCandStride);
-                            if (mu) copy_side(&out->up, &sh.ccand[__ffs(mu) - 1].up);
-                            else { Side e; side_empty(e, true); copy_side(&out->up, &e); }
-                            if (ml) copy_side(&out->low, &sh.ccand[__ffs(ml) - 1].low);
-                            else { Side e; side_empty(e, false); copy_side(&out->low, &e); }
-                            out->count = (int32_t)cc;
-                            st_release_u32(A.seq + ((size_t)par * nlead + cid) * kSeqStride, epoch);
+                        if constexpr (BITS) {
+                            if (lane == 0) {
+                                CandFull *out = reinterpret_cast<CandFull *>(static_cast<unsigned char *>(A.cand) +
+                                                                             ((size_t)par * nlead + cid) * kCandStride);
+                                if (mu) copy_side(&out->up, &sh.ccand[__ffs(mu) - 1].up);
+                                else { Side e; side_empty(e, true); copy_side(&out->up, &e); }
+                                if (ml) copy_side(&out->low, &sh.ccand[__ffs(ml) - 1].low);
+                                else { Side e; side_empty(e, false); copy_side(&out->low, &e); }
+                                out->count = (int32_t)cc;
+                                st_release_u32(A.seq + ((size_t)par * nlead + cid) * kSeqStride, epoch);
+                            }
+                        } else if (lane < kTagPairs) {
+                            // the first 48 bytes of both winning sides and the
+                            // count, as tagged words (lane j: words 2j, 2j + 1)
+                            const uint32_t *wsu = reinterpret_cast<const uint32_t *>(mu ? &sh.ccand[__ffs(mu) - 1].up : &sh.none[0]);
+                            const uint32_t *wsl = reinterpret_cast<const uint32_t *>(ml ? &sh.ccand[__ffs(ml) - 1].low : &sh.none[1]);
+                            auto word = [&](int q) -> uint32_t {
+                                return q < 12 ? wsu[q] : (q < 24 ? wsl[q - 12] : (q == 24 ? (uint32_t)cc : 0u));
+                            };
+                            st_tagged2(tslot(par, cid) + lane, word(2 * lane), word(2 * lane + 1), epoch);
                         }
                     }
+                    if (rel_on && warp == rwarps && lane == 0) st_release_u32(A.seq + (size_t)cid * kSeqStride, epoch);
                     if (warp < rwarps) {
                         const int c = warp * 32 + lane;
                         int ai = INT_MAX, bi = INT_MAX;
@@ -1628,28 +1733,61 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         // writes its side without another trip to L2
                         uint4 wu0 = make_uint4(0, 0, 0, 0), wu1 = wu0, wu2 = wu0, wl0 = wu0, wl1 = wu0, wl2 = wu0;
                         if (c < nlead) {
-                            const unsigned *sp = A.seq + ((size_t)par * nlead + c) * kSeqStride;
                             uint64_t t0 = 0;
                             int spins = 0;
-                            // acquire loads: the slot was written before the flag
-                            while (ld_acquire_u32(sp) < epoch) {
+                            auto waited_out = [&]() {
                                 if (++spins >= 256) {
                                     spins = 0;
                                     uint64_t now = global_ns();
                                     if (t0 == 0) t0 = now;
-                                    else if (now - t0 > (uint64_t)A.timeout_ns) { timed_out = 1; break; }
-                                    if (*(volatile int *)&A.ctrl->err) { timed_out = 1; break; }
+                                    else if (now - t0 > (uint64_t)A.timeout_ns) return true;
+                                    if (*(volatile int *)&A.ctrl->err) return true;
+                                }
+                                return false;
+                            };
+                            if constexpr (BITS) {
+                                const unsigned *sp = A.seq + ((size_t)par * nlead + c) * kSeqStride;
+                                // acquire loads: the slot was written before the flag
+                                while (ld_acquire_u32(sp) < epoch) {
+                                    if (waited_out()) { timed_out = 1; break; }
+                                }
+                                if (!timed_out) {
+                                    // L2 reads (bypass L1, which is not coherent across SMs)
+                                    gp = reinterpret_cast<const CandFull *>(static_cast<const unsigned char *>(A.cand) +
+                                                                            ((size_t)par * nlead + c) * kCandStride);
+                                    const uint4 *pu = reinterpret_cast<const uint4 *>(&gp->up);
+                                    const uint4 *pl = reinterpret_cast<const uint4 *>(&gp->low);
+                                    wu0 = __ldcg(pu); wu1 = __ldcg(pu + 1); wu2 = __ldcg(pu + 2);
+                                    wl0 = __ldcg(pl); wl1 = __ldcg(pl + 1); wl2 = __ldcg(pl + 2);
+                                    cc = __ldcg(&gp->count);
+                                }
+                            } else {
+                                // every word of the slot tagged with this epoch
+                                const ulonglong2 *sp = tslot(par, c);
+                                uint32_t d[2 * kTagPairs];
+                                for (;;) {
+                                    unsigned ok = 1u;
+#pragma unroll
+                                    for (int j = 0; j < kTagPairs; ++j) {
+                                        const ulonglong2 w = ld_tagged2(sp + j);
+                                        d[2 * j] = (uint32_t)w.x;
+                                        d[2 * j + 1] = (uint32_t)w.y;
+                                        ok &= (unsigned)((uint32_t)(w.x >> 32) == epoch) & (unsigned)((uint32_t)(w.y >> 32) == epoch);
+                                    }
+                                    if (ok) break;
+                                    if (waited_out()) { timed_out = 1; break; }
+                                }
+                                if (!timed_out) {
+                                    wu0 = make_uint4(d[0], d[1], d[2], d[3]);
+                                    wu1 = make_uint4(d[4], d[5], d[6], d[7]);
+                                    wu2 = make_uint4(d[8], d[9], d[10], d[11]);
+                                    wl0 = make_uint4(d[12], d[13], d[14], d[15]);
+                                    wl1 = make_uint4(d[16], d[17], d[18], d[19]);
+                                    wl2 = make_uint4(d[20], d[21], d[22], d[23]);
+                                    cc = (int)d[24];
                                 }
                             }
                             if (!timed_out) {
-                                // L2 reads (bypass L1, which is not coherent across SMs)
-                                gp = reinterpret_cast<const CandFull *>(static_cast<const unsigned char *>(A.cand) +
-                                                                        ((size_t)par * nlead + c) * kCandStride);
-                                const uint4 *pu = reinterpret_cast<const uint4 *>(&gp->up);
-                                const uint4 *pl = reinterpret_cast<const uint4 *>(&gp->low);
-                                wu0 = __ldcg(pu); wu1 = __ldcg(pu + 1); wu2 = __ldcg(pu + 2);
-                                wl0 = __ldcg(pl); wl1 = __ldcg(pl + 1); wl2 = __ldcg(pl + 2);
-                                cc = __ldcg(&gp->count);
                                 ai = (int)wu2.x;
                                 bi = (int)wl2.x;
                                 af = __hiloint2double((int)wu0.y, (int)wu0.x);
@@ -1664,52 +1802,84 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         if (gx) { k2 = k1; i2 = i1; }
                         warp_min_ki(k1, i1);
                         warp_min_ki(k2, i2);
-    #pragma unroll
-                        for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
-                        if (lane == 0) {
-                            sh.rkup[warp] = k1; sh.riup[warp] = i1;
-                            sh.rklow[warp] = k2; sh.rilow[warp] = i2;
-                            sh.rcount[warp] = cc;
-                            sh.rto[warp] = any_to;
-                        }
-                        if constexpr (BITS) {
-                            if (i1 != INT_MAX && ai == i1) copy_side_ldcg(&sh.rup[warp], &gp->up);
-                            if (i2 != INT_MAX && bi == i2) copy_side_ldcg(&sh.rlow[warp], &gp->low);
-                        } else {
-                            auto put48 = [](Side *dst, const uint4 &a, const uint4 &b, const uint4 &c) {
-                                unsigned long long *d8 = reinterpret_cast<unsigned long long *>(dst);
-                                const uint4 v[3] = {a, b, c};
 #pragma unroll
-                                for (int w = 0; w < 3; ++w) {
-                                    d8[2 * w] = ((unsigned long long)v[w].y << 32) | v[w].x;
-                                    d8[2 * w + 1] = ((unsigned long long)v[w].w << 32) | v[w].z;
-                                }
-                            };
-                            if (i1 != INT_MAX && ai == i1) put48(&sh.rup[warp], wu0, wu1, wu2);
-                            if (i2 != INT_MAX && bi == i2) put48(&sh.rlow[warp], wl0, wl1, wl2);
+                        for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
+                        if (!BITS && rwarps == 1) {
+                            // one warp holds every leader's candidate: the
+                            // winning sides go from their lanes straight into
+                            // the result area of every CTA of the cluster
+                            // (lane q writes CTA q's)
+                            const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && ai == i1);
+                            const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && bi == i2);
+                            const int su = mu ? __ffs(mu) - 1 : 0, sl = ml ? __ffs(ml) - 1 : 0;
+                            uint4 ru[3] = {shfl_u4(wu0, su), shfl_u4(wu1, su), shfl_u4(wu2, su)};
+                            uint4 rl[3] = {shfl_u4(wl0, sl), shfl_u4(wl1, sl), shfl_u4(wl2, sl)};
+                            if (!mu) {
+                                const uint4 *e = reinterpret_cast<const uint4 *>(&sh.none[0]);
+                                ru[0] = e[0]; ru[1] = e[1]; ru[2] = e[2];
+                            }
+                            if (!ml) {
+                                const uint4 *e = reinterpret_cast<const uint4 *>(&sh.none[1]);
+                                rl[0] = e[0]; rl[1] = e[1]; rl[2] = e[2];
+                            }
+                            const double fu = __hiloint2double((int)ru[0].y, (int)ru[0].x);
+                            const double fl = __hiloint2double((int)rl[0].y, (int)rl[0].x);
+                            const uint4 tail = make_uint4((unsigned)(unsigned long long)cc, (unsigned)((unsigned long long)cc >> 32),
+                                                          (unsigned)any_to, (unsigned)dless(A.thr, fl - fu));
+                            if (lane < csize) {
+                                uint4 *o = reinterpret_cast<uint4 *>(cluster.map_shared_rank(&sh.res, lane));
+                                o[0] = ru[0]; o[1] = ru[1]; o[2] = ru[2];
+                                o[5] = rl[0]; o[6] = rl[1]; o[7] = rl[2];
+                                o[10] = tail;
+                            }
+                        } else {
+                            if (lane == 0) {
+                                sh.rkup[warp] = k1; sh.riup[warp] = i1;
+                                sh.rklow[warp] = k2; sh.rilow[warp] = i2;
+                                sh.rcount[warp] = cc;
+                                sh.rto[warp] = any_to;
+                            }
+                            if constexpr (BITS) {
+                                if (i1 != INT_MAX && ai == i1) copy_side_ldcg(&sh.rup[warp], &gp->up);
+                                if (i2 != INT_MAX && bi == i2) copy_side_ldcg(&sh.rlow[warp], &gp->low);
+                            } else {
+                                auto put48 = [](Side *dst, const uint4 &a, const uint4 &b, const uint4 &c) {
+                                    unsigned long long *d8 = reinterpret_cast<unsigned long long *>(dst);
+                                    const uint4 v[3] = {a, b, c};
+#pragma unroll
+                                    for (int w = 0; w < 3; ++w) {
+                                        d8[2 * w] = ((unsigned long long)v[w].y << 32) | v[w].x;
+                                        d8[2 * w + 1] = ((unsigned long long)v[w].w << 32) | v[w].z;
+                                    }
+                                };
+                                if (i1 != INT_MAX && ai == i1) put48(&sh.rup[warp], wu0, wu1, wu2);
+                                if (i2 != INT_MAX && bi == i2) put48(&sh.rlow[warp], wl0, wl1, wl2);
+                            }
                         }
                     }
-                    __syncthreads();
-                    if (warp == 0) {
-                        // final winner, pushed to every CTA of the cluster
-                        unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
-                        int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0, to = sh.rto[0];
-                        long long cc = sh.rcount[0];
-                        for (int w = 1; w < rwarps; ++w) {
-                            if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
-                            if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
-                            cc += sh.rcount[w];
-                            to |= sh.rto[w];
+                    if (BITS || rwarps > 1) {
+                        __syncthreads();
+                        if (warp == 0) {
+                            // final winner, pushed to every CTA of the cluster
+                            unsigned long long ku = sh.rkup[0], kl = sh.rklow[0];
+                            int iu = sh.riup[0], il = sh.rilow[0], wu = 0, wl = 0, to = sh.rto[0];
+                            long long cc = sh.rcount[0];
+                            for (int w = 1; w < rwarps; ++w) {
+                                if (ki_less(sh.rkup[w], sh.riup[w], ku, iu)) { ku = sh.rkup[w]; iu = sh.riup[w]; wu = w; }
+                                if (ki_less(sh.rklow[w], sh.rilow[w], kl, il)) { kl = sh.rklow[w]; il = sh.rilow[w]; wl = w; }
+                                cc += sh.rcount[w];
+                                to |= sh.rto[w];
+                            }
+                            if (lane == 0) {
+                                if (iu != INT_MAX) copy_side(&sh.res.up, &sh.rup[wu]); else side_empty(sh.res.up, true);
+                                if (il != INT_MAX) copy_side(&sh.res.low, &sh.rlow[wl]); else side_empty(sh.res.low, false);
+                                sh.res.total = cc;
+                                sh.res.flag = to;
+                                sh.res.gap_open = dless(A.thr, sh.res.low.f - sh.res.up.f);
+                            }
+                            __syncwarp();
+                            if (lane > 0 && lane < csize) copy_result(cluster.map_shared_rank(&sh.res, lane), &sh.res);
                         }
-                        if (lane == 0) {
-                            if (iu != INT_MAX) copy_side(&sh.res.up, &sh.rup[wu]); else side_empty(sh.res.up, true);
-                            if (il != INT_MAX) copy_side(&sh.res.low, &sh.rlow[wl]); else side_empty(sh.res.low, false);
-                            sh.res.total = cc;
-                            sh.res.flag = to;
-                            sh.res.gap_open = dless(A.thr, sh.res.low.f - sh.res.up.f);
-                        }
-                        __syncwarp();
-                        if (lane > 0 && lane < csize) copy_result(cluster.map_shared_rank(&sh.res, lane), &sh.res);
                     }
                 }
                 cluster.sync();

@@ -326,7 +326,7 @@ constexpr int kChunkRows = 4096;
 constexpr int64_t kFp64OneClusterRows = 8192;
 // smallest FP64-mode problem that takes one CTA per SM with the flat exchange
 // even when its segments fit in shared memory
-constexpr int64_t kFp64FlatRows = 49152;
+constexpr int64_t kFp64FlatRows = 200000;
 __global__ void k_sub_len_sums(int64_t m, const int32_t *idx, const int64_t *indptr, int64_t *sums)
 {
     __shared__ unsigned long long s;
@@ -1082,7 +1082,7 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
     int32_t *act = ar.alloc<int32_t>(n);
     int32_t *seg_cnt = ar.alloc<int32_t>(256);
     // exchange slots and flags for the largest grid of any level (<= 256 CTAs)
-    void *cand = ar.alloc<unsigned char>(2 * (size_t)256 * smo_cand_bytes());
+    void *cand = ar.alloc<unsigned char>(smo_cand_slots(256) * smo_cand_bytes());
     unsigned *seq = ar.alloc<unsigned>(smo_seq_words(256));
     SmoCtrl *ctrl = ar.alloc<SmoCtrl>(1);
     const int64_t trace_len = (P->trace && P->trace_len > 0) ? P->trace_len : 0;
@@ -1330,6 +1330,8 @@ int train_impl(const svm_csr *X, const int8_t *y, const svm_params *P, const svm
         A.compact_below = (relayout_ok && hh > 0 && !one_cluster_on_chip && L.n >= 2048) ? L.n * 3 / 4 : 0;
         CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
         CK(cudaMemsetAsync(seq, 0, sizeof(unsigned) * smo_seq_words(L.shape.G), st));
+        // tagged slots: a word of an earlier launch must not carry this one's epochs
+        CK(cudaMemsetAsync(cand, 0, smo_cand_slots(L.shape.G) * smo_cand_bytes(), st));
         A.thr = thr;
         A.h = hh;
         A.iter_limit = limit;
@@ -2753,7 +2755,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     uint8_t *status = W.take<uint8_t>(n);
     int32_t *act = W.take<int32_t>(n);
     int32_t *seg_cnt = W.take<int32_t>(G);
-    void *cand = W.take<unsigned char>(2 * (size_t)G * smo_cand_bytes());
+    void *cand = W.take<unsigned char>(smo_cand_slots(G) * smo_cand_bytes());
     unsigned *seq = W.take<unsigned>(smo_seq_words(G));
     SmoCtrl *ctrl = W.take<SmoCtrl>(1);
     const int nbf = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 4095) / 4096));
@@ -2802,6 +2804,7 @@ int train_fixed_impl(const svm_csr *X, const int8_t *y, const svm_params *P, dou
     // every call starts from a zeroed exchange area and a fresh control block
     CK(cudaMemcpyAsync(ctrl, &hc, sizeof hc, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(seq, 0, sizeof(unsigned) * smo_seq_words(G), st));
+    CK(cudaMemsetAsync(cand, 0, smo_cand_slots(G) * smo_cand_bytes(), st));
     CK(launch_smo_persistent(mode, lpr, A, L0.total, st, cs));
     ++launches;
     CK(cudaMemcpyAsync(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost, st));

@@ -105,7 +105,7 @@ struct SmoArgs {
     uint8_t *status;           // bits 0-2 index set, bit 7 label is +1
     int32_t *act;              // active lists, segment s at [lo(s), lo(s) + cnt(s))
     int32_t *seg_cnt;
-    void *cand;                // [2][G] candidate slots of smo_cand_bytes() each
+    void *cand;                // smo_cand_slots(G) candidate slots of smo_cand_bytes() each
     unsigned *seq;             // [2][G], zeroed before each launch
     SmoCtrl *ctrl;
     int32_t *trace;            // [2 * trace_len]
@@ -278,6 +278,9 @@ __host__ __device__ inline size_t smo_kdir_bytes(int64_t n, int slots, int direc
 // apart (a 128-byte line each); the array holds smo_seq_words(G) words
 constexpr int kSeqStride = 32;
 __host__ __device__ inline size_t smo_seq_words(int G) { return 2 * (size_t)G * kSeqStride; }
+// global exchange slots of smo_cand_bytes() each for a launch of G CTAs: one
+// per leader and epoch parity
+__host__ __device__ inline size_t smo_cand_slots(int G) { return 2 * (size_t)G; }
 size_t smo_static_smem(int mode);   // static shared memory of the step kernel of this mode
 int smo_threads();
 
