@@ -493,6 +493,12 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
     // warps that poll the exchange slots; the warp after them releases the
     // leader's epochs and the rest record those of all leaders (FP64 cache)
     const int xwarps = (nlead + 31) / 32;
+    // leaders' slots as tagged words when one warp polls them all; a flat
+    // launch over more CTAs (every slot read by every CTA) and bit-mask rows
+    // use a release flag per slot and read only what they need after it
+    const bool tagged = !BITS && nlead <= 32;
+    // the leaders' release flags for the FP64 kernel-row cache
+    auto rel_flag = [&](int c) { return A.seq + ((size_t)2 * nlead + c) * kSeqStride; };
     const int d = A.d;
     // kernel-row cache: K(x_up, .) and K(x_low, .) of recent steps, per CTA
     // segment, in device memory (FP64 and mixed modes)
@@ -822,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             unsigned seen = 0xffffffffu;
                             for (int w = xwarps + 1; w < kWarps; ++w) seen = min(seen, sh.rrel[w]);
                             if (seen < need)
-                                wait_released(A.seq + (size_t)low.owner * kSeqStride, need, A.timeout_ns, &A.ctrl->err);
+                                wait_released(rel_flag(low.owner), need, A.timeout_ns, &A.ctrl->err);
                         }
                         sh.kc_kul = __ldcg(static_cast<const double *>(A.kc) + (size_t)su_ * A.kc_ld + low.i);
                     }
@@ -1678,7 +1684,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                 if (rel_on && warp > rwarps) {
                     unsigned m = 0xffffffffu;
                     for (int c = (warp - rwarps - 1) * 32 + lane; c < nlead; c += (kWarps - rwarps - 1) * 32)
-                        m = min(m, ld_acquire_u32(A.seq + (size_t)c * kSeqStride));
+                        m = min(m, ld_acquire_u32(rel_flag(c)));
                     m = __reduce_min_sync(0xffffffffu, m);
                     if (lane == 0) sh.rrel[warp] = m;
                 }
@@ -1698,7 +1704,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
                         const unsigned mu = __ballot_sync(0xffffffffu, i1 != INT_MAX && k1s == k1 && i1s == i1);
                         const unsigned ml = __ballot_sync(0xffffffffu, i2 != INT_MAX && k2s == k2 && i2s == i2);
-                        if constexpr (BITS) {
+                        if (!tagged) {
                             if (lane == 0) {
                                 CandFull *out = reinterpret_cast<CandFull *>(static_cast<unsigned char *>(A.cand) +
                                                                              ((size_t)par * nlead + cid) * kCandStride);
@@ -1720,7 +1726,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             st_tagged2(tslot(par, cid) + lane, word(2 * lane), word(2 * lane + 1), epoch);
                         }
                     }
-                    if (rel_on && warp == rwarps && lane == 0) st_release_u32(A.seq + (size_t)cid * kSeqStride, epoch);
+                    if (rel_on && warp == rwarps && lane == 0) st_release_u32(rel_flag(cid), epoch);
                     if (warp < rwarps) {
                         const int c = warp * 32 + lane;
                         int ai = INT_MAX, bi = INT_MAX;
@@ -1745,7 +1751,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                                 }
                                 return false;
                             };
-                            if constexpr (BITS) {
+                            if (!tagged) {
                                 const unsigned *sp = A.seq + ((size_t)par * nlead + c) * kSeqStride;
                                 // acquire loads: the slot was written before the flag
                                 while (ld_acquire_u32(sp) < epoch) {
@@ -1804,7 +1810,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                         warp_min_ki(k2, i2);
 #pragma unroll
                         for (int off = 16; off >= 1; off >>= 1) cc += __shfl_xor_sync(0xffffffffu, cc, off);
-                        if (!BITS && rwarps == 1) {
+                        if (tagged) {
                             // one warp holds every leader's candidate: the
                             // winning sides go from their lanes straight into
                             // the result area of every CTA of the cluster
@@ -1857,7 +1863,7 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                             }
                         }
                     }
-                    if (BITS || rwarps > 1) {
+                    if (!tagged) {
                         __syncthreads();
                         if (warp == 0) {
                             // final winner, pushed to every CTA of the cluster

@@ -274,10 +274,11 @@ __host__ __device__ inline size_t smo_kdir_bytes(int64_t n, int slots, int direc
 {
     return direct ? (size_t)((n + 31) / 32) * 4 : (size_t)slots * 8;
 }
-// global exchange flags: one per leader and epoch parity, kSeqStride words
-// apart (a 128-byte line each); the array holds smo_seq_words(G) words
+// global exchange flags, kSeqStride words apart (a 128-byte line each): one
+// per leader and epoch parity, then one per leader releasing its epochs to
+// the FP64 kernel-row cache's cross-CTA reads; smo_seq_words(G) words
 constexpr int kSeqStride = 32;
-__host__ __device__ inline size_t smo_seq_words(int G) { return 2 * (size_t)G * kSeqStride; }
+__host__ __device__ inline size_t smo_seq_words(int G) { return 3 * (size_t)G * kSeqStride; }
 // global exchange slots of smo_cand_bytes() each for a launch of G CTAs: one
 // per leader and epoch parity
 __host__ __device__ inline size_t smo_cand_slots(int G) { return 2 * (size_t)G; }
