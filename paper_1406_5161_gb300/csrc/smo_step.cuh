@@ -20,9 +20,11 @@
 //      FP64 gradient update of Eq. (fup), on shrink iterations the rule of
 //      Eq. (shrink), and the CTA's best I_up / I_low candidates;
 //   4. a grid-wide exchange of the CTA candidates (the paper's
-//      MPI_Allreduce "GlobalMinMax") through release/acquire flags in global
-//      memory; every CTA reduces the candidates in the same order and gets
-//      the same next pair (Eq. bminmax, lowest index on ties);
+//      MPI_Allreduce "GlobalMinMax"): within a cluster through distributed
+//      shared memory, between cluster leaders through global memory (slots
+//      of epoch-tagged words, or release/acquire flags); every CTA reduces
+//      the candidates in the same order and gets the same next pair
+//      (Eq. bminmax, lowest index on ties);
 //   5. on shrink iterations each CTA compacts its active list in place.
 //
 // All waits on other CTAs are bounded by a time limit; on expiry the kernel
@@ -1576,7 +1578,8 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
             //         candidates in the same order. Several clusters: the CTAs of a
             //         cluster hand their candidates to its first CTA through
             //         distributed shared memory; only those leaders exchange
-            //         through global memory (release/acquire flags, bounded
+            //         through global memory (tagged slots when one warp polls
+            //         them all, else a release/acquire flag per slot; bounded
             //         waits) and push the result back to their cluster.
             ++epoch;
             const int par = (int)(epoch & 1);
