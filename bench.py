@@ -177,11 +177,39 @@ def job_totals(dist, seconds: float, units: float, device) -> tuple[float, float
     return float(t.item()), float(u.item())
 
 
-def kernel_source_hash() -> str:
+def _code_tokens(text: str) -> str:
+    """C/C++ source without its comments and whitespace (string and character
+    literals kept whole), so that the hash below changes with the code only."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            if not c.isspace():
+                out.append(c)
+            i += 1
+    return "".join(out)
+
+
+def kernel_source_hash(root: str = ROOT) -> str:
+    """Hash of the fused step kernel's code (its sources without comments or
+    whitespace): the committed ncu records carry it, and a record whose hash
+    differs was taken on other code."""
     h = hashlib.sha256()
     for name in ("smo_step.cuh", "svm_internal.cuh", "fp64_math.cuh", "expfx_table.inc"):
-        with open(os.path.join(ROOT, "paper_1406_5161_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(root, "paper_1406_5161_gb300", "csrc", name), encoding="utf-8") as fh:
+            h.update(_code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
