@@ -819,12 +819,12 @@ __global__ void __launch_bounds__(kThreads, 1) smo_persistent_kernel(SmoArgs A)
                     if (hu_) {
                         // the entry was written by the CTA that owns x_low's
                         // row. Several clusters: its leader's release of an
-                        // epoch after the write, acquired by this cluster's
-                        // leader during the exchange or here, makes it
-                        // visible: the epoch just ended for a slot filled in
-                        // the previous step, else the one before (the least
-                        // epoch this CTA saw released by every leader during
-                        // the last exchange is in sh.rrel)
+                        // epoch after the write, acquired by this CTA's spare
+                        // warps during the last exchange (the least epoch
+                        // they saw released by every leader is in sh.rrel)
+                        // or here, makes it visible: the epoch just ended for
+                        // a slot filled in the previous step, else the one
+                        // before
                         if constexpr (!SOLO) {
                             const unsigned need = (su_ == kc_pf0 || su_ == kc_pf1) ? epoch : epoch - 1u;
                             unsigned seen = 0xffffffffu;
